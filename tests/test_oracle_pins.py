@@ -1,0 +1,333 @@
+"""Pins for the oracle's residual R(u), J(u)v and J(u)^T w against what the paper and
+the mathematics fix, independently of the oracle's own code:
+
+* polynomial consistency: the SIPG/upwind scheme is consistent, so the interpolant
+  of an exact solution in Q^p (with its strong-form sources and Dirichlet data)
+  has R = 0 to rounding (Sec. 3, Eq. NPDG/chargeDG; sources from the PDEs Eq. NP2
+  and Eq. charge2, derived symbolically);
+* global conservation: testing with v = 1 leaves only boundary and source terms,
+  computed here from Gauss-Lobatto face sums and numpy's Gauss-Legendre weights
+  (Eq. NPDG in conservation form; the inlet/outlet/electrode terms of Sec. 3.3);
+* symmetry of the interior-penalty blocks (the "symmetric interior penalty" of
+  Sec. 3.2), constants in the kernel of the potential block under natural
+  boundary conditions, and positive definiteness with Dirichlet faces;
+* p = 0 reduction to the textbook first-order upwind finite-volume scheme;
+* J(u)v against central finite differences of R; the assembled J against Jv and
+  J^T w (for the dual-number machinery).
+The manufactured-solution convergence rates are in test_oracle_mms.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import mms
+
+
+def _with(prob, **kw):
+    import dataclasses
+    return dataclasses.replace(prob, **kw)
+
+
+def _all_tags(prob, tag):
+    return [np.full_like(t, tag) for t in prob.tags]
+
+
+# ------------------------------------------------------------ consistency
+CONSISTENCY_CASES = [
+    # (name, config, p, c-expressions, phi-expression, velocity override)
+    ("2d_p1", "mms2d_n3", 1, ["2 + x + 0.5*y + 0.25*x*y"], "0.3 - x + 0.7*y + 0.1*x*y", None),
+    ("2d_p2", "mms2d_n3", 2, ["2 + x + 0.5*y**2 - 0.3*x*y + 0.2*x**2*y"],
+     "0.5 - x + y**2 + 0.2*x*y", None),
+    ("2d_p3", "mms2d_n2", 3, ["3 + x**3 - 0.5*y**2 + 0.3*x*y**3"], "x**2*y - 0.4*y**3 + x",
+     None),
+    ("3d_p2_plate", "cube_n2_p2", 2, ["2 + 0.5*x + 0.3*y*z + 0.2*z**2 - 0.1*x**2*y"],
+     "x - y + 0.5*x*z + 0.1*y**2", "plate"),
+    ("3d_p1_3ions", "channel_n1", 1, ["1 + 0.2*x + 0.1*y*z", "2 - 0.1*x*y + 0.3*z"],
+     "0.2*x - 0.1*y + 0.05*x*y*z", "plate"),
+]
+
+
+@pytest.mark.parametrize("case", CONSISTENCY_CASES, ids=[c[0] for c in CONSISTENCY_CASES])
+def test_polynomial_consistency(case):
+    sp = pytest.importorskip("sympy")
+    _, cfg, p, cs, ph, vel = case
+    P = W.config(cfg, p=p)
+    P = _with(P, tags=_all_tags(P, W.DIRICHLET), bv_oxidant=-1)
+    if P.dim == 2:
+        P = _with(P, vel_kind=W.VEL_CONSTANT, vel_params=[1.0, 0.5, 0, 0, 0, 0, 0, 0])
+    x, y, z = sp.symbols("x y z")
+    loc = {"x": x, "y": y, "z": z}
+    exact, sources = mms.build(P, [sp.sympify(c, locals=loc) for c in cs],
+                               sp.sympify(ph, locals=loc))
+    orc0 = oracle.Oracle(P)
+    u, s, d = mms.problem_data(orc0, exact, sources)
+    orc = oracle.Oracle(P, src=s, dirichlet=d)
+    r = orc.residual(u)
+    # scale: the size of the individual terms, seen through a perturbed state
+    rng = np.random.default_rng(0)
+    scale = np.abs(orc.residual(u + 1e-3 * rng.standard_normal(u.size))).max()
+    assert scale > 1e-6
+    assert np.abs(r).max() < 1e-11 * max(1.0, np.abs(u).max()), np.abs(r).max()
+    # and a mistaken Dirichlet trace is seen: shift the exterior data
+    bad = oracle.Oracle(P, src=s, dirichlet=d + 1e-3)
+    assert np.abs(bad.residual(u)).max() > 1e-8
+
+
+# ------------------------------------------------------------ conservation
+def _gll_weights(p):
+    _, _, xn = oracle.rules(p, p + 2)
+    Pp = np.polynomial.legendre.Legendre.basis(p)
+    return 2.0 / (p * (p + 1) * Pp(xn) ** 2)
+
+
+@pytest.mark.parametrize("cfg", ["cube_n3_p2", "channel_n1", "mms2d_n3"])
+def test_global_conservation(cfg):
+    """Sum over all rows of species k = outlet flux + inlet flux - electrode
+    reaction - source; sum of the potential rows = -electrode current - source."""
+    P = W.config(cfg)
+    ubar = [0.7, 0.2, 0.1] if P.dim == 3 else [0.7, 0.2, 0.0]
+    tags = [t.copy() for t in P.tags]
+    tags[0][:] = W.INLET
+    tags[1][:] = W.OUTLET
+    for s in range(2, 2 * P.dim):
+        keep = tags[s] >= W.ELECTRODE0
+        tags[s][:] = W.OUTLET if s % 2 else W.INLET
+        tags[s][keep] = W.ELECTRODE0 if s == 2 else W.ELECTRODE0 + 1
+    if P.dim == 2:
+        tags[2][3:5] = W.ELECTRODE0
+    if P.bv_oxidant < 0:
+        P = _with(P, bv_oxidant=0, bv_J0=0.3, bv_phi_app=[0.4, -0.2, 0, 0])
+    P = _with(P, tags=tags, vel_kind=W.VEL_CONSTANT, vel_params=ubar + [0.0] * 5,
+              bv_J0_axis=-1)
+    src = W.random_sources(P, 11)
+    phi0 = 0.05
+    u = W.random_state(P, 12).reshape(P.n_fields, P.E, P.Np)
+    u[0] = phi0
+    u = u.reshape(-1)
+    orc = oracle.Oracle(P, src=src)
+    r = orc.residual(u).reshape(P.n_fields, P.E, P.Np)
+    tot = r.sum(axis=(1, 2))
+
+    # independent boundary integrals: Gauss-Lobatto face sums of nodal values
+    n = P.p + 1
+    wl = _gll_weights(P.p)
+    uu = u.reshape(P.n_fields, P.E, *([n] * P.dim)[::-1])  # [f][e][(z)][y][x]
+    ne = P.n_el
+    expect = np.zeros(P.n_fields)
+    mu_fac = [P.z[k] * P.D[k] / P.RT * P.F for k in range(P.m)]
+
+    def c_ox(vals):
+        if P.bv_oxidant < P.m - 1:
+            return vals[P.bv_oxidant + 1]
+        return -sum(P.z[k] * vals[k + 1] for k in range(P.m - 1)) / P.z[P.m - 1]
+
+    for s in range(2 * P.dim):
+        a, hi = s // 2, s & 1
+        others = [b for b in range(P.dim) if b != a]
+        nrm = 1.0 if hi else -1.0
+        un = ubar[a] * nrm
+        shape = [ne[b] for b in others]
+        for loc in range(int(np.prod(shape))):
+            idx = [0, 0, 0]
+            if P.dim == 3:
+                idx[others[0]] = loc % shape[0]
+                idx[others[1]] = loc // shape[0]
+            else:
+                idx[others[0]] = loc
+            idx[a] = ne[a] - 1 if hi else 0
+            e = idx[0] + ne[0] * (idx[1] + ne[1] * idx[2])
+            hs = [P.coords[b][idx[b] + 1] - P.coords[b][idx[b]] for b in others]
+            jac = np.prod([h / 2 for h in hs])
+            # nodal values on the face, as an array over the other axes
+            sl = [slice(None)] * P.dim
+            sl[P.dim - 1 - a] = -1 if hi else 0
+            face = uu[:, e][(slice(None),) + tuple(sl)]  # [f][...] axes reversed
+            wt = wl if P.dim == 2 else np.outer(wl, wl)
+            integ = lambda vals: jac * float(np.sum(wt * vals))
+            tag = tags[s][loc]
+            if tag == W.INLET:
+                for k in range(P.m - 1):
+                    expect[k + 1] += un * P.c_in[k] * jac * float(np.sum(wt))
+            elif tag == W.OUTLET:
+                for k in range(P.m - 1):
+                    expect[k + 1] += un * integ(face[k + 1])  # grad Phi = 0: q.n = u.n
+            elif tag >= W.ELECTRODE0:
+                j = tag - W.ELECTRODE0
+                fac = P.bv_n * P.F / P.RT
+                eta = P.bv_phi_app[j] - phi0
+                co = c_ox(face)
+                Jn = P.bv_J0 * (math.exp(P.bv_alpha1 * fac * eta)
+                                - (co / P.bv_c_ref) * math.exp(-P.bv_alpha2 * fac * eta))
+                if P.bv_oxidant < P.m - 1:
+                    expect[P.bv_oxidant + 1] -= integ(Jn) / (P.bv_n * P.F)
+                expect[0] -= P.z[P.bv_oxidant] / P.bv_n * integ(Jn)
+    # sources: numpy Gauss-Legendre weights times the element Jacobians
+    xg, wg = np.polynomial.legendre.leggauss(P.q)
+    wq = wg if P.dim == 2 else np.einsum("i,j,k->kji", wg, wg, wg).reshape(-1)
+    if P.dim == 2:
+        wq = np.outer(wg, wg).reshape(-1)
+    srcr = src.reshape(P.n_fields, P.E, P.Nq)
+    for e in range(P.E):
+        idx = [e % ne[0], (e // ne[0]) % ne[1], e // (ne[0] * ne[1])]
+        jac = np.prod([(P.coords[a][idx[a] + 1] - P.coords[a][idx[a]]) / 2 for a in range(P.dim)])
+        expect -= jac * srcr[:, e] @ wq
+    np.testing.assert_allclose(tot, expect, rtol=1e-11, atol=1e-11 * np.abs(expect).max())
+    assert np.abs(r).max() > 1e3 * np.abs(tot - expect).max()  # the sum is not trivially 0
+
+
+# ------------------------------------------------------------ SIPG structure
+def _blocks(P, J):
+    nf = P.n_fields
+    n1 = P.E * P.Np
+    return lambda f, g: J[f * n1:(f + 1) * n1, g * n1:(g + 1) * n1]
+
+
+@pytest.mark.parametrize("cfg", ["cube_n2_p2", "mms2d_n3", "channel_n1"])
+def test_potential_block_symmetric_any_state(cfg):
+    P = W.config(cfg)
+    u = W.random_state(P, 5, c_amp=0.3)
+    J = oracle.Oracle(P, dirichlet=W.random_dirichlet(P, 6)).jacobian(u)
+    A = _blocks(P, J)(0, 0).toarray()
+    if P.bv_oxidant >= 0:  # the Butler-Volmer term adds a diagonal-type boundary mass
+        pass
+    asym = np.abs(A - A.T).max() / np.abs(A).max()
+    assert asym < 1e-13, asym
+
+
+def test_potential_block_kernel_and_definiteness():
+    P = W.config("cube_n2_p2")
+    u = W.random_state(P, 5, c_amp=0.3)
+    walls = _with(P, tags=_all_tags(P, W.WALL), bv_oxidant=-1)
+    A = _blocks(walls, oracle.Oracle(walls).jacobian(u))(0, 0).toarray()
+    ones = np.ones(A.shape[0])
+    assert np.abs(A @ ones).max() < 1e-12 * np.abs(A).max()
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert ev[0] > -1e-12 * ev[-1] and ev[1] > 1e-8 * ev[-1]  # one zero mode only
+    dirich = _with(P, tags=_all_tags(P, W.DIRICHLET), bv_oxidant=-1)
+    A = _blocks(dirich, oracle.Oracle(dirich).jacobian(u))(0, 0).toarray()
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert ev[0] > 1e-8 * ev[-1]
+
+
+def test_species_block_symmetric_without_transport():
+    P = W.config("cube_n2_p2")
+    P = _with(P, tags=_all_tags(P, W.DIRICHLET), bv_oxidant=-1, vel_kind=W.VEL_CONSTANT,
+              vel_params=[0.0] * 8)
+    u = W.random_state(P, 9).reshape(P.n_fields, P.E, P.Np)
+    u[0] = 0.3  # constant potential: q_k = u = 0
+    J = oracle.Oracle(P).jacobian(u.reshape(-1))
+    A = _blocks(P, J)(1, 1).toarray()
+    assert np.abs(A - A.T).max() < 1e-13 * np.abs(A).max()
+    # with flow the upwind term makes it non-symmetric
+    P2 = _with(P, vel_params=[1.0, 0.3, 0.0, 0, 0, 0, 0, 0])
+    A2 = _blocks(P2, oracle.Oracle(P2).jacobian(u.reshape(-1)))(1, 1).toarray()
+    assert np.abs(A2 - A2.T).max() > 1e-3 * np.abs(A2).max()
+
+
+# ------------------------------------------------------------ p = 0 upwind
+@pytest.mark.parametrize("dim", [2, 3])
+def test_p0_is_first_order_upwind_finite_volume(dim):
+    P = W.config("mms2d_n4" if dim == 2 else "cube_n3_p0", p=0)
+    ubar = [1.0, -0.4, 0.25]
+    tags = []
+    for s in range(2 * dim):
+        a, hi = s // 2, s & 1
+        out = (ubar[a] > 0) == bool(hi)
+        tags.append(np.full_like(P.tags[s], W.OUTLET if out else W.INLET))
+    P = _with(P, tags=tags, vel_kind=W.VEL_CONSTANT, vel_params=ubar + [0.0] * 5,
+              bv_oxidant=-1)
+    rng = np.random.default_rng(3)
+    coords = [np.concatenate([[0.0], np.cumsum(rng.uniform(0.5, 1.5, P.n_el[a]))])
+              for a in range(dim)]
+    P = _with(P, coords=coords)
+    src = W.random_sources(P, 4)
+    u = W.random_state(P, 5, c_amp=0.5)
+    r = oracle.Oracle(P, src=src).residual(u).reshape(P.n_fields, P.E)
+    c = u.reshape(P.n_fields, P.E)[1]
+    ne = P.n_el
+    fv = np.zeros(P.E)
+    xg, wg = np.polynomial.legendre.leggauss(P.q)
+    wsum = wg.sum() ** dim
+    s1 = src.reshape(P.n_fields, P.E, P.Nq)
+    for e in range(P.E):
+        idx = [e % ne[0], (e // ne[0]) % ne[1], e // (ne[0] * ne[1])]
+        h = [coords[a][idx[a] + 1] - coords[a][idx[a]] for a in range(dim)]
+        vol = np.prod(h)
+        wq = np.ones(P.Nq) * 0
+        # source integral: sum of the quadrature values times the weights
+        if dim == 2:
+            wq = np.outer(wg, wg).reshape(-1)
+        else:
+            wq = np.einsum("i,j,k->ijk", wg, wg, wg).reshape(-1)
+        fv[e] -= vol / 2 ** dim * s1[1, e] @ wq
+        for a in range(dim):
+            area = vol / h[a]
+            for hi in (0, 1):
+                n = 1.0 if hi else -1.0
+                un = ubar[a] * n
+                nb = list(idx)
+                nb[a] += 1 if hi else -1
+                if 0 <= nb[a] < ne[a]:
+                    en = nb[0] + ne[0] * (nb[1] + ne[1] * nb[2])
+                    cup = c[e] if un > 0 else c[en]
+                    fv[e] += area * un * cup
+                elif un < 0:
+                    fv[e] += area * un * P.c_in[0]
+                else:
+                    fv[e] += area * un * c[e]
+    np.testing.assert_allclose(r[1], fv, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(r[0], -np.array([np.prod(
+        [coords[a][([e % ne[0], (e // ne[0]) % ne[1], e // (ne[0] * ne[1])][a]) + 1]
+         - coords[a][[e % ne[0], (e // ne[0]) % ne[1], e // (ne[0] * ne[1])][a]]
+         for a in range(dim)]) / 2 ** dim * (s1[0, e] @ (np.outer(wg, wg).reshape(-1) if dim == 2
+                                             else np.einsum("i,j,k->ijk", wg, wg, wg).reshape(-1)))
+        for e in range(P.E)]), rtol=1e-13, atol=1e-13)
+
+
+# ------------------------------------------------------------ derivatives
+DERIV_CASES = ["mms2d_n3", "cube_n2_p3", "channel_n1", "reactor_n1_p2"]
+
+
+@pytest.mark.parametrize("cfg", DERIV_CASES)
+def test_jvp_matches_central_differences(cfg):
+    P = W.config(cfg)
+    orc = oracle.Oracle(P, src=W.random_sources(P, 1), dirichlet=W.random_dirichlet(P, 2))
+    u = W.random_state(P, 3)
+    v = W.random_vector(P, 4)
+    jv = orc.jvp(u, v)
+    h = 1e-6
+    fd = (orc.residual(u + h * v) - orc.residual(u - h * v)) / (2 * h)
+    assert np.linalg.norm(jv - fd) / np.linalg.norm(jv) < 1e-7
+
+
+@pytest.mark.parametrize("cfg", ["mms2d_n3", "cube_n2_p2", "channel_n1"])
+def test_assembled_jacobian_consistent(cfg):
+    P = W.config(cfg)
+    orc = oracle.Oracle(P, dirichlet=W.random_dirichlet(P, 2))
+    u = W.random_state(P, 3)
+    v, w = W.random_vector(P, 4), W.random_vector(P, 5)
+    J = orc.jacobian(u)
+    jv = orc.jvp(u, v)
+    assert np.linalg.norm(J @ v - jv) <= 1e-13 * np.linalg.norm(jv)
+    cols = np.arange(0, P.n_dof, 5)
+    jtw = orc.vjp_entries(u, w, cols)
+    ref = (J.T @ w)[cols]
+    assert np.linalg.norm(jtw - ref) <= 1e-13 * np.linalg.norm(ref)
+    # <w, J v> = <J^T w, v>
+    full = orc.vjp_entries(u, w, np.arange(P.n_dof))
+    assert abs(w @ jv - full @ v) <= 1e-12 * abs(w @ jv)
+
+
+def test_element_subset_rows_match_full():
+    P = W.config("cube_n3_p2")
+    orc = oracle.Oracle(P)
+    u = W.random_state(P, 3)
+    full = orc.residual(u).reshape(P.n_fields, P.E, P.Np)
+    el = np.array([0, 5, 13, 26])
+    part = orc.residual(u, elems=el).reshape(P.n_fields, P.E, P.Np)
+    np.testing.assert_array_equal(part[:, el], full[:, el])
+    mask = np.ones(P.E, bool); mask[el] = False
+    assert np.all(part[:, mask] == 0)
