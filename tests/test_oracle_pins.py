@@ -83,10 +83,16 @@ def _gll_weights(p):
     return 2.0 / (p * (p + 1) * Pp(xn) ** 2)
 
 
-@pytest.mark.parametrize("cfg", ["cube_n3_p2", "channel_n1", "mms2d_n3"])
-def test_global_conservation(cfg):
+@pytest.mark.parametrize("cfg,grad_phi", [("cube_n3_p2", None), ("channel_n1", None),
+                                          ("mms2d_n3", None), ("cube_n3_p2", (0.4, -0.3, 0.2)),
+                                          ("channel_n1", (-0.5, 0.25, 0.1)),
+                                          ("mms2d_n3", (0.6, 0.3, 0.0))])
+def test_global_conservation(cfg, grad_phi):
     """Sum over all rows of species k = outlet flux + inlet flux - electrode
-    reaction - source; sum of the potential rows = -electrode current - source."""
+    reaction - source; sum of the potential rows = -electrode current - source.
+    With grad_phi the potential is the linear function grad_phi . x (exactly in
+    Q^p), there are no electrodes, and the outlet flux carries the migration
+    velocity q_k . n = u . n - z_k mu_k F dPhi/dn."""
     P = W.config(cfg)
     ubar = [0.7, 0.2, 0.1] if P.dim == 3 else [0.7, 0.2, 0.0]
     tags = [t.copy() for t in P.tags]
@@ -105,7 +111,15 @@ def test_global_conservation(cfg):
     src = W.random_sources(P, 11)
     phi0 = 0.05
     u = W.random_state(P, 12).reshape(P.n_fields, P.E, P.Np)
-    u[0] = phi0
+    gphi = np.zeros(3)
+    if grad_phi is not None:
+        tags = [np.where(t >= W.ELECTRODE0, W.WALL, t).astype(np.uint8) for t in tags]
+        P = _with(P, tags=tags)
+        gphi = np.asarray(grad_phi, dtype=float)
+        xn = oracle.Oracle(P).node_points().reshape(P.E, P.Np, 3)
+        u[0] = phi0 + xn @ gphi
+    else:
+        u[0] = phi0
     u = u.reshape(-1)
     orc = oracle.Oracle(P, src=src)
     r = orc.residual(u).reshape(P.n_fields, P.E, P.Np)
@@ -153,7 +167,8 @@ def test_global_conservation(cfg):
                     expect[k + 1] += un * P.c_in[k] * jac * float(np.sum(wt))
             elif tag == W.OUTLET:
                 for k in range(P.m - 1):
-                    expect[k + 1] += un * integ(face[k + 1])  # grad Phi = 0: q.n = u.n
+                    qn = un - mu_fac[k] * gphi[a] * nrm
+                    expect[k + 1] += qn * integ(face[k + 1])
             elif tag >= W.ELECTRODE0:
                 j = tag - W.ELECTRODE0
                 fac = P.bv_n * P.F / P.RT
@@ -221,6 +236,13 @@ def test_species_block_symmetric_without_transport():
     J = oracle.Oracle(P).jacobian(u.reshape(-1))
     A = _blocks(P, J)(1, 1).toarray()
     assert np.abs(A - A.T).max() < 1e-13 * np.abs(A).max()
+    # coercive with the penalty C_IP = 10 (Sec. 3.2): positive definite; the
+    # penalty-free form of the same block is indefinite on this mesh
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert ev[0] > 1e-8 * ev[-1]
+    P0 = _with(P, C_IP=0.0)
+    A0 = _blocks(P0, oracle.Oracle(P0).jacobian(u.reshape(-1)))(1, 1).toarray()
+    assert np.linalg.eigvalsh(0.5 * (A0 + A0.T))[0] < 0
     # with flow the upwind term makes it non-symmetric
     P2 = _with(P, vel_params=[1.0, 0.3, 0.0, 0, 0, 0, 0, 0])
     A2 = _blocks(P2, oracle.Oracle(P2).jacobian(u.reshape(-1)))(1, 1).toarray()
@@ -228,15 +250,20 @@ def test_species_block_symmetric_without_transport():
 
 
 # ------------------------------------------------------------ p = 0 upwind
-@pytest.mark.parametrize("dim", [2, 3])
-def test_p0_is_first_order_upwind_finite_volume(dim):
+@pytest.mark.parametrize("dim,dirichlet", [(2, False), (3, False), (2, True), (3, True)])
+def test_p0_is_first_order_upwind_finite_volume(dim, dirichlet):
+    """At p = 0 every gradient and the penalty (p^2 = 0) vanish, leaving the
+    textbook upwind finite-volume scheme: flux u.n c_upwind through each face,
+    with c_in on inlets, the cell value on outlets, and on Dirichlet faces the
+    exterior state g as the upwind value where u.n < 0."""
     P = W.config("mms2d_n4" if dim == 2 else "cube_n3_p0", p=0)
     ubar = [1.0, -0.4, 0.25]
     tags = []
     for s in range(2 * dim):
         a, hi = s // 2, s & 1
         out = (ubar[a] > 0) == bool(hi)
-        tags.append(np.full_like(P.tags[s], W.OUTLET if out else W.INLET))
+        t = W.DIRICHLET if dirichlet else (W.OUTLET if out else W.INLET)
+        tags.append(np.full_like(P.tags[s], t))
     P = _with(P, tags=tags, vel_kind=W.VEL_CONSTANT, vel_params=ubar + [0.0] * 5,
               bv_oxidant=-1)
     rng = np.random.default_rng(3)
@@ -244,8 +271,12 @@ def test_p0_is_first_order_upwind_finite_volume(dim):
               for a in range(dim)]
     P = _with(P, coords=coords)
     src = W.random_sources(P, 4)
+    gd = W.random_dirichlet(P, 6, amp=0.5).reshape(P.n_fields, P.n_bfaces, P.Nfq)
     u = W.random_state(P, 5, c_amp=0.5)
-    r = oracle.Oracle(P, src=src).residual(u).reshape(P.n_fields, P.E)
+    r = oracle.Oracle(P, src=src, dirichlet=gd.reshape(-1)).residual(u).reshape(P.n_fields, P.E)
+    side_off = np.concatenate([[0], np.cumsum([len(t) for t in P.tags])])
+    xg1, wg1 = np.polynomial.legendre.leggauss(P.q)
+    wface = wg1 if dim == 2 else np.outer(wg1, wg1).reshape(-1)  # point order irrelevant: sum
     c = u.reshape(P.n_fields, P.E)[1]
     ne = P.n_el
     fv = np.zeros(P.E)
@@ -274,6 +305,15 @@ def test_p0_is_first_order_upwind_finite_volume(dim):
                     en = nb[0] + ne[0] * (nb[1] + ne[1] * nb[2])
                     cup = c[e] if un > 0 else c[en]
                     fv[e] += area * un * cup
+                elif dirichlet:
+                    others = [b for b in range(dim) if b != a]
+                    loc = idx[others[0]] + (ne[others[0]] * idx[others[1]] if dim == 3 else 0)
+                    bf = side_off[2 * a + hi] + loc
+                    if un > 0:
+                        fv[e] += area * un * c[e]
+                    else:  # mean of the exterior state over the face
+                        gmean = gd[1, bf] @ wface / wface.sum()
+                        fv[e] += area * un * gmean
                 elif un < 0:
                     fv[e] += area * un * P.c_in[0]
                 else:
