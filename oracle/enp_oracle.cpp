@@ -687,7 +687,7 @@ int oracle_vjp_entries(void* h, const double* u, const double* w, const double* 
       long long c = cols[t];
       int Kc = (int)((c / P.Np) % P.E);
       ud[c].d = 1.0;
-      int nb[6]; int cnt = neighbours(P, Kc, nb);
+      int nb[7]; int cnt = neighbours(P, Kc, nb);  // up to 2*dim neighbours + itself
       nb[cnt++] = Kc;
       double acc = 0.0;
       for (int j = 0; j < cnt; ++j) {

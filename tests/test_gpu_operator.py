@@ -1,0 +1,175 @@
+"""Parity of the CUDA operator (through the C ABI) with the FP64 CPU oracle.
+
+R(u), J(u)v and J(u)^T w are compared element by element on the same seeded
+inputs, as a norm-wise relative error ||x_gpu - x_oracle|| / ||x_oracle||:
+FP64 must agree to 1e-12 (the exact result up to rounding order: the oracle
+uses full quadrature, the GPU sum factorisation). Small meshes are checked in
+full; the full-size workloads on sampled elements, which the oracle computes
+row block by row block. J(u)^T w is checked against the oracle's assembled
+transpose (dual-number columns).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def _enp():
+    import paper_2112_09271_gb300 as enp
+    enp.build()
+    return enp
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _setup(cfg, seed=0, sources=True):
+    import torch
+    enp = _enp()
+    P = W.config(cfg) if isinstance(cfg, str) else cfg
+    src = W.random_sources(P, 100 + seed) if sources else None
+    dirv = W.random_dirichlet(P, 200 + seed) if sources else None
+    orc = oracle.Oracle(P, src=src, dirichlet=dirv)
+    op = enp.Operator(P)
+    if sources:
+        op.set_sources(torch.tensor(src, device="cuda"), torch.tensor(dirv, device="cuda"))
+    return P, orc, op
+
+
+SMALL = ["mms2d_n3", "mms2d_n4", "cube_n3_p1", "cube_n3_p2", "cube_n3_p3", "cube_n2_p4",
+         "channel_n1", "channel_n2", "reactor_n1_p2"]
+
+
+def _small(cfg):
+    if cfg == "mms2d_n4":
+        return W.config("mms2d_n4", p=3)
+    if cfg == "channel_n1":
+        return W.config("channel_n1", p=2)
+    return W.config(cfg)
+
+
+@pytest.mark.parametrize("cfg", SMALL)
+def test_residual_matches_oracle(cfg):
+    import torch
+    P, orc, op = _setup(_small(cfg), sources=True)
+    u = W.random_state(P, 1)
+    r = op.residual(torch.tensor(u, device="cuda")).cpu().numpy()
+    ref = orc.residual(u)
+    assert _rel(r, ref) < TOL64, _rel(r, ref)
+
+
+@pytest.mark.parametrize("cfg", SMALL)
+def test_jvp_matches_oracle(cfg):
+    import torch
+    P, orc, op = _setup(_small(cfg), sources=True)
+    u, v = W.random_state(P, 1), W.random_vector(P, 2)
+    jv = op.jvp(torch.tensor(u, device="cuda"), torch.tensor(v, device="cuda")).cpu().numpy()
+    ref = orc.jvp(u, v)
+    assert _rel(jv, ref) < TOL64, _rel(jv, ref)
+
+
+@pytest.mark.parametrize("cfg", SMALL)
+def test_vjp_matches_oracle_transpose(cfg):
+    import torch
+    P, orc, op = _setup(_small(cfg), sources=True)
+    u, w = W.random_state(P, 1), W.random_vector(P, 3)
+    jtw = op.vjp(torch.tensor(u, device="cuda"), torch.tensor(w, device="cuda")).cpu().numpy()
+    ref = orc.vjp_entries(u, w, np.arange(P.n_dof))
+    assert _rel(jtw, ref) < TOL64, _rel(jtw, ref)
+
+
+def test_vjp_is_the_adjoint_of_jvp_on_gpu():
+    import torch
+    P, orc, op = _setup("cube_n4_p3", sources=False)
+    u = torch.tensor(W.random_state(P, 1), device="cuda")
+    v = torch.tensor(W.random_vector(P, 2), device="cuda")
+    w = torch.tensor(W.random_vector(P, 3), device="cuda")
+    lhs = torch.dot(w, op.jvp(u, v)).item()
+    rhs = torch.dot(op.vjp(u, w), v).item()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+FULL = [("cube16_p3", 48), ("channel64_p3", 24), ("cube24_p2", 24), ("reactor192_p2", 24)]
+
+
+@pytest.mark.parametrize("cfg,nsample", FULL)
+def test_full_size_sampled_rows(cfg, nsample):
+    """At the benchmark sizes, in the launch configuration the bench uses: the
+    GPU computes every row, the oracle the rows of sampled elements (including
+    boundary and electrode elements)."""
+    import torch
+    P = W.config(cfg)
+    enp = _enp()
+    op = enp.Operator(P)
+    orc = oracle.Oracle(P)
+    u = W.random_state(P, 2)
+    v = W.random_vector(P, 3)
+    w = W.random_vector(P, 4)
+    rng = np.random.default_rng(5)
+    el = np.unique(np.concatenate([rng.choice(P.E, nsample, replace=False),
+                                   [0, P.E - 1, P.n_el[0] * P.n_el[1] // 2]]))
+    ud, vd, wd = (torch.tensor(x, device="cuda") for x in (u, v, w))
+    r = op.residual(ud).cpu().numpy().reshape(P.n_fields, P.E, P.Np)[:, el]
+    jv = op.jvp(ud, vd).cpu().numpy().reshape(P.n_fields, P.E, P.Np)[:, el]
+    rr = orc.residual(u, elems=el).reshape(P.n_fields, P.E, P.Np)[:, el]
+    jr = orc.jvp(u, v, elems=el).reshape(P.n_fields, P.E, P.Np)[:, el]
+    assert _rel(r, rr) < TOL64
+    assert _rel(jv, jr) < TOL64
+    # J^T w on the columns of a few sampled elements
+    cols = np.concatenate([f * P.E * P.Np + e * P.Np + np.arange(P.Np)
+                           for e in el[:6] for f in range(P.n_fields)])
+    jtw = op.vjp(ud, wd).cpu().numpy()[cols]
+    assert _rel(jtw, orc.vjp_entries(u, w, cols)) < TOL64
+
+
+@pytest.mark.parametrize("cfg", ["cube_n3_p3", "channel_n2"])
+def test_jvp_f32_matches_oracle_to_single_precision(cfg):
+    import torch
+    P, orc, op = _setup(cfg, sources=False)
+    u, v = W.random_state(P, 1), W.random_vector(P, 2)
+    jv = op.jvp_f32(torch.tensor(u, device="cuda", dtype=torch.float32),
+                    torch.tensor(v, device="cuda", dtype=torch.float32)).cpu().numpy()
+    ref = orc.jvp(u, v)
+    assert _rel(jv.astype(np.float64), ref) < 2e-5
+
+
+def test_batched_operating_points_match_single_runs():
+    import torch
+    enp = _enp()
+    P = W.config("reactor_n1_p2")
+    B = 3
+    phis = np.array([[0.1 * 38.92 * (b + 1), 0.0, 0.0, 0.0] for b in range(B)])
+    opb = enp.Operator(P, batch=B)
+    opb.set_phi_app(phis)
+    u = np.concatenate([W.random_state(P, 10 + b) for b in range(B)])
+    v = np.concatenate([W.random_vector(P, 20 + b) for b in range(B)])
+    ud, vd = torch.tensor(u, device="cuda"), torch.tensor(v, device="cuda")
+    rb = opb.residual(ud).cpu().numpy().reshape(B, -1)
+    jb = opb.jvp(ud, vd).cpu().numpy().reshape(B, -1)
+    import dataclasses
+    for b in range(B):
+        Pb = dataclasses.replace(P, bv_phi_app=list(phis[b]))
+        orc = oracle.Oracle(Pb)
+        ub, vb = u.reshape(B, -1)[b], v.reshape(B, -1)[b]
+        assert _rel(rb[b], orc.residual(ub)) < TOL64
+        assert _rel(jb[b], orc.jvp(ub, vb)) < TOL64
+
+
+def test_unsupported_and_invalid_inputs_raise():
+    import dataclasses
+    enp = _enp()
+    P = W.config("cube_n2_p3")
+    with pytest.raises(enp.EnpError) as ei:
+        enp.Operator(dataclasses.replace(P, q=P.p + 1))
+    assert ei.value.status == enp.ENP_ERR_UNSUPPORTED
+    bad = [c.copy() for c in P.coords]
+    bad[0][1] = bad[0][0]
+    with pytest.raises(enp.EnpError) as ei:
+        enp.Operator(dataclasses.replace(P, coords=bad))
+    assert ei.value.status == enp.ENP_ERR_INVALID_ARG

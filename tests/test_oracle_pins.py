@@ -343,7 +343,7 @@ def test_jvp_matches_central_differences(cfg):
     assert np.linalg.norm(jv - fd) / np.linalg.norm(jv) < 1e-7
 
 
-@pytest.mark.parametrize("cfg", ["mms2d_n3", "cube_n2_p2", "channel_n1"])
+@pytest.mark.parametrize("cfg", ["mms2d_n3", "cube_n2_p2", "cube_n3_p1", "channel_n1"])
 def test_assembled_jacobian_consistent(cfg):
     P = W.config(cfg)
     orc = oracle.Oracle(P, dirichlet=W.random_dirichlet(P, 2))
