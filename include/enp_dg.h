@@ -1,0 +1,164 @@
+/*
+ * enp_dg.h -- C ABI of the GB300 (sm_103a) discontinuous Galerkin operator for
+ * the electroneutral Nernst-Planck equations in charge-conservation form (CNP).
+ *
+ * The operator is the DG scheme of Sec. 3.3 (Eq. NPDG for the species
+ * c_1..c_{m-1}, Eq. chargeDG for the potential Phi; c_m is eliminated by
+ * Eq. substitution), on structured tensor-product quadrilateral (2D) and
+ * hexahedral (3D) meshes with a nodal Gauss-Lobatto basis of degree p and
+ * Gauss-Legendre quadrature with q = p + 2 points per direction (Sec. 4:
+ * "higher-order quadrature rules compared to the polynomial degree").
+ *
+ * Vector layout (every double/float vector argument): device memory, caller
+ * owned, contiguous, indexed [b][f][e][i]:
+ *   b  operating point, 0 <= b < batch (enp_disc_desc.batch);
+ *   f  field: 0 = Phi (charge-conservation rows), k = c_k for k = 1..m-1;
+ *   e  element, lexicographic with x fastest;
+ *   i  node, lexicographic with x fastest, (p+1)^dim per element.
+ * This is the block ordering [R_Phi; R_c1; ...; R_c(m-1)] of Sec. 4 (Eq. blockmatrix).
+ *
+ * Calls are asynchronous on the handle's CUDA stream unless stated. They return
+ * an enp_status; on failure enp_last_error() gives a message. No call throws,
+ * aborts or traps. Device pointers must be 8-byte aligned (4 for float).
+ * A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef ENP_DG_H
+#define ENP_DG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct enp_dg* enp_handle;
+
+typedef enum {
+  ENP_OK = 0,
+  ENP_ERR_INVALID_ARG = 1,   /* a null pointer, an out-of-range size or parameter */
+  ENP_ERR_CUDA = 2,          /* a CUDA runtime error (message in enp_last_error) */
+  ENP_ERR_OOM = 3,           /* device allocation failed */
+  ENP_ERR_NONFINITE = 4,     /* a NaN/Inf was found where the call checks for one */
+  ENP_ERR_NOT_CONVERGED = 5, /* an iterative solve stopped at its iteration limit */
+  ENP_ERR_TIMEOUT = 6,       /* a device-side loop hit its safety cap */
+  ENP_ERR_UNSUPPORTED = 7    /* a valid configuration this build does not implement */
+} enp_status;
+
+/* Boundary face tags (one byte per boundary face). The boundary classification of
+ * Sec. 2.1 (inlet, outlet, wall, electrode), plus DIRICHLET for manufactured
+ * solutions (Sec. 5.1: "all boundary conditions ... prescribed using the exact
+ * solutions"), imposed weakly in Nitsche form. */
+enum {
+  ENP_FACE_WALL = 1,       /* Eq. wall: no term */
+  ENP_FACE_INLET = 2,      /* Eq. inlet: + int (u.n) c_k^in v */
+  ENP_FACE_OUTLET = 3,     /* Eq. NPDG outlet term: + int (q_k.n) c_k v */
+  ENP_FACE_DIRICHLET = 4,  /* exterior state from enp_set_sources */
+  ENP_FACE_ELECTRODE0 = 5  /* electrode j = tag - 5 (j < 4), Butler-Volmer Eq. bv */
+};
+
+enum { ENP_VEL_CONSTANT = 0, ENP_VEL_PLATE = 1 };
+#define ENP_MAX_SPECIES 4
+
+/* Structured box mesh. Host arrays, read during enp_dg_create only.
+ * coords[a]: n_el[a]+1 strictly increasing vertex coordinates along axis a.
+ * face_tag[s]: boundary side s = 2a + (0 low, 1 high), one tag per face, faces
+ * numbered lexicographically over the remaining axes (lowest axis fastest). */
+typedef struct {
+  int dim;                          /* 2 or 3 */
+  int n_el[3];                      /* elements per axis (n_el[2] ignored in 2D) */
+  const double* coords[3];
+  const unsigned char* face_tag[6];
+} enp_mesh_desc;
+
+/* Physical parameters (Sec. 2). mu_k = D_k / RT (Eq. NE). F = RT = 1 gives the
+ * nondimensional form of Sec. 2.3 when concentrations are scaled by c^in.
+ * velocity_kind CONSTANT: u = (vel_params[0..2]).
+ * velocity_kind PLATE (Sec. 5.2): flow axis A = vel_params[0], normal axis
+ *   N = vel_params[1], wall at y0 = vel_params[2], height H = vel_params[3],
+ *   mean speed vel_params[4]: u_A = 6 u_avg s (H - s) / H^2, s = x_N - y0.
+ * Butler-Volmer (Eq. bv), with the reductant the solid electrode (ratio 1):
+ *   J_n = J_0 [exp(alpha1 n F/RT (phi_app_j - Phi)) - (c_o/c_ref)^gamma exp(-alpha2 n F/RT (phi_app_j - Phi))],
+ *   g_ox = J_n / (n F) (species row of the oxidant, if not c_m), g = z_ox J_n / n
+ *   (charge row). J_0 is constant, or with bv_J0_axis >= 0 the profile
+ *   3/5 J_0 [2 - ((t - w/2)/(w/2))^2], t = x_axis - lo, w = hi - lo (Sec. 5.2). */
+typedef struct {
+  int m;                            /* species, 2 <= m <= ENP_MAX_SPECIES; z[m-1] != 0 */
+  double z[ENP_MAX_SPECIES];
+  double D[ENP_MAX_SPECIES];
+  double c_in[ENP_MAX_SPECIES];
+  double F, RT;
+  int velocity_kind;
+  double vel_params[8];
+  int bv_oxidant;                   /* species index of the oxidant (0-based), -1: no reaction */
+  double bv_J0, bv_alpha1, bv_alpha2, bv_n, bv_gamma, bv_c_ref;
+  double bv_phi_app[4];             /* applied potential of electrodes 0..3 */
+  int bv_J0_axis;
+  double bv_J0_lo, bv_J0_hi;
+} enp_physics_desc;
+
+/* Discretisation: delta_p = C_IP p^2 / h (Eq. deltap) with h the element
+ * diagonal (mean of both elements on an interior face); the paper uses C_IP = 10. */
+typedef struct {
+  int p;          /* 1..4 in 3D, 1..3 in 2D */
+  int q;          /* Gauss points per direction; must be p + 2 */
+  double C_IP;
+  int batch;      /* operating points carried by every vector, >= 1 */
+} enp_disc_desc;
+
+/* Create an operator handle. Uploads the mesh, tags and basis tables, using
+ * stream (a cudaStream_t, may be 0) for every later call. Synchronises once.
+ * Errors: INVALID_ARG (bad descriptor), UNSUPPORTED (p, q, m or dim outside
+ * the compiled set), OOM, CUDA. *out is NULL on failure. */
+enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh,
+                         const enp_physics_desc* phys, const enp_disc_desc* disc,
+                         void* stream);
+enp_status enp_dg_destroy(enp_handle h);
+
+/* Sizes: DOFs per operating point (m * E * (p+1)^dim), fields, nodes and
+ * quadrature points per element, boundary faces. Any pointer may be NULL. */
+enp_status enp_dg_sizes(enp_handle h, long long* n_dof, int* n_fields, int* n_nodes,
+                        int* n_qpoints, int* n_bfaces);
+
+/* Replace the stream later calls run on (a cudaStream_t). */
+enp_status enp_set_stream(enp_handle h, void* stream);
+
+/* Optional problem data, copied into handle-owned device memory (NULL clears):
+ *   src [m][E][q^dim]: volume sources at the Gauss points (field 0: f of
+ *       Eq. chargeDG; field k: R_k of Eq. NPDG), subtracted as -int src v;
+ *   dir [m][NBF][q^(dim-1)]: exterior states (Phi, c_1..c_{m-1}) at the Gauss
+ *       points of every boundary face (side-major, face order as face_tag,
+ *       points lexicographic, lower axis fastest); read on DIRICHLET faces.
+ * Both are device pointers, read before the call returns. */
+enp_status enp_set_sources(enp_handle h, const double* src, const double* dir);
+
+/* Applied electrode potentials per operating point, host array [batch][4]
+ * (NULL: every operating point uses bv_phi_app). Copied. */
+enp_status enp_set_phi_app(enp_handle h, const double* phi_app);
+
+/* Physical coordinates of the volume Gauss points [E][q^dim][3] and of the
+ * boundary-face Gauss points [NBF][q^(dim-1)][3] (device pointers, either NULL). */
+enp_status enp_quadrature_points(enp_handle h, double* xq, double* xbq);
+
+/* r = R(u): the left-hand sides of Eq. NPDG (rows f = 1..m-1) and Eq. chargeDG
+ * (rows f = 0), tested with every basis function. u, r: [batch][m][E][Np]. */
+enp_status enp_residual(enp_handle h, const double* u, double* r);
+
+/* jv = J(u) v, the Gateaux derivative of R at u in direction v (Eq. blockmatrix),
+ * matrix-free (Sec. 4.3). d|x|/dx is taken as 0 at x = 0. */
+enp_status enp_jvp(enp_handle h, const double* u, const double* v, double* jv);
+
+/* The same in single precision (inner Krylov operator of the mixed-precision
+ * solve): u, v, jv are float vectors in the same layout. */
+enp_status enp_jvp_f32(enp_handle h, const float* u, const float* v, float* jv);
+
+/* jtw = J(u)^T w, the adjoint of enp_jvp, by element-local recomputation (no
+ * stored quadrature-point state). The paper has no adjoint; this is the
+ * transpose of Eq. blockmatrix. */
+enp_status enp_vjp(enp_handle h, const double* u, const double* w, double* jtw);
+
+/* Message of the last failed call on this handle ("" if none). The pointer is
+ * owned by the handle and valid until the next call on it. */
+const char* enp_last_error(enp_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENP_DG_H */

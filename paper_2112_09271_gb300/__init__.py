@@ -1,0 +1,285 @@
+"""Python binding of the GB300 CNP discontinuous Galerkin operator (libenp_dg.so).
+
+Argument marshalling only: every step of the operator, the preconditioner and
+the solvers runs in the library's CUDA kernels. PyTorch supplies device memory
+and streams. There is no fallback: if the shared library is missing or cannot
+be loaded, every entry point raises.
+
+The C ABI is declared in include/enp_dg.h; each method here has the name of the
+C function it calls, without the ``enp_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libenp_dg.so")
+SOURCES = ["enp_api.cu", "op_f64.cu", "op_f32.cu"]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC",
+              "--expt-relaxed-constexpr"]
+
+ENP_OK, ENP_ERR_INVALID_ARG, ENP_ERR_CUDA, ENP_ERR_OOM, ENP_ERR_NONFINITE = 0, 1, 2, 3, 4
+ENP_ERR_NOT_CONVERGED, ENP_ERR_TIMEOUT, ENP_ERR_UNSUPPORTED = 5, 6, 7
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NONFINITE", 5: "NOT_CONVERGED",
+           6: "TIMEOUT", 7: "UNSUPPORTED"}
+
+
+class EnpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (one object per source, in parallel)
+    and link libenp_dg.so in-tree. Returns the library path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_CSRC, s) for s in SOURCES]
+    deps = srcs + [os.path.join(_CSRC, f) for f in os.listdir(_CSRC)
+                   if f.endswith((".cuh", ".h"))]
+    deps.append(os.path.join(_ROOT, "include", "enp_dg.h"))
+    newest = max(os.path.getmtime(d) for d in deps)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, os.path.basename(src) + ".o")
+        cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+        if verbose and r.stderr:
+            print(r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc, ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ----------------------------------------------------------------- ctypes ABI
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_el", ctypes.c_int * 3),
+                ("coords", ctypes.c_void_p * 3), ("face_tag", ctypes.c_void_p * 6)]
+
+
+class PhysicsDesc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("z", ctypes.c_double * 4), ("D", ctypes.c_double * 4),
+                ("c_in", ctypes.c_double * 4), ("F", ctypes.c_double), ("RT", ctypes.c_double),
+                ("velocity_kind", ctypes.c_int), ("vel_params", ctypes.c_double * 8),
+                ("bv_oxidant", ctypes.c_int), ("bv_J0", ctypes.c_double),
+                ("bv_alpha1", ctypes.c_double), ("bv_alpha2", ctypes.c_double),
+                ("bv_n", ctypes.c_double), ("bv_gamma", ctypes.c_double),
+                ("bv_c_ref", ctypes.c_double), ("bv_phi_app", ctypes.c_double * 4),
+                ("bv_J0_axis", ctypes.c_int), ("bv_J0_lo", ctypes.c_double),
+                ("bv_J0_hi", ctypes.c_double)]
+
+
+class DiscDesc(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int), ("C_IP", ctypes.c_double),
+                ("batch", ctypes.c_int)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported function declared in include/enp_dg.h
+_V, _I, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+_PROTOS = [
+    ("enp_dg_create", _I, [ctypes.POINTER(_V), ctypes.POINTER(MeshDesc),
+                           ctypes.POINTER(PhysicsDesc), ctypes.POINTER(DiscDesc), _V]),
+    ("enp_dg_destroy", _I, [_V]),
+    ("enp_dg_sizes", _I, [_V, ctypes.POINTER(_LL), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                          ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("enp_set_stream", _I, [_V, _V]),
+    ("enp_set_sources", _I, [_V, _V, _V]),
+    ("enp_set_phi_app", _I, [_V, _V]),
+    ("enp_quadrature_points", _I, [_V, _V, _V]),
+    ("enp_residual", _I, [_V, _V, _V]),
+    ("enp_jvp", _I, [_V, _V, _V, _V]),
+    ("enp_jvp_f32", _I, [_V, _V, _V, _V]),
+    ("enp_vjp", _I, [_V, _V, _V, _V]),
+    ("enp_last_error", ctypes.c_char_p, [_V]),
+]
+
+
+def load(path: str | None = None):
+    """Load libenp_dg.so (built in-tree by ``build()``) and declare its prototypes."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise EnpError(ENP_ERR_UNSUPPORTED,
+                       f"{path} is missing: call paper_2112_09271_gb300.build() first")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _PROTOS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_names():
+    return [p[0] for p in _PROTOS]
+
+
+def _dptr(t, dtype):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Operator:
+    """One CNP DG operator (a handle of the C library).
+
+    ``prob`` is any object with the attributes of ``workloads.Problem`` (dim,
+    n_el, coords, tags, m, z, D, c_in, F, RT, vel_kind, vel_params, bv_*, p, q,
+    C_IP). Vectors are CUDA tensors [batch * m * E * Np] in the library layout.
+    """
+
+    def __init__(self, prob, batch: int = 1, stream=None):
+        import torch
+        lib = load()
+        self.prob = prob
+        self.batch = batch
+        dim = prob.dim
+        self._coords = [np.ascontiguousarray(prob.coords[a], dtype=np.float64) for a in range(dim)]
+        self._tags = [np.ascontiguousarray(t, dtype=np.uint8) for t in prob.tags]
+        mesh = MeshDesc()
+        mesh.dim = dim
+        for a in range(3):
+            mesh.n_el[a] = int(prob.n_el[a]) if a < dim else 1
+            mesh.coords[a] = self._coords[a].ctypes.data if a < dim else None
+        for s in range(6):
+            mesh.face_tag[s] = self._tags[s].ctypes.data if s < 2 * dim else None
+        ph = PhysicsDesc()
+        ph.m = prob.m
+        for k in range(4):
+            ph.z[k] = prob.z[k] if k < prob.m else 0.0
+            ph.D[k] = prob.D[k] if k < prob.m else 0.0
+            ph.c_in[k] = prob.c_in[k] if k < prob.m else 0.0
+        ph.F, ph.RT = prob.F, prob.RT
+        ph.velocity_kind = prob.vel_kind
+        for i in range(8):
+            ph.vel_params[i] = prob.vel_params[i] if i < len(prob.vel_params) else 0.0
+        ph.bv_oxidant = prob.bv_oxidant
+        ph.bv_J0, ph.bv_alpha1, ph.bv_alpha2 = prob.bv_J0, prob.bv_alpha1, prob.bv_alpha2
+        ph.bv_n, ph.bv_gamma, ph.bv_c_ref = prob.bv_n, prob.bv_gamma, prob.bv_c_ref
+        for j in range(4):
+            ph.bv_phi_app[j] = prob.bv_phi_app[j]
+        ph.bv_J0_axis, ph.bv_J0_lo, ph.bv_J0_hi = prob.bv_J0_axis, prob.bv_J0_lo, prob.bv_J0_hi
+        disc = DiscDesc(prob.p, prob.q, prob.C_IP, batch)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = lib.enp_dg_create(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(ph),
+                               ctypes.byref(disc), ctypes.c_void_p(stream.cuda_stream))
+        if st != ENP_OK:
+            raise EnpError(st, "enp_dg_create failed")
+        self.h = h
+        self._lib = lib
+        n = ctypes.c_longlong(); nf = ctypes.c_int(); nn = ctypes.c_int(); nq = ctypes.c_int()
+        nb = ctypes.c_int()
+        self._check(lib.enp_dg_sizes(h, ctypes.byref(n), ctypes.byref(nf), ctypes.byref(nn),
+                                     ctypes.byref(nq), ctypes.byref(nb)))
+        self.n_dof, self.n_fields, self.n_nodes = n.value, nf.value, nn.value
+        self.n_qpoints, self.n_bfaces = nq.value, nb.value
+        self.n = self.n_dof * batch
+
+    def _check(self, st):
+        if st != ENP_OK:
+            msg = self._lib.enp_last_error(self.h)
+            raise EnpError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.enp_dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _new(self, like_dtype):
+        import torch
+        return torch.empty(self.n, dtype=like_dtype, device="cuda")
+
+    def set_sources(self, src=None, dirichlet=None):
+        import torch
+        s = _dptr(src, torch.float64) if src is not None else None
+        d = _dptr(dirichlet, torch.float64) if dirichlet is not None else None
+        self._check(self._lib.enp_set_sources(self.h, s, d))
+
+    def set_phi_app(self, phi_app):
+        a = None if phi_app is None else np.ascontiguousarray(phi_app, dtype=np.float64)
+        if a is not None and a.size != 4 * self.batch:
+            raise ValueError("phi_app must have batch x 4 entries")
+        self._phi = a
+        self._check(self._lib.enp_set_phi_app(self.h, None if a is None else a.ctypes.data))
+
+    def quadrature_points(self):
+        import torch
+        P = self.prob
+        xq = torch.empty((P.E, self.n_qpoints, 3), dtype=torch.float64, device="cuda")
+        xb = torch.empty((self.n_bfaces, P.q ** (P.dim - 1), 3), dtype=torch.float64,
+                         device="cuda")
+        self._check(self._lib.enp_quadrature_points(self.h, ctypes.c_void_p(xq.data_ptr()),
+                                                    ctypes.c_void_p(xb.data_ptr())))
+        return xq, xb
+
+    def residual(self, u, out=None):
+        import torch
+        out = self._new(torch.float64) if out is None else out
+        self._check(self._lib.enp_residual(self.h, _dptr(u, torch.float64),
+                                           _dptr(out, torch.float64)))
+        return out
+
+    def jvp(self, u, v, out=None):
+        import torch
+        out = self._new(torch.float64) if out is None else out
+        self._check(self._lib.enp_jvp(self.h, _dptr(u, torch.float64), _dptr(v, torch.float64),
+                                      _dptr(out, torch.float64)))
+        return out
+
+    def jvp_f32(self, u, v, out=None):
+        import torch
+        out = self._new(torch.float32) if out is None else out
+        self._check(self._lib.enp_jvp_f32(self.h, _dptr(u, torch.float32),
+                                          _dptr(v, torch.float32), _dptr(out, torch.float32)))
+        return out
+
+    def vjp(self, u, w, out=None):
+        import torch
+        out = self._new(torch.float64) if out is None else out
+        self._check(self._lib.enp_vjp(self.h, _dptr(u, torch.float64), _dptr(w, torch.float64),
+                                      _dptr(out, torch.float64)))
+        return out

@@ -1,0 +1,33 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+#include "enp_common.cuh"
+
+namespace enp {
+
+// Launch the operator kernel for (dim, p, NF) chosen at run time.
+// mode: 0 residual, 1 J v, 2 J^T w. Returns cudaErrorInvalidConfiguration if the
+// shape is not compiled.
+template <class R>
+cudaError_t launch_op(int mode, const OpParams& prm, const Tables* tabs, const R* u, const R* v,
+                      R* out, int batch, cudaStream_t stream);
+
+bool shape_supported(int dim, int p, int nf);
+
+}  // namespace enp
+
+struct enp_dg {
+  enp::OpParams prm{};
+  enp::Tables htab{};
+  enp::Tables* d_tab = nullptr;
+  double* d_xv[3] = {nullptr, nullptr, nullptr};
+  uint8_t* d_btag = nullptr;
+  double* d_src = nullptr;
+  double* d_dir = nullptr;
+  double* d_phiapp = nullptr;
+  int batch = 1;
+  long long n_dof = 0;           // per operating point
+  cudaStream_t stream = nullptr;
+  std::string err;
+};

@@ -1,0 +1,67 @@
+// Run-time dispatch from (dim, p, fields, mode) to a compiled operator kernel.
+#pragma once
+#include "enp_internal.h"
+#include "enp_operator.cuh"
+
+namespace enp {
+
+template <int DIM, int P, int NF, int MODE, class R>
+static cudaError_t launch_one(const OpParams& prm, const Tables* tabs, const R* u, const R* v,
+                              R* out, int batch, cudaStream_t stream) {
+  using M = WarpSmem<DIM, P, NF, MODE>;
+  constexpr size_t per_warp = (size_t)M::total * sizeof(R);
+  constexpr int WPB = per_warp * 4 <= 96 * 1024 ? 4 : (per_warp * 2 <= 110 * 1024 ? 2 : 1);
+  const size_t smem = ((size_t)TabSmem<P>::total + (size_t)WPB * M::total) * sizeof(R);
+  auto kern = op_kernel<DIM, P, NF, MODE, WPB, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((prm.E + WPB - 1) / WPB, batch);
+  kern<<<grid, WPB * 32, smem, stream>>>(prm, tabs, u, v, out);
+  return cudaGetLastError();
+}
+
+template <int DIM, int P, int NF, class R>
+static cudaError_t launch_mode(int mode, const OpParams& prm, const Tables* t, const R* u,
+                               const R* v, R* out, int batch, cudaStream_t s) {
+  switch (mode) {
+    case kResidual: return launch_one<DIM, P, NF, kResidual, R>(prm, t, u, v, out, batch, s);
+    case kJvp: return launch_one<DIM, P, NF, kJvp, R>(prm, t, u, v, out, batch, s);
+    case kVjp: return launch_one<DIM, P, NF, kVjp, R>(prm, t, u, v, out, batch, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int DIM, int P, class R>
+static cudaError_t launch_nf(int mode, const OpParams& prm, const Tables* t, const R* u,
+                             const R* v, R* out, int batch, cudaStream_t s) {
+  if (prm.NF == 2) return launch_mode<DIM, P, 2, R>(mode, prm, t, u, v, out, batch, s);
+  if (prm.NF == 3) return launch_mode<DIM, P, 3, R>(mode, prm, t, u, v, out, batch, s);
+  return cudaErrorInvalidConfiguration;
+}
+
+template <class R>
+cudaError_t launch_op(int mode, const OpParams& prm, const Tables* t, const R* u, const R* v,
+                      R* out, int batch, cudaStream_t s) {
+  if (prm.dim == 3) {
+    switch (prm.p) {
+      case 1: return launch_nf<3, 1, R>(mode, prm, t, u, v, out, batch, s);
+      case 2: return launch_nf<3, 2, R>(mode, prm, t, u, v, out, batch, s);
+      case 3: return launch_nf<3, 3, R>(mode, prm, t, u, v, out, batch, s);
+      case 4: return launch_nf<3, 4, R>(mode, prm, t, u, v, out, batch, s);
+    }
+  } else if (prm.dim == 2) {
+    switch (prm.p) {
+      case 1: return launch_nf<2, 1, R>(mode, prm, t, u, v, out, batch, s);
+      case 2: return launch_nf<2, 2, R>(mode, prm, t, u, v, out, batch, s);
+      case 3: return launch_nf<2, 3, R>(mode, prm, t, u, v, out, batch, s);
+    }
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace enp

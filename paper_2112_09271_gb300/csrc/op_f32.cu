@@ -1,0 +1,5 @@
+// FP32 instantiations of the operator kernel (inner Krylov operator of the
+// mixed-precision solve).
+#include "enp_op_dispatch.cuh"
+template cudaError_t enp::launch_op<float>(int, const OpParams&, const Tables*, const float*,
+                                           const float*, float*, int, cudaStream_t);

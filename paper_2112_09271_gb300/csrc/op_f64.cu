@@ -1,0 +1,4 @@
+// FP64 instantiations of the operator kernel: R(u), J(u)v and J(u)^T w.
+#include "enp_op_dispatch.cuh"
+template cudaError_t enp::launch_op<double>(int, const OpParams&, const Tables*, const double*,
+                                            const double*, double*, int, cudaStream_t);
