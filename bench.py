@@ -1,0 +1,383 @@
+"""Benchmark of the CNP DG operator hot path on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl native|reference]
+
+A step is one pass of the operator rows over one synthetic state of the
+workload (inputs resident in HBM): R(u), J(u)v and J(u)^T w in FP64 and the
+single-precision J(u)v of the mixed-precision inner solve. `value` counts
+degrees of freedom times operator applications per second (GDOF/s), summed over
+ranks. Each step is timed with CUDA events on the launching stream; between
+steps a 512 MB buffer is written to flush the 129 MB L2 (outside the events).
+
+Extra keys: per-operator throughput (`ops`), the roofline of the dominant kernel
+(`roofline`), the CPU oracle on a bounded sample (`cpu_baseline`), the same
+metric end to end through the C ABI with host buffers (`e2e`), SM clocks sampled
+during the timed region (`clocks`) and the number of kernel launches (`gpu_launches`).
+
+`--impl reference` times the CPU oracle (the plain FP64 reference
+implementation of the same operator) on a bounded sample of the same workload,
+on the host cores; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ENP DG Jv GDOF/s at p=3 hex, FP64 vs mixed; % of HBM roofline; solve time"
+DEFAULT_WORKLOAD = "channel64_p3"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 issue rate of GB300: 2 FMA per clock per SM (measured 1.20 TFLOP/s with an
+# FMA loop at 1.99 GHz; 152 SMs x 2 x 2 flop x 2.07 GHz = 1.26 TFLOP/s nominal).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
+# the hash of the operator source it was taken from (stale -> reported null).
+TRAFFIC = {
+    ("21a4a7a60dc3", "jvp_f64", "channel64_p3"): 134.96e6,
+}
+
+
+def _kernel_hash():
+    h = hashlib.sha1()
+    for f in ("enp_operator.cuh", "enp_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2112_09271_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def contraction_flops(dim, p, nf, mode):
+    """Floating-point operations (2 per multiply-add) of the sum-factorised
+    contractions of one element for one operator application (mode 'res', 'jvp'
+    or 'vjp'), all faces counted as interior. Pointwise physics is excluded."""
+    n, q = p + 1, p + 2
+    if dim == 3:
+        interp = q * n ** 3 + q * q * n * n + q ** 3 * n + 3 * q ** 4
+        trace = n ** 3 + 2 * (q * n * n + q * q * n)
+        ftest = 2 * (q * q * n + q * n * n) + n ** 3
+    else:
+        interp = q * n * n + q * q * n + 2 * q ** 3
+        trace = n * n + 2 * q * n
+        ftest = 2 * q * n + n * n
+    nv = 1 if mode == "res" else 2
+    vol = nf * (nv * interp + interp)
+    faces = 2 * dim * nf * (2 * nv * trace + ftest)
+    return 2 * (vol + faces)
+
+
+def algorithmic_bytes_per_dof(mode, word):
+    """Each vector read or written once (Sec. 8(d) of the design): R reads u and
+    writes r; J v and J^T w read u and v (or w) and write the result."""
+    return {"res": 2, "jvp": 3, "vjp": 3}[mode] * word
+
+
+def read_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, path):
+        self.path = path
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(prob, budget_s=12.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload's elements: R(u) and J(u)v rows of randomly chosen elements, in
+    batches that grow until about budget_s seconds of CPU time are spent."""
+    import oracle
+    import workloads as W
+    orc = oracle.Oracle(prob)
+    u, v = W.random_state(prob, 2), W.random_vector(prob, 3)
+    rng = np.random.default_rng(0)
+    n_el = min(64, prob.E)
+    t_ops, dofs, n_total = 0.0, 0, 0
+    while t_ops < budget_s:
+        el = rng.choice(prob.E, n_el, replace=False)
+        t0 = time.perf_counter()
+        orc.residual(u, elems=el)
+        orc.jvp(u, v, elems=el)
+        dt = time.perf_counter() - t0
+        t_ops += dt
+        n_total += n_el
+        dofs += 2 * n_el * prob.n_fields * prob.Np
+        want = n_el * (budget_s - t_ops) / max(dt, 1e-4)
+        n_el = int(max(1, min(prob.E, want, 8 * n_el)))
+    return {"value": dofs / t_ops / 1e9, "unit": "GDOF/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"R(u) and J(u)v rows of {n_total} randomly chosen elements (with "
+                      f"repeats) of {prob.name} ({prob.E} elements), {t_ops:.1f} s of CPU time"}
+
+
+def run_reference(args, rank, world):
+    import workloads as W
+    if rank != 0:
+        return
+    prob = W.config(args.workload)
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(prob, budget_s=budget / 4)
+    vals, t0 = [], time.perf_counter()
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(prob, budget_s=budget)
+        vals.append(cb["value"])
+    wall = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": prob.name, "n_dof": prob.n_dof, "p": prob.p,
+                       "elements": prob.E, "fields": prob.n_fields, "l2": "sampled rows (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_2112_09271_gb300 as enp
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    enp.build()
+    prob = W.config(args.workload)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    op = enp.Operator(prob, stream=stream)
+    n = op.n
+    u = torch.tensor(W.random_state(prob, 2), device="cuda")
+    v = torch.tensor(W.random_vector(prob, 3), device="cuda")
+    w = torch.tensor(W.random_vector(prob, 4), device="cuda")
+    u32, v32 = u.float(), v.float()
+    r, jv, jtw = (torch.empty_like(u) for _ in range(3))
+    jv32 = torch.empty_like(u32)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ops = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32"]
+    launches_per_step = len(ops)
+
+    def run_op(name):
+        if name == "residual_f64":
+            op.residual(u, out=r)
+        elif name == "jvp_f64":
+            op.jvp(u, v, out=jv)
+        elif name == "vjp_f64":
+            op.vjp(u, w, out=jtw)
+        else:
+            op.jvp_f32(u32, v32, out=jv32)
+
+    ev = {nm: [torch.cuda.Event(enable_timing=True) for _ in range(2)] for nm in ops}
+    t_ops = {nm: 0.0 for nm in ops}
+
+    def step(timed):
+        for nm in ops:
+            if timed:
+                ev[nm][0].record(stream)
+            run_op(nm)
+            if timed:
+                ev[nm][1].record(stream)
+
+    for _ in range(args.warmup):
+        step(False)
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    import tempfile
+    cdir = os.path.join(ROOT, "gpurun_out")
+    sampler = ClockSampler(local, os.path.join(cdir if os.path.isdir(cdir) else tempfile.gettempdir(),
+                                               f"clocks_rank{rank}.csv"))
+    sampler.start()
+    time.sleep(0.3)
+    total_ms = 0.0
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        s0.record(stream)
+        step(True)
+        s1.record(stream)
+        s1.synchronize()
+        total_ms += s0.elapsed_time(s1)
+        for nm in ops:
+            t_ops[nm] += ev[nm][0].elapsed_time(ev[nm][1])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    units = n * len(ops)
+    value = world * units / (ms_step * 1e-3) / 1e9
+
+    per_op = {nm: {"ms": t_ops[nm] / args.steps,
+                   "GDOF_s": n / (t_ops[nm] / args.steps * 1e-3) / 1e9} for nm in ops}
+    # roofline of the dominant kernel (the FP64 operator: ALU-bound on GB300)
+    dom = max(("residual_f64", "jvp_f64", "vjp_f64"), key=lambda k: t_ops[k])
+    if t_ops["jvp_f64"] >= 0.95 * t_ops[dom]:
+        dom = "jvp_f64"  # the metric's operator, when within 5 % of the slowest
+    mode = {"residual_f64": "res", "jvp_f64": "jvp", "vjp_f64": "vjp"}[dom]
+    fl = contraction_flops(prob.dim, prob.p, prob.n_fields, mode) * prob.E * op.batch
+    dom_s = t_ops[dom] / args.steps * 1e-3
+    achieved = fl / dom_s / 1e12
+    hbm, hbm_kind = read_peaks()
+    hbm_bytes = algorithmic_bytes_per_dof(mode, 8) * n
+    kh = _kernel_hash()
+    traffic = TRAFFIC.get((kh, dom, prob.name))
+    roof = {"bound": "alu", "kernel": f"op_kernel<{prob.dim}D,p={prob.p},NF={prob.n_fields},"
+                                      f"{mode},double>",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (measured FMA loop 1.20)",
+            "traffic": traffic,
+            "hbm_achieved_GBs": hbm_bytes / dom_s / 1e9, "hbm_peak_GBs": hbm,
+            "hbm_frac": hbm_bytes / dom_s / 1e9 / hbm, "hbm_peak_kind": hbm_kind,
+            "flops_per_launch": fl, "algorithmic_bytes_per_launch": hbm_bytes}
+    f32_fl = contraction_flops(prob.dim, prob.p, prob.n_fields, "jvp") * prob.E
+    f32_s = t_ops["jvp_f32"] / args.steps * 1e-3
+    per_op["jvp_f32"]["fp32_TFLOPs"] = f32_fl / f32_s / 1e12
+    per_op["jvp_f32"]["fp32_frac"] = f32_fl / f32_s / 1e12 / FP32_PEAK_TFLOPS
+    per_op["jvp_f32"]["hbm_frac"] = algorithmic_bytes_per_dof("jvp", 4) * n / f32_s / 1e9 / hbm
+
+    # end to end through the C ABI with host buffers: H2D of u, v, w (pinned),
+    # the operators, D2H of the results, every step
+    hu, hv, hw = (x.cpu().pin_memory() for x in (u, v, w))
+    hr, hj, ht = (torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3))
+    hj32 = torch.empty(n, dtype=torch.float32).pin_memory()
+    du, dv, dw = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
+
+    def e2e_step():
+        du.copy_(hu, non_blocking=True); dv.copy_(hv, non_blocking=True)
+        dw.copy_(hw, non_blocking=True)
+        op.residual(du, out=r); op.jvp(du, dv, out=jv); op.vjp(du, dw, out=jtw)
+        du32, dv32 = du.float(), dv.float()
+        op.jvp_f32(du32, dv32, out=jv32)
+        hr.copy_(r, non_blocking=True); hj.copy_(jv, non_blocking=True)
+        ht.copy_(jtw, non_blocking=True); hj32.copy_(jv32, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_steps = max(3, args.steps // 2)
+    s0.record(stream)
+    for _ in range(e_steps):
+        e2e_step()
+    s1.record(stream)
+    s1.synchronize()
+    e2e_ms = s0.elapsed_time(s1) / e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
+           "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 3 * n * 8 + n * 4,
+           "ms_per_step": e2e_ms}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(prob)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": prob.name, "elements": prob.E, "p": prob.p,
+                           "fields": prob.n_fields, "n_dof": prob.n_dof,
+                           "n_dof_incl_cm": prob.n_dof // prob.n_fields * (prob.n_fields + 1),
+                           "step": "R f64 + J v f64 + J^T w f64 + J v f32",
+                           "l2": "flushed between steps (512 MB write)"},
+                "ops": per_op, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+                "kernel_hash": kh}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
