@@ -154,6 +154,88 @@ enp_status enp_jvp_f32(enp_handle h, const float* u, const float* v, float* jv);
  * transpose of Eq. blockmatrix. */
 enp_status enp_vjp(enp_handle h, const double* u, const double* w, double* jtw);
 
+/* c_m = -(1/z_m) sum_{k<m} z_k c_k at every node (Eq. substitution): the
+ * eliminated concentration. u: [batch][m][E][Np]; cm: [batch][E][Np]. */
+enp_status enp_recover_cm(enp_handle h, const double* u, double* cm);
+
+/* out[b] = <x_b, y_b> for every operating point b (host array of batch
+ * doubles). Reduced on the device in a fixed order (warp shuffles, one partial
+ * per thread block, then one block), so the result does not depend on timing.
+ * Synchronises the stream. */
+enp_status enp_inner_product(enp_handle h, const double* x, const double* y, double* out);
+
+/* The element-diagonal blocks of J(u): for every element K, the derivative of
+ * K's rows with respect to K's own unknowns (volume terms and K's side of every
+ * face term, all fields coupled). The "element-wise Jacobi" of Sec. 4.2, which
+ * ignores inter-element couplings. blocks: device [batch][E][nb][nb] row-major,
+ * nb = m * Np, row/column index f * Np + i. */
+enp_status enp_block_diagonal(enp_handle h, const double* u, double* blocks);
+
+/* Assemble and invert the element-diagonal blocks of J(u) (Gauss-Jordan with
+ * partial pivoting; FP64 arithmetic for storage 0, FP32 otherwise) and keep
+ * the inverses in handle-owned memory, stored as 0 = FP64, 1 = FP32, 2 = BF16.
+ * Synchronises. Errors: NONFINITE if a block is singular or not finite. */
+enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage);
+
+/* y = P^{-1} x with P the block diagonal of the last setup. x, y: [batch][m][E][Np]. */
+enp_status enp_block_jacobi_apply(enp_handle h, const double* x, double* y);
+
+typedef struct {
+  int restart;   /* Krylov vectors per cycle (FGMRES(restart)) */
+  int max_it;    /* total iterations */
+  double rtol;   /* stop when ||b - A x|| <= max(rtol ||b||, atol) */
+  double atol;
+} enp_krylov_opts;
+
+typedef struct {
+  int iterations;
+  int converged;
+  double initial_norm;       /* largest ||b - A x0|| over operating points */
+  double residual_norm;      /* largest final ||b - A x|| */
+  double relative_residual;  /* largest final ||b - A x|| / ||b|| */
+} enp_krylov_stats;
+
+/* Solve J(u_lin) x = b by flexible GMRES (the outer solver of Sec. 4.3, which
+ * tolerates a preconditioner that varies between iterations), right-
+ * preconditioned with the block-Jacobi inverse of the last setup (identity if
+ * none), classical Gram-Schmidt applied twice. x holds the initial guess on
+ * entry. Every operating point of the batch is solved independently. stats is
+ * a host pointer (may be NULL); the call synchronises.
+ * Errors: NOT_CONVERGED (x holds the last iterate), NONFINITE, OOM, CUDA. */
+enp_status enp_fgmres_solve(enp_handle h, const double* u_lin, const double* b, double* x,
+                            const enp_krylov_opts* opts, enp_krylov_stats* stats);
+
+/* The same with the single-precision operator and Krylov vectors (float
+ * u_lin, b, x): the inner solve of the mixed-precision Newton method. */
+enp_status enp_fgmres_solve_f32(enp_handle h, const float* u_lin, const float* b, float* x,
+                                const enp_krylov_opts* opts, enp_krylov_stats* stats);
+
+typedef struct {
+  int max_it;            /* Newton iterations */
+  double rtol, atol;     /* stop when ||R(u)|| <= max(rtol ||R(u0)||, atol) */
+  double armijo_c;       /* sufficient decrease: ||R(u + lam du)|| <= (1 - c lam) ||R(u)|| */
+  int max_backtracks;    /* halvings of lam per iteration */
+  int bj_storage;        /* block-Jacobi storage: 0 FP64, 1 FP32, 2 BF16 */
+  int mixed;             /* 1: inner FGMRES with the FP32 operator and vectors */
+  enp_krylov_opts krylov;
+} enp_newton_opts;
+
+typedef struct {
+  int iterations;
+  int krylov_iterations;
+  int converged;
+  double initial_norm;
+  double residual_norm;
+  double history[64];    /* ||R|| after each iteration (largest over operating points) */
+} enp_newton_stats;
+
+/* Newton's method with backtracking line search (Sec. 4) on R(u) = 0, in
+ * place on u (device, [batch][m][E][Np]). Each iteration rebuilds the
+ * block-Jacobi preconditioner at u and solves J du = -R with FGMRES to
+ * opts->krylov.rtol. Synchronises. Errors: NOT_CONVERGED, NONFINITE, OOM, CUDA. */
+enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* opts,
+                            enp_newton_stats* stats);
+
 /* Message of the last failed call on this handle ("" if none). The pointer is
  * owned by the handle and valid until the next call on it. */
 const char* enp_last_error(enp_handle h);

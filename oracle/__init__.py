@@ -197,6 +197,32 @@ class Oracle:
         self._lib.oracle_node_points(self.h, _ptr(xn))
         return xn
 
+    def block_diagonal(self, u):
+        """The element-diagonal blocks of the assembled J(u): [E, nb, nb] with
+        row/column index f * Np + i (the "element-wise Jacobi" of Sec. 4.2)."""
+        P = self.prob
+        J = self.jacobian(u).tocsr()
+        nb = P.n_fields * P.Np
+        out = np.zeros((P.E, nb, nb))
+        loc = np.arange(nb)
+        f, i = loc // P.Np, loc % P.Np
+        for e in range(P.E):
+            g = f * P.E * P.Np + e * P.Np + i
+            out[e] = J[g][:, g].toarray()
+        return out
+
+    def block_jacobi_apply(self, blocks, x):
+        """y_e = B_e^{-1} x_e for every element (dense LU solves)."""
+        P = self.prob
+        xe = x.reshape(P.n_fields, P.E, P.Np).transpose(1, 0, 2).reshape(P.E, -1)
+        ye = np.linalg.solve(blocks, xe[..., None])[..., 0]
+        return ye.reshape(P.E, P.n_fields, P.Np).transpose(1, 0, 2).reshape(-1)
+
+    def linear_solve(self, u, b):
+        """x with J(u) x = b, by a sparse direct solve (SuperLU)."""
+        import scipy.sparse.linalg as spla
+        return spla.spsolve(self.jacobian(u).tocsc(), np.asarray(b, dtype=np.float64))
+
     def newton_solve(self, u0, rtol=1e-10, max_it=30, c_armijo=1e-4):
         """Newton's method with a backtracking line search on ||R||, each linear
         system solved directly (sparse LU). Small meshes only."""
@@ -220,3 +246,13 @@ class Oracle:
             u, r = ut, rt
             hist.append(np.linalg.norm(r))
         return u, hist
+
+
+def recover_cm(prob, u):
+    """The eliminated concentration c_m = -(1/z_m) sum_{k<m} z_k c_k
+    (Eq. substitution), node by node: [E * Np]."""
+    uu = np.asarray(u, dtype=np.float64).reshape(prob.n_fields, prob.E * prob.Np)
+    s = np.zeros(prob.E * prob.Np)
+    for k in range(prob.m - 1):
+        s = s + prob.z[k] * uu[k + 1]
+    return -s / prob.z[prob.m - 1]

@@ -22,7 +22,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libenp_dg.so")
-SOURCES = ["enp_api.cu", "op_f64.cu", "op_f32.cu"]
+SOURCES = ["enp_api.cu", "op_f64.cu", "op_f32.cu", "enp_solver.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC",
               "--expt-relaxed-constexpr"]
@@ -102,6 +102,31 @@ class DiscDesc(ctypes.Structure):
                 ("batch", ctypes.c_int)]
 
 
+class KrylovOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_it", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double)]
+
+
+class KrylovStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("initial_norm", ctypes.c_double), ("residual_norm", ctypes.c_double),
+                ("relative_residual", ctypes.c_double)]
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("max_it", ctypes.c_int), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("armijo_c", ctypes.c_double), ("max_backtracks", ctypes.c_int),
+                ("bj_storage", ctypes.c_int), ("mixed", ctypes.c_int), ("krylov", KrylovOpts)]
+
+
+class NewtonStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
+                ("converged", ctypes.c_int), ("initial_norm", ctypes.c_double),
+                ("residual_norm", ctypes.c_double), ("history", ctypes.c_double * 64)]
+
+
+BJ_F64, BJ_F32, BJ_BF16 = 0, 1, 2
+
 _lib = None
 
 # (name, restype, argtypes) of every exported function declared in include/enp_dg.h
@@ -120,6 +145,14 @@ _PROTOS = [
     ("enp_jvp", _I, [_V, _V, _V, _V]),
     ("enp_jvp_f32", _I, [_V, _V, _V, _V]),
     ("enp_vjp", _I, [_V, _V, _V, _V]),
+    ("enp_recover_cm", _I, [_V, _V, _V]),
+    ("enp_inner_product", _I, [_V, _V, _V, _V]),
+    ("enp_block_diagonal", _I, [_V, _V, _V]),
+    ("enp_block_jacobi_setup", _I, [_V, _V, _I]),
+    ("enp_block_jacobi_apply", _I, [_V, _V, _V]),
+    ("enp_fgmres_solve", _I, [_V, _V, _V, _V, _V, _V]),
+    ("enp_fgmres_solve_f32", _I, [_V, _V, _V, _V, _V, _V]),
+    ("enp_newton_solve", _I, [_V, _V, _V, _V]),
     ("enp_last_error", ctypes.c_char_p, [_V]),
 ]
 
@@ -275,6 +308,76 @@ class Operator:
         out = self._new(torch.float32) if out is None else out
         self._check(self._lib.enp_jvp_f32(self.h, _dptr(u, torch.float32),
                                           _dptr(v, torch.float32), _dptr(out, torch.float32)))
+        return out
+
+    def recover_cm(self, u, out=None):
+        import torch
+        P = self.prob
+        out = torch.empty(self.batch * P.E * self.n_nodes, dtype=torch.float64,
+                          device="cuda") if out is None else out
+        self._check(self._lib.enp_recover_cm(self.h, _dptr(u, torch.float64),
+                                             _dptr(out, torch.float64)))
+        return out
+
+    def inner_product(self, x, y):
+        import torch
+        out = np.zeros(self.batch)
+        self._check(self._lib.enp_inner_product(self.h, _dptr(x, torch.float64),
+                                                _dptr(y, torch.float64),
+                                                ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def block_diagonal(self, u, out=None):
+        import torch
+        nb = self.n_fields * self.n_nodes
+        out = torch.empty(self.batch * self.prob.E * nb * nb, dtype=torch.float64,
+                          device="cuda") if out is None else out
+        self._check(self._lib.enp_block_diagonal(self.h, _dptr(u, torch.float64),
+                                                 _dptr(out, torch.float64)))
+        return out
+
+    def block_jacobi_setup(self, u, storage=BJ_F64):
+        import torch
+        self._check(self._lib.enp_block_jacobi_setup(self.h, _dptr(u, torch.float64),
+                                                     int(storage)))
+
+    def block_jacobi_apply(self, x, out=None):
+        import torch
+        out = self._new(torch.float64) if out is None else out
+        self._check(self._lib.enp_block_jacobi_apply(self.h, _dptr(x, torch.float64),
+                                                     _dptr(out, torch.float64)))
+        return out
+
+    def fgmres_solve(self, u_lin, b, x, restart=30, max_it=300, rtol=1e-8, atol=0.0,
+                     raise_on_fail=True):
+        """Solve J(u_lin) x = b in place on x; returns the stats as a dict."""
+        import torch
+        f32 = u_lin.dtype == torch.float32
+        dt = torch.float32 if f32 else torch.float64
+        o = KrylovOpts(restart, max_it, rtol, atol)
+        st = KrylovStats()
+        fn = self._lib.enp_fgmres_solve_f32 if f32 else self._lib.enp_fgmres_solve
+        rc = fn(self.h, _dptr(u_lin, dt), _dptr(b, dt), _dptr(x, dt), ctypes.byref(o),
+                ctypes.byref(st))
+        if rc != ENP_OK and (raise_on_fail or rc != ENP_ERR_NOT_CONVERGED):
+            self._check(rc)
+        return {k: getattr(st, k) for k, _ in KrylovStats._fields_} | {"status": rc}
+
+    def newton_solve(self, u, max_it=20, rtol=1e-10, atol=0.0, armijo_c=1e-4,
+                     max_backtracks=12, bj_storage=BJ_F64, mixed=False, krylov_restart=30,
+                     krylov_max_it=500, krylov_rtol=1e-3, raise_on_fail=True):
+        """Newton with backtracking line search in place on u; returns the stats."""
+        import torch
+        o = NewtonOpts(max_it, rtol, atol, armijo_c, max_backtracks, bj_storage, int(mixed),
+                       KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0))
+        st = NewtonStats()
+        rc = self._lib.enp_newton_solve(self.h, _dptr(u, torch.float64), ctypes.byref(o),
+                                        ctypes.byref(st))
+        if rc != ENP_OK and raise_on_fail:
+            self._check(rc)
+        out = {k: getattr(st, k) for k, _ in NewtonStats._fields_ if k != "history"}
+        out["history"] = list(st.history[: st.iterations + 1])
+        out["status"] = rc
         return out
 
     def vjp(self, u, w, out=None):

@@ -292,6 +292,7 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
 
 enp_status enp_dg_destroy(enp_handle h) {
   if (!h) return ENP_ERR_INVALID_ARG;
+  enp_solver_free(h);
   for (int a = 0; a < 3; ++a) cudaFree(h->d_xv[a]);
   cudaFree(h->d_btag);
   cudaFree(h->d_tab);

@@ -16,6 +16,11 @@ constexpr int kMaxP = 4;
 constexpr int kMaxN = kMaxP + 1;
 constexpr int kMaxQ = kMaxP + 2;
 
+// kBlockCol: column blockIdx.y of every element-diagonal block of J(u): the
+// J v pass with v = the local unit vector e_col in every element and the
+// neighbour's tangent set to zero, written to blk[e][row][col].
+enum OpMode : int { kResidual = 0, kJvp = 1, kVjp = 2, kBlockCol = 3 };
+
 enum FaceTag : int { kInterior = 0, kWall = 1, kInlet = 2, kOutlet = 3, kDirichlet = 4, kElectrode0 = 5 };
 
 // Everything the operator kernels read besides the vectors. Passed by value.

@@ -17,6 +17,9 @@ bool shape_supported(int dim, int p, int nf);
 
 }  // namespace enp
 
+struct enp_solver_ext;
+void enp_solver_free(struct enp_dg* h);
+
 struct enp_dg {
   enp::OpParams prm{};
   enp::Tables htab{};
@@ -30,4 +33,5 @@ struct enp_dg {
   long long n_dof = 0;           // per operating point
   cudaStream_t stream = nullptr;
   std::string err;
+  enp_solver_ext* solver = nullptr;   // block-Jacobi, Krylov and reduction workspace
 };

@@ -1,4 +1,6 @@
 // Run-time dispatch from (dim, p, fields, mode) to a compiled operator kernel.
+// For kBlockCol, `batch` is the number of block columns (NF * Np): grid.y runs
+// over the columns.
 #pragma once
 #include "enp_internal.h"
 #include "enp_operator.cuh"
@@ -32,6 +34,7 @@ static cudaError_t launch_mode(int mode, const OpParams& prm, const Tables* t, c
     case kResidual: return launch_one<DIM, P, NF, kResidual, R>(prm, t, u, v, out, batch, s);
     case kJvp: return launch_one<DIM, P, NF, kJvp, R>(prm, t, u, v, out, batch, s);
     case kVjp: return launch_one<DIM, P, NF, kVjp, R>(prm, t, u, v, out, batch, s);
+    case kBlockCol: return launch_one<DIM, P, NF, kBlockCol, R>(prm, t, u, v, out, batch, s);
   }
   return cudaErrorInvalidValue;
 }

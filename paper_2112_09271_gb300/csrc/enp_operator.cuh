@@ -17,7 +17,6 @@
 
 namespace enp {
 
-enum OpMode : int { kResidual = 0, kJvp = 1, kVjp = 2 };
 
 template <int DIM, int P, int NF>
 struct Shape {
@@ -35,7 +34,7 @@ struct Shape {
 template <int DIM, int P, int NF, int MODE>
 struct WarpSmem {
   using S = Shape<DIM, P, NF>;
-  static constexpr int NV = MODE == kResidual ? 1 : 2;           // vectors carried
+  static constexpr int NV = MODE == kResidual ? 1 : 2;           // vectors carried (block mode: 2)
   static constexpr int kNodes = NV * NF * S::NN;                   // own element data
   static constexpr int kOut = NF * S::NN;                          // element rows
   static constexpr int kTmp = 2 * S::TMP;
@@ -400,6 +399,8 @@ template <int DIM, int P, int NF, int MODE, int WPB, class R>
 __global__ void __launch_bounds__(WPB * 32)
 op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restrict__ u,
           const R* __restrict__ v, R* __restrict__ out) {
+  constexpr bool kBlk = MODE == kBlockCol;
+  constexpr int MODEc = kBlk ? kJvp : MODE;  // the arithmetic of the column pass is J v
   using S = Shape<DIM, P, NF>;
   using M = WarpSmem<DIM, P, NF, MODE>;
   constexpr int N = S::N, Q = S::Q, NN = S::NN, NQ = S::NQ, FQ = S::FQ;
@@ -421,7 +422,9 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x * WPB + warp;
   if (e >= prm.E) return;
-  const long long boff = (long long)blockIdx.y * prm.batch_stride;
+  const int col = kBlk ? (int)blockIdx.y : -1;
+  const long long boff = kBlk ? 0 : (long long)blockIdx.y * prm.batch_stride;
+  const int bidx = kBlk ? 0 : (int)blockIdx.y;
   R* base = sm + TabSmem<P>::total + warp * M::total;
   R* XA = base;                       // [NV][NF][NN] own data (u, then v or w)
   R* RO = XA + M::kNodes;             // [NF][NN] rows
@@ -455,7 +458,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
     const int f = t / NN, i = t % NN;
     const long long gi = boff + f * EN + (long long)e * NN + i;
     XA[t] = u[gi];
-    if (NV == 2) XA[NF * NN + t] = v[gi];
+    if (NV == 2) XA[NF * NN + t] = kBlk ? R(t == col ? 1 : 0) : v[gi];
   }
   __syncwarp();
 
@@ -506,7 +509,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
       for (int a = 0; a < 3; ++a) g0[f][a] = a < DIM ? V[(1 + a) * NQ + pt] * sc[a] : R(0);
     }
     R outS[NF], outG[NF][3];
-    if (MODE == kResidual) {
+    if (MODEc == kResidual) {
       R Sf[NF], Gf[NF][3];
       volume_flux<NF, DIM, R, R>(prm, c0, g0, uv, Sf, Gf);
 #pragma unroll
@@ -524,7 +527,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
 #pragma unroll
         for (int a = 0; a < 3; ++a) g1[f][a] = a < DIM ? V[(1 + a) * NQ + pt] * sc[a] : R(0);
       }
-      if (MODE == kJvp) {
+      if (MODEc == kJvp) {
         Tan<R> ct[NF], gt[NF][3], Sf[NF], Gf[NF][3];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -602,7 +605,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
       const int loc = DIM == 3 ? idx[b0] + prm.ne[b0] * idx[b1] : idx[b0];
       tag = prm.btag[prm.side_off[s] + loc];
       bface = prm.side_off[s] + loc;
-      if (tag == kWall || (tag == kInlet && MODE != kResidual)) continue;
+      if (tag == kWall || (tag == kInlet && MODEc != kResidual)) continue;
     } else {
       en = e + (hi ? stride[a] : -stride[a]);
       int in[3] = {idx[0], idx[1], idx[2]};
@@ -619,7 +622,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
         const int f = t / NN, i = t % NN;
         const long long gi = boff + f * EN + (long long)en * NN + i;
         XN[t] = u[gi];
-        if (NV == 2) XN[NF * NN + t] = v[gi];
+        if (NV == 2) XN[NF * NN + t] = kBlk ? R(0) : v[gi];
       }
       __syncwarp();
     }
@@ -642,7 +645,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
     const R sca = R(2) / h[a] * nrm;           // reference -> physical normal derivative, this side
     const R scn = boundary ? R(0) : R(2) / hn * nrm;  // other side, along this side's normal
     const R phiapp = (tag >= kElectrode0)
-        ? (prm.phiapp_batch ? R(prm.phiapp_batch[blockIdx.y * 4 + (tag - kElectrode0)])
+        ? (prm.phiapp_batch ? R(prm.phiapp_batch[bidx * 4 + (tag - kElectrode0)])
                             : R(prm.phiapp[tag - kElectrode0]))
         : R(0);
     for (int pt = lane; pt < FQ; pt += 32) {
@@ -671,7 +674,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
         g[f] = (tag == kDirichlet && prm.dirv)
                    ? R(prm.dirv[((long long)f * prm.NBF + bface) * prm.Nfq + pt]) : R(0);
       R oS[NF], oT[NF];
-      if (MODE == kResidual) {
+      if (MODEc == kResidual) {
         if (boundary) face_boundary_flux<NF, R, R>(prm, tag, cm, dm, g, un, delta, xp, phiapp, oS, oT);
         else face_interior_flux<NF, R, R>(prm, cm, dm, cp, dp, un, delta, oS, oT);
       } else {
@@ -685,7 +688,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
             cp1[f] = tn[pt]; dp1[f] = tn[FQ + pt] * scn;
           } else { cp1[f] = R(0); dp1[f] = R(0); }
         }
-        if (MODE == kJvp) {
+        if (MODEc == kJvp) {
           Tan<R> tm[NF], tdm[NF], tp[NF], tdp[NF], Sf[NF], Tf[NF];
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
@@ -734,9 +737,14 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
   }
 
   // ---- write rows
-  for (int t = lane; t < NF * NN; t += 32) {
-    const int f = t / NN, i = t % NN;
-    out[boff + f * EN + (long long)e * NN + i] = RO[t];
+  if (kBlk) {
+    const long long nb = NF * NN;
+    for (int t = lane; t < NF * NN; t += 32) out[((long long)e * nb + t) * nb + col] = RO[t];
+  } else {
+    for (int t = lane; t < NF * NN; t += 32) {
+      const int f = t / NN, i = t % NN;
+      out[boff + f * EN + (long long)e * NN + i] = RO[t];
+    }
   }
 }
 

@@ -1,0 +1,825 @@
+// Element block-Jacobi preconditioner, Krylov and Newton solvers, c_m recovery.
+//
+//  * block setup: the element-diagonal blocks of J(u) (volume terms plus this
+//    element's own-side face terms, all fields coupled), one column per grid.y
+//    of the J v kernel, then batched Gauss-Jordan inversion with partial
+//    pivoting; the inverse is stored transposed in FP64, FP32 or BF16.
+//  * block apply: y_e = B_e^{-1} x_e, one thread block per element, threads over
+//    rows, reading the stored inverse once (an HBM-bound batched GEMV).
+//  * FGMRES(m) with right preconditioning (flexible: the preconditioner may
+//    change between iterations), classical Gram-Schmidt applied twice, dot
+//    products reduced on the device in a fixed order (warp shuffles, then one
+//    partial per block, then one block), so results do not depend on timing.
+//  * Newton's method with backtracking line search on ||R|| (Sec. 4).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/enp_dg.h"
+#include "enp_internal.h"
+
+namespace enp {
+
+// ------------------------------------------------------------------ c_m
+// Eq. substitution: c_m = -(1/z_m) sum_{k<m} z_k c_k, node by node.
+__global__ void recover_cm_kernel(const double* __restrict__ u, double* __restrict__ cm, int NF,
+                                  long long EN, double zk0, double zk1, double zk2, double inv_zm,
+                                  long long batch_stride, int batch) {
+  const double zk[3] = {zk0, zk1, zk2};
+  long long total = EN * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long b = t / EN, i = t % EN;
+    double s = 0.0;
+    for (int k = 0; k < NF - 1; ++k) s += zk[k] * u[b * batch_stride + (k + 1) * EN + i];
+    cm[t] = -inv_zm * s;
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 608;  // 4 blocks per SM on 152 SMs; partials per dot product
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Partial sums of nd dot products <V_i, w> (i < nd) over each batch item:
+// part[b][i][block]. V_i = V + i * vstride. Fixed reduction order.
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+multidot_partial(const T* __restrict__ V, long long vstride, int nd, const T* __restrict__ w,
+                 long long n, long long bstride, double* __restrict__ part) {
+  __shared__ double red[kRedThreads / 32][32];
+  const int b = blockIdx.y;
+  const T* wb = w + b * bstride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < nd; i0 += 32) {
+    const int ni = min(32, nd - i0);
+    double acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+    for (long long k = blockIdx.x * (long long)kRedThreads + threadIdx.x; k < n;
+         k += (long long)gridDim.x * kRedThreads) {
+      const double wk = (double)wb[k];
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i < ni) acc[i] += (double)V[(i0 + i) * vstride + b * bstride + k] * wk;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      if (i >= ni) break;
+      double s = warp_sum(acc[i]);
+      if (lane == 0) red[warp][i] = s;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < ni) {
+      double s = 0.0;
+      for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[wv][lane];
+      part[((long long)b * nd + i0 + lane) * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[b][i] = sum over blocks of part[b][i][:], in block order.
+__global__ void finish_partials(const double* __restrict__ part, int nparts, int count,
+                                double* __restrict__ out) {
+  const int i = blockIdx.x;  // one block per (b, i)
+  if (i >= count) return;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += 32) s += part[(long long)i * nparts + k];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) out[i] = s;
+}
+
+// w[b] -= sum_i V_i[b] h[b][i]  (h on the device, [batch][nd])
+template <class T>
+__global__ void multi_axpy(const T* __restrict__ V, long long vstride, int nd,
+                           const double* __restrict__ h, T* __restrict__ w, long long n,
+                           long long bstride) {
+  const int b = blockIdx.y;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    double acc = (double)w[b * bstride + k];
+    for (int i = 0; i < nd; ++i) acc -= h[b * nd + i] * (double)V[i * vstride + b * bstride + k];
+    w[b * bstride + k] = (T)acc;
+  }
+}
+
+// y[b] = sum_{i<nd} V_i[b] c[b * cstride + i] (+ y[b] if accumulate)
+template <class T, class TY>
+__global__ void combine(const T* __restrict__ V, long long vstride, int nd,
+                        const double* __restrict__ c, int cstride, TY* __restrict__ y,
+                        long long n, long long bstride, int accumulate) {
+  const int b = blockIdx.y;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    double acc = accumulate ? (double)y[b * bstride + k] : 0.0;
+    for (int i = 0; i < nd; ++i) acc += c[b * cstride + i] * (double)V[i * vstride + b * bstride + k];
+    y[b * bstride + k] = (TY)acc;
+  }
+}
+
+// y[b] = a[b] * x[b] (+ beta * y) with per-batch scalars on the device
+template <class TX, class TY>
+__global__ void scale_copy(const TX* __restrict__ x, const double* __restrict__ a, double beta,
+                           TY* __restrict__ y, long long n, long long bstride) {
+  const int b = blockIdx.y;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    double v = a[b] * (double)x[b * bstride + k];
+    if (beta != 0.0) v += beta * (double)y[b * bstride + k];
+    y[b * bstride + k] = (TY)v;
+  }
+}
+
+__global__ void axpby_kernel(double a, const double* __restrict__ x, double bcoef,
+                             const double* __restrict__ y, double* __restrict__ z, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    z[k] = a * x[k] + bcoef * y[k];
+}
+
+template <class TX, class TY>
+__global__ void convert_kernel(const TX* __restrict__ x, TY* __restrict__ y, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] = (TY)x[k];
+}
+
+__global__ void count_nonfinite(const double* __restrict__ x, long long n, int* __restrict__ flag) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[k])) { atomicOr(flag, 1); return; }
+}
+
+// ------------------------------------------------------------------ block inverse
+// In-place Gauss-Jordan inversion with partial (row) pivoting of one n x n
+// block per thread block. The matrix lives in shared memory when it fits
+// (SMEM = true) else in global memory. Row swaps are undone at the end as
+// column swaps in reverse order. A zero or non-finite pivot sets *singular.
+// The inverse is written transposed (out[e][c][r] = inv[r][c]) in type TS.
+template <class T, class TS, bool SMEM>
+__global__ void gj_invert(const double* __restrict__ blocks, T* __restrict__ work, TS* __restrict__ out,
+                          int n, int* __restrict__ singular) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const long long e = blockIdx.x;
+  const long long nn = (long long)n * n;
+  T* A = SMEM ? reinterpret_cast<T*>(gsm) : work + e * nn;
+  T* colk = SMEM ? A + nn : reinterpret_cast<T*>(gsm);
+  int* piv = reinterpret_cast<int*>(colk + n);
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double* src = blocks + e * nn;
+  for (long long t = tid; t < nn; t += nt) A[t] = (T)src[t];
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // pivot: argmax_{i >= k} |A[i][k]| (lowest index on ties)
+    double best = -1.0; int bi = k;
+    for (int i = k + tid; i < n; i += nt) {
+      double a = fabs((double)A[(long long)i * n + k]);
+      if (a > best) { best = a; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = rv[0]; int i0 = ri[0];
+      for (int wv = 1; wv < (nt + 31) / 32; ++wv)
+        if (rv[wv] > b || (rv[wv] == b && ri[wv] < i0)) { b = rv[wv]; i0 = ri[wv]; }
+      s_p = i0;
+      piv[k] = i0;
+      if (!(b > 0.0) || !isfinite(b)) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int p = s_p;
+    if (p != k)
+      for (int j = tid; j < n; j += nt) {
+        T tmp = A[(long long)k * n + j];
+        A[(long long)k * n + j] = A[(long long)p * n + j];
+        A[(long long)p * n + j] = tmp;
+      }
+    __syncthreads();
+    const T pinv = T(1) / A[(long long)k * n + k];
+    for (int i = tid; i < n; i += nt) colk[i] = A[(long long)i * n + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) A[(long long)k * n + j] = (j == k) ? pinv : A[(long long)k * n + j] * pinv;
+    __syncthreads();
+    for (long long t = tid; t < nn; t += nt) {
+      const int i = (int)(t / n), j = (int)(t % n);
+      if (i == k) continue;
+      if (j == k) A[t] = -colk[i] * pinv;
+      else A[t] -= colk[i] * A[(long long)k * n + j];
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (tid == 0) atomicOr(singular, 1);
+    return;
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = tid; i < n; i += nt) {
+        T tmp = A[(long long)i * n + k];
+        A[(long long)i * n + k] = A[(long long)i * n + p];
+        A[(long long)i * n + p] = tmp;
+      }
+    __syncthreads();
+  }
+  TS* o = out + e * nn;
+  for (long long t = tid; t < nn; t += nt) {
+    const int r = (int)(t / n), c = (int)(t % n);
+    o[(long long)c * n + r] = (TS)A[t];
+  }
+}
+
+// y_e = Binv_e x_e with the inverse stored transposed (BT[c][r]); accumulation in TA.
+template <class TS, class TA, class TV>
+__global__ void bj_apply_kernel(const TS* __restrict__ BT, const TV* __restrict__ x,
+                                TV* __restrict__ y, int n, int NF, int Np, long long EN,
+                                long long bstride) {
+  extern __shared__ __align__(16) unsigned char xsm_raw[];
+  TA* xs = reinterpret_cast<TA*>(xsm_raw);
+  const long long e = blockIdx.x;
+  const int b = blockIdx.y;
+  const long long E = EN / Np;
+  const TV* xb = x + b * bstride;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const int f = c / Np, i = c % Np;
+    xs[c] = (TA)xb[f * EN + e * Np + i];
+  }
+  __syncthreads();
+  const TS* B = BT + ((long long)b * E + e) * (long long)n * n;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    TA acc = TA(0);
+    for (int c = 0; c < n; ++c) acc += (TA)B[(long long)c * n + r] * xs[c];
+    const int f = r / Np, i = r % Np;
+    y[b * bstride + f * EN + e * Np + i] = (TV)acc;
+  }
+}
+
+}  // namespace enp
+
+// ====================================================================== host
+using enp::OpParams;
+
+namespace {
+
+int grid_for(long long n, int threads = 256) {
+  long long g = (n + threads - 1) / threads;
+  return (int)std::max(1LL, std::min(g, 152LL * 8));
+}
+
+struct SolverState {
+  // block-Jacobi
+  int nb = 0;
+  int storage = -1;               // 0 f64, 1 f32, 2 bf16
+  double* blocks = nullptr;       // [batch][E][nb][nb] assembled blocks (FP64)
+  void* binv = nullptr;           // [batch][E][nb][nb] inverse, transposed, in `storage`
+  void* gj_work = nullptr;        // global work for blocks too large for shared memory
+  size_t gj_work_bytes = 0;
+  int* d_flag = nullptr;
+  // reductions
+  double* part = nullptr;
+  size_t part_count = 0;
+  double* dsmall = nullptr;       // device small vectors
+  size_t dsmall_count = 0;
+  // Krylov workspace
+  void* V = nullptr;
+  void* Z = nullptr;
+  size_t krylov_bytes = 0;
+};
+
+}  // namespace
+
+struct enp_solver_ext {
+  SolverState s;
+};
+
+namespace {
+
+SolverState& state_of(enp_handle h) {
+  if (!h->solver) h->solver = new enp_solver_ext();
+  return h->solver->s;
+}
+
+enp_status cuda_err(enp_handle h, cudaError_t e, const char* what) {
+  h->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? ENP_ERR_OOM : ENP_ERR_CUDA;
+}
+
+template <class P>
+cudaError_t ensure(P** p, size_t& have, size_t want_count) {
+  if (*p && have >= want_count) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  have = 0;
+  cudaError_t e = cudaMalloc((void**)p, want_count * sizeof(P));
+  if (e == cudaSuccess) have = want_count;
+  return e;
+}
+
+// Batched dot products <V_i, w>_b for i < nd, into dsmall[0 .. batch*nd).
+template <class T>
+cudaError_t multidot(enp_handle h, const T* V, long long vstride, int nd, const T* w,
+                     double* out) {
+  SolverState& S = state_of(h);
+  const long long n = h->n_dof;
+  const int B = h->batch;
+  cudaError_t e = ensure(&S.part, S.part_count, (size_t)B * std::max(nd, 1) * enp::kRedBlocks);
+  if (e != cudaSuccess) return e;
+  dim3 g(enp::kRedBlocks, B);
+  enp::multidot_partial<T><<<g, enp::kRedThreads, 0, h->stream>>>(V, vstride, nd, w, n, n, S.part);
+  enp::finish_partials<<<B * nd, 32, 0, h->stream>>>(S.part, enp::kRedBlocks, B * nd, out);
+  return cudaGetLastError();
+}
+
+cudaError_t small(enp_handle h, size_t count) {
+  SolverState& S = state_of(h);
+  return ensure(&S.dsmall, S.dsmall_count, count);
+}
+
+}  // namespace
+
+void enp_solver_free(enp_handle h) {
+  if (!h || !h->solver) return;
+  SolverState& S = h->solver->s;
+  cudaFree(S.blocks); cudaFree(S.binv); cudaFree(S.gj_work); cudaFree(S.d_flag);
+  cudaFree(S.part); cudaFree(S.dsmall); cudaFree(S.V);
+  delete h->solver;
+  h->solver = nullptr;
+}
+
+extern "C" {
+
+enp_status enp_recover_cm(enp_handle h, const double* u, double* cm) {
+  if (!h || !u || !cm) return ENP_ERR_INVALID_ARG;
+  const OpParams& P = h->prm;
+  const long long EN = (long long)P.E * P.Np;
+  double zk[3] = {0, 0, 0};
+  for (int k = 0; k < P.NF - 1 && k < 3; ++k) zk[k] = P.z[k];
+  enp::recover_cm_kernel<<<grid_for(EN * h->batch), 256, 0, h->stream>>>(
+      u, cm, P.NF, EN, zk[0], zk[1], zk[2], 1.0 / P.z[P.NF - 1], P.batch_stride, h->batch);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "recover_cm");
+}
+
+enp_status enp_inner_product(enp_handle h, const double* x, const double* y, double* out) {
+  if (!h || !x || !y || !out) return ENP_ERR_INVALID_ARG;
+  cudaError_t e = small(h, (size_t)h->batch);
+  if (e == cudaSuccess) e = multidot<double>(h, x, 0, 1, y, state_of(h).dsmall);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, state_of(h).dsmall, sizeof(double) * h->batch, cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "inner_product");
+}
+
+enp_status enp_block_diagonal(enp_handle h, const double* u, double* blocks) {
+  if (!h || !u || !blocks) return ENP_ERR_INVALID_ARG;
+  const OpParams& P = h->prm;
+  const int nb = P.NF * P.Np;
+  const long long bsz = (long long)P.E * nb * nb;
+  for (int b = 0; b < h->batch; ++b) {
+    OpParams Pb = P;
+    if (P.phiapp_batch) Pb.phiapp_batch = P.phiapp_batch + 4 * b;
+    cudaError_t e = enp::launch_op<double>(enp::kBlockCol, Pb, h->d_tab, u + b * P.batch_stride,
+                                           nullptr, blocks + b * bsz, nb, h->stream);
+    if (e != cudaSuccess) return cuda_err(h, e, "block columns");
+  }
+  return ENP_OK;
+}
+
+enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
+  if (!h || !u || storage < 0 || storage > 2) return ENP_ERR_INVALID_ARG;
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  const int nb = P.NF * P.Np;
+  const long long nblk = (long long)h->batch * P.E;
+  const size_t nn = (size_t)nb * nb;
+  cudaError_t e;
+  if (!S.blocks || S.nb != nb) {
+    cudaFree(S.blocks);
+    S.blocks = nullptr;
+    e = cudaMalloc(&S.blocks, sizeof(double) * nn * nblk);
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc blocks");
+  }
+  const size_t esz = storage == 0 ? 8 : (storage == 1 ? 4 : 2);
+  if (!S.binv || S.nb != nb || S.storage != storage) {
+    cudaFree(S.binv);
+    S.binv = nullptr;
+    e = cudaMalloc(&S.binv, esz * nn * nblk);
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc block inverses");
+  }
+  S.nb = nb;
+  S.storage = storage;
+  if (!S.d_flag) {
+    e = cudaMalloc(&S.d_flag, sizeof(int));
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc flag");
+  }
+  enp_status st = enp_block_diagonal(h, u, S.blocks);
+  if (st != ENP_OK) return st;
+  cudaMemsetAsync(S.d_flag, 0, sizeof(int), h->stream);
+  // the factorisation runs in FP64 for FP64 storage, else in FP32
+  const bool f64 = storage == 0;
+  const size_t telt = f64 ? 8 : 4;
+  const size_t smem_full = telt * (nn + nb) + sizeof(int) * nb;
+  const bool in_smem = smem_full <= 200 * 1024;
+  const int threads = 512;
+  if (!in_smem) {
+    e = ensure((char**)&S.gj_work, S.gj_work_bytes, telt * nn * nblk);
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc inversion work");
+  }
+  const size_t smem = in_smem ? smem_full : telt * nb + sizeof(int) * nb;
+#define ENP_GJ(T, TS, SM)                                                                        \
+  {                                                                                             \
+    auto k = enp::gj_invert<T, TS, SM>;                                                         \
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+    if (e == cudaSuccess) {                                                                     \
+      k<<<(unsigned)nblk, threads, smem, h->stream>>>(S.blocks, (T*)S.gj_work, (TS*)S.binv, nb, \
+                                                      S.d_flag);                                \
+      e = cudaGetLastError();                                                                   \
+    }                                                                                           \
+  }
+  if (storage == 0) { if (in_smem) ENP_GJ(double, double, true) else ENP_GJ(double, double, false) }
+  else if (storage == 1) { if (in_smem) ENP_GJ(float, float, true) else ENP_GJ(float, float, false) }
+  else { if (in_smem) ENP_GJ(float, __nv_bfloat16, true) else ENP_GJ(float, __nv_bfloat16, false) }
+#undef ENP_GJ
+  if (e != cudaSuccess) return cuda_err(h, e, "block inversion");
+  int flag = 0;
+  e = cudaMemcpyAsync(&flag, S.d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_err(h, e, "block inversion sync");
+  if (flag) {
+    h->err = "singular or non-finite element block";
+    return ENP_ERR_NONFINITE;
+  }
+  return ENP_OK;
+}
+
+}  // extern "C"
+
+// Apply the stored block inverse to a vector of type TV (double or float).
+template <class TV>
+static cudaError_t bj_apply_any(enp_handle h, const TV* x, TV* y) {
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  const int nb = S.nb;
+  const long long EN = (long long)P.E * P.Np;
+  dim3 g(P.E, h->batch);
+  int threads = std::min(256, ((nb + 31) / 32) * 32);
+  if (S.storage == 0) {
+    size_t sm = sizeof(double) * nb;
+    enp::bj_apply_kernel<double, double, TV><<<g, threads, sm, h->stream>>>(
+        (const double*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride);
+  } else if (S.storage == 1) {
+    size_t sm = sizeof(float) * nb;
+    enp::bj_apply_kernel<float, float, TV><<<g, threads, sm, h->stream>>>(
+        (const float*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride);
+  } else {
+    size_t sm = sizeof(float) * nb;
+    enp::bj_apply_kernel<__nv_bfloat16, float, TV><<<g, threads, sm, h->stream>>>(
+        (const __nv_bfloat16*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride);
+  }
+  return cudaGetLastError();
+}
+
+extern "C" enp_status enp_block_jacobi_apply(enp_handle h, const double* x, double* y) {
+  if (!h || !x || !y) return ENP_ERR_INVALID_ARG;
+  if (!h->solver || state_of(h).storage < 0) {
+    h->err = "enp_block_jacobi_setup has not been called";
+    return ENP_ERR_INVALID_ARG;
+  }
+  cudaError_t e = bj_apply_any<double>(h, x, y);
+  return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "block apply");
+}
+
+// ---------------------------------------------------------------- FGMRES
+// Solves J(u_lin) x = b (right-preconditioned by the block-Jacobi inverse set
+// up last; identity if none) for every operating point of the batch. TV is the
+// Krylov vector type: double (FP64 operator) or float (FP32 operator, inner
+// solve of the mixed-precision Newton method).
+template <class TV>
+static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
+                             const enp_krylov_opts* o, enp_krylov_stats* st) {
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  const long long n = h->n_dof;
+  const int B = h->batch;
+  const int m = std::max(1, std::min(o->restart, 200));
+  const long long ntot = n * B;
+  const bool precond = S.storage >= 0;
+  cudaError_t e;
+  const size_t vbytes = sizeof(TV) * ntot;
+  const size_t need = vbytes * (size_t)(m + 1) + vbytes * (size_t)m;
+  if (S.krylov_bytes < need) {
+    cudaFree(S.V); S.V = nullptr; S.Z = nullptr; S.krylov_bytes = 0;
+    e = cudaMalloc(&S.V, need);
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc Krylov basis");
+    S.krylov_bytes = need;
+  }
+  TV* V = (TV*)S.V;                       // [m+1][B][n]
+  TV* Z = (TV*)((char*)S.V + vbytes * (m + 1));  // [m][B][n]
+  const long long vs = ntot;             // stride between basis vectors
+  e = small(h, (size_t)B * (2 * (m + 2)) + (size_t)B * m);
+  if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc small");
+  double* dh = S.dsmall;                          // [B][m+1] projections
+  double* dc = S.dsmall + (size_t)B * (m + 2);    // [B][m+1] per-batch scalars
+  double* dcoef = S.dsmall + (size_t)B * 2 * (m + 2);  // [B][m] update coefficients
+  std::vector<double> H((size_t)B * (m + 1) * m), g((size_t)B * (m + 1)), cs((size_t)B * m),
+      sn((size_t)B * m), hh((size_t)B * (m + 1)), beta0(B, 0.0), resn(B, 0.0), bnorm(B, 0.0);
+  std::vector<int> done(B, 0), jconv(B, m);
+  const int gx = grid_for(n);
+  dim3 gv(gx, B);
+  auto apply_A = [&](const TV* in, TV* outv) -> cudaError_t {
+    return enp::launch_op<TV>(enp::kJvp, P, h->d_tab, ulin, in, outv, B, h->stream);
+  };
+  auto dots = [&](const TV* Vb, int nd, const TV* w, std::vector<double>& hostv) -> cudaError_t {
+    cudaError_t er = multidot<TV>(h, Vb, vs, nd, w, dh);
+    if (er != cudaSuccess) return er;
+    hostv.assign((size_t)B * nd, 0.0);
+    er = cudaMemcpyAsync(hostv.data(), dh, sizeof(double) * B * nd, cudaMemcpyDeviceToHost, h->stream);
+    if (er != cudaSuccess) return er;
+    return cudaStreamSynchronize(h->stream);
+  };
+  std::vector<double> tmp;
+  // ||b||
+  if ((e = dots(b, 1, b, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres norm");
+  for (int i = 0; i < B; ++i) bnorm[i] = std::sqrt(tmp[i]);
+  int total_it = 0;
+  bool all_done = false;
+  double first_norm = -1.0;
+  for (int cycle = 0; !all_done && total_it < o->max_it; ++cycle) {
+    // r0 = b - A x  -> V_0
+    if ((e = apply_A(x, V)) != cudaSuccess) return cuda_err(h, e, "fgmres A x");
+    std::vector<double> one(B, -1.0);
+    // V0 = b - V0
+    {
+      std::vector<double> ones(B, 1.0);
+      cudaMemcpyAsync(dc, one.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
+      enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, dc, 0.0, V, n, n);
+      cudaMemcpyAsync(dc, ones.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
+      enp::combine<TV, TV><<<gv, 256, 0, h->stream>>>(b, 0, 1, dc, 1, V, n, n, 1);
+    }
+    if ((e = dots(V, 1, V, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres r0");
+    for (int i = 0; i < B; ++i) {
+      beta0[i] = std::sqrt(tmp[i]);
+      if (first_norm < 0) resn[i] = beta0[i];
+    }
+    if (first_norm < 0) {
+      first_norm = 0;
+      for (int i = 0; i < B; ++i) first_norm = std::max(first_norm, beta0[i]);
+    }
+    std::vector<double> inv(B);
+    all_done = true;
+    for (int i = 0; i < B; ++i) {
+      double tol = std::max(o->rtol * bnorm[i], o->atol);
+      done[i] = !(beta0[i] > tol);
+      if (!std::isfinite(beta0[i])) { h->err = "non-finite residual in FGMRES"; return ENP_ERR_NONFINITE; }
+      inv[i] = done[i] ? 0.0 : 1.0 / beta0[i];
+      all_done = all_done && done[i];
+      resn[i] = beta0[i];
+    }
+    if (all_done) break;
+    cudaMemcpyAsync(dc, inv.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
+    enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, dc, 0.0, V, n, n);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    for (int i = 0; i < B; ++i) { g[(size_t)i * (m + 1)] = beta0[i]; jconv[i] = -1; }
+    int j = 0;
+    for (; j < m && total_it < o->max_it; ++j) {
+      TV* vj = V + j * vs;
+      TV* zj = Z + j * vs;
+      TV* w = V + (j + 1) * vs;
+      if (precond) e = bj_apply_any<TV>(h, vj, zj);
+      else e = cudaMemcpyAsync(zj, vj, vbytes, cudaMemcpyDeviceToDevice, h->stream);
+      if (e != cudaSuccess) return cuda_err(h, e, "fgmres precondition");
+      if ((e = apply_A(zj, w)) != cudaSuccess) return cuda_err(h, e, "fgmres A z");
+      // classical Gram-Schmidt, twice
+      std::vector<double> hsum((size_t)B * (j + 1), 0.0);
+      for (int pass = 0; pass < 2; ++pass) {
+        if ((e = dots(V, j + 1, w, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres dots");
+        cudaMemcpyAsync(dh, tmp.data(), sizeof(double) * B * (j + 1), cudaMemcpyHostToDevice, h->stream);
+        enp::multi_axpy<TV><<<gv, 256, 0, h->stream>>>(V, vs, j + 1, dh, w, n, n);
+        for (size_t t = 0; t < hsum.size(); ++t) hsum[t] += tmp[t];
+      }
+      if ((e = dots(w, 1, w, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres norm w");
+      ++total_it;
+      std::vector<double> invn(B);
+      bool alldone_now = true;
+      for (int i = 0; i < B; ++i) {
+        double* Hi = &H[(size_t)i * (m + 1) * m];
+        double* gi = &g[(size_t)i * (m + 1)];
+        double* csi = &cs[(size_t)i * m];
+        double* sni = &sn[(size_t)i * m];
+        const double hn = std::sqrt(tmp[i]);
+        invn[i] = (hn > 0 && jconv[i] < 0) ? 1.0 / hn : 0.0;
+        if (jconv[i] >= 0) continue;  // this operating point already converged
+        for (int r = 0; r <= j; ++r) Hi[(size_t)r * m + j] = hsum[(size_t)i * (j + 1) + r];
+        Hi[(size_t)(j + 1) * m + j] = hn;
+        for (int r = 0; r < j; ++r) {  // apply previous rotations
+          double a = Hi[(size_t)r * m + j], bb = Hi[(size_t)(r + 1) * m + j];
+          Hi[(size_t)r * m + j] = csi[r] * a + sni[r] * bb;
+          Hi[(size_t)(r + 1) * m + j] = -sni[r] * a + csi[r] * bb;
+        }
+        double a = Hi[(size_t)j * m + j], bb = Hi[(size_t)(j + 1) * m + j];
+        double rr = std::hypot(a, bb);
+        csi[j] = rr > 0 ? a / rr : 1.0;
+        sni[j] = rr > 0 ? bb / rr : 0.0;
+        Hi[(size_t)j * m + j] = rr;
+        Hi[(size_t)(j + 1) * m + j] = 0.0;
+        gi[j + 1] = -sni[j] * gi[j];
+        gi[j] = csi[j] * gi[j];
+        resn[i] = std::fabs(gi[j + 1]);
+        if (!std::isfinite(resn[i])) { h->err = "non-finite value in FGMRES"; return ENP_ERR_NONFINITE; }
+        double tol = std::max(o->rtol * bnorm[i], o->atol);
+        if (resn[i] <= tol || hn == 0.0) jconv[i] = j;
+        alldone_now = alldone_now && jconv[i] >= 0;
+      }
+      cudaMemcpyAsync(dc, invn.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
+      enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(w, dc, 0.0, w, n, n);
+      if (alldone_now) { ++j; break; }
+    }
+    // x += Z y, y from the triangular system of each operating point
+    const int jm = j;
+    std::vector<double> coef((size_t)B * m, 0.0);
+    for (int i = 0; i < B; ++i) {
+      const int ji = jconv[i] >= 0 ? jconv[i] + 1 : jm;
+      const double* Hi = &H[(size_t)i * (m + 1) * m];
+      const double* gi = &g[(size_t)i * (m + 1)];
+      for (int r = ji - 1; r >= 0; --r) {
+        double s = gi[r];
+        for (int c = r + 1; c < ji; ++c) s -= Hi[(size_t)r * m + c] * coef[(size_t)i * m + c];
+        coef[(size_t)i * m + r] = Hi[(size_t)r * m + r] != 0 ? s / Hi[(size_t)r * m + r] : 0.0;
+      }
+    }
+    cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * B * m, cudaMemcpyHostToDevice, h->stream);
+    enp::combine<TV, TV><<<gv, 256, 0, h->stream>>>(Z, vs, jm, dcoef, m, x, n, n, 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(h, e, "fgmres update");
+    all_done = true;
+    for (int i = 0; i < B; ++i) all_done = all_done && jconv[i] >= 0;
+    if (all_done) {
+      // true residual check of the final iterate
+      if ((e = apply_A(x, V)) != cudaSuccess) return cuda_err(h, e, "fgmres final A x");
+      std::vector<double> minus1(B, -1.0), ones(B, 1.0);
+      cudaMemcpyAsync(dc, minus1.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
+      enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, dc, 0.0, V, n, n);
+      cudaMemcpyAsync(dc, ones.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
+      enp::combine<TV, TV><<<gv, 256, 0, h->stream>>>(b, 0, 1, dc, 1, V, n, n, 1);
+      if ((e = dots(V, 1, V, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres final r");
+      for (int i = 0; i < B; ++i) resn[i] = std::sqrt(tmp[i]);
+    }
+  }
+  double worst_rel = 0.0, worst = 0.0;
+  bool conv = true;
+  for (int i = 0; i < B; ++i) {
+    double tol = std::max(o->rtol * bnorm[i], o->atol);
+    // the true residual may exceed the recurrence estimate by rounding
+    if (!(resn[i] <= tol * 1.0001 + 0.0)) conv = false;
+    worst = std::max(worst, resn[i]);
+    worst_rel = std::max(worst_rel, bnorm[i] > 0 ? resn[i] / bnorm[i] : resn[i]);
+  }
+  if (st) {
+    st->iterations = total_it;
+    st->residual_norm = worst;
+    st->relative_residual = worst_rel;
+    st->initial_norm = first_norm;
+    st->converged = conv ? 1 : 0;
+  }
+  if (!conv) { h->err = "FGMRES reached max_it"; return ENP_ERR_NOT_CONVERGED; }
+  return ENP_OK;
+}
+
+extern "C" enp_status enp_fgmres_solve(enp_handle h, const double* u_lin, const double* b, double* x,
+                                       const enp_krylov_opts* o, enp_krylov_stats* st) {
+  if (!h || !u_lin || !b || !x || !o || o->restart < 1 || o->max_it < 1) return ENP_ERR_INVALID_ARG;
+  return fgmres_any<double>(h, u_lin, b, x, o, st);
+}
+
+extern "C" enp_status enp_fgmres_solve_f32(enp_handle h, const float* u_lin, const float* b, float* x,
+                                           const enp_krylov_opts* o, enp_krylov_stats* st) {
+  if (!h || !u_lin || !b || !x || !o || o->restart < 1 || o->max_it < 1) return ENP_ERR_INVALID_ARG;
+  return fgmres_any<float>(h, u_lin, b, x, o, st);
+}
+
+// ---------------------------------------------------------------- Newton
+// Newton's method with backtracking line search (Sec. 4): solve J du = -R with
+// FGMRES (FP64, or with the FP32 operator when opts->mixed), then halve the step
+// until ||R(u + lam du)|| <= (1 - c lam) ||R(u)||. The block-Jacobi
+// preconditioner is rebuilt at every Newton iterate. The norm tested is the
+// largest over the operating points.
+extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* o,
+                                       enp_newton_stats* st) {
+  if (!h || !u || !o || o->max_it < 0) return ENP_ERR_INVALID_ARG;
+  SolverState& S = state_of(h);
+  const long long ntot = h->n_dof * h->batch;
+  const int B = h->batch;
+  cudaError_t e;
+  (void)S;
+  double *r = nullptr, *du = nullptr, *ut = nullptr, *rt = nullptr;
+  float *u32 = nullptr, *b32 = nullptr, *x32 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(r); cudaFree(du); cudaFree(ut); cudaFree(rt);
+    cudaFree(u32); cudaFree(b32); cudaFree(x32);
+  };
+  e = cudaMalloc(&r, sizeof(double) * ntot);
+  if (e == cudaSuccess) e = cudaMalloc(&du, sizeof(double) * ntot);
+  if (e == cudaSuccess) e = cudaMalloc(&ut, sizeof(double) * ntot);
+  if (e == cudaSuccess) e = cudaMalloc(&rt, sizeof(double) * ntot);
+  if (e == cudaSuccess && o->mixed) {
+    e = cudaMalloc(&u32, sizeof(float) * ntot);
+    if (e == cudaSuccess) e = cudaMalloc(&b32, sizeof(float) * ntot);
+    if (e == cudaSuccess) e = cudaMalloc(&x32, sizeof(float) * ntot);
+  }
+  if (e != cudaSuccess) { cleanup(); return cuda_err(h, e, "cudaMalloc newton work"); }
+  auto norms = [&](const double* v, std::vector<double>& out) -> cudaError_t {
+    cudaError_t er = small(h, (size_t)B * 4);
+    if (er != cudaSuccess) return er;
+    er = multidot<double>(h, v, 0, 1, v, S.dsmall);
+    if (er != cudaSuccess) return er;
+    out.assign(B, 0.0);
+    er = cudaMemcpyAsync(out.data(), S.dsmall, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream);
+    if (er != cudaSuccess) return er;
+    er = cudaStreamSynchronize(h->stream);
+    for (auto& x : out) x = std::sqrt(x);
+    return er;
+  };
+  auto maxof = [](const std::vector<double>& v) { double m = 0; for (double x : v) m = std::max(m, std::isnan(x) ? INFINITY : x); return m; };
+  enp_status status = ENP_OK;
+  std::vector<double> rn;
+  if ((e = enp::launch_op<double>(enp::kResidual, h->prm, h->d_tab, u, nullptr, r, B, h->stream)) != cudaSuccess ||
+      (e = norms(r, rn)) != cudaSuccess) { cleanup(); return cuda_err(h, e, "newton residual"); }
+  double r0 = maxof(rn), rcur = r0;
+  if (!std::isfinite(r0)) { cleanup(); h->err = "non-finite initial residual"; return ENP_ERR_NONFINITE; }
+  int it = 0, kry_total = 0;
+  if (st) { std::memset(st, 0, sizeof(*st)); st->initial_norm = r0; st->history[0] = r0; }
+  const int gx = grid_for(ntot);
+  while (true) {
+    if (rcur <= std::max(o->rtol * r0, o->atol)) break;
+    if (it >= o->max_it) { status = ENP_ERR_NOT_CONVERGED; h->err = "Newton reached max_it"; break; }
+    enp_status s2 = enp_block_jacobi_setup(h, u, o->bj_storage);
+    if (s2 != ENP_OK) { status = s2; break; }
+    enp_krylov_stats ks{};
+    enp_krylov_opts ko = o->krylov;
+    // b = -r, x = 0
+    enp::axpby_kernel<<<gx, 256, 0, h->stream>>>(-1.0, r, 0.0, r, rt, ntot);
+    cudaMemsetAsync(du, 0, sizeof(double) * ntot, h->stream);
+    if (o->mixed) {
+      enp::convert_kernel<double, float><<<gx, 256, 0, h->stream>>>(u, u32, ntot);
+      enp::convert_kernel<double, float><<<gx, 256, 0, h->stream>>>(rt, b32, ntot);
+      cudaMemsetAsync(x32, 0, sizeof(float) * ntot, h->stream);
+      s2 = fgmres_any<float>(h, u32, b32, x32, &ko, &ks);
+      enp::convert_kernel<float, double><<<gx, 256, 0, h->stream>>>(x32, du, ntot);
+    } else {
+      s2 = fgmres_any<double>(h, u, rt, du, &ko, &ks);
+    }
+    kry_total += ks.iterations;
+    if (s2 != ENP_OK && s2 != ENP_ERR_NOT_CONVERGED) { status = s2; break; }
+    // backtracking line search
+    double lam = 1.0, rnew = INFINITY;
+    int bt = 0;
+    for (;; ++bt) {
+      enp::axpby_kernel<<<gx, 256, 0, h->stream>>>(1.0, u, lam, du, ut, ntot);
+      if ((e = enp::launch_op<double>(enp::kResidual, h->prm, h->d_tab, ut, nullptr, rt, B, h->stream)) != cudaSuccess ||
+          (e = norms(rt, rn)) != cudaSuccess) { cleanup(); return cuda_err(h, e, "newton line search"); }
+      rnew = maxof(rn);
+      if (rnew <= (1.0 - o->armijo_c * lam) * rcur || bt >= o->max_backtracks) break;
+      lam *= 0.5;
+    }
+    cudaMemcpyAsync(u, ut, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(r, rt, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, h->stream);
+    ++it;
+    rcur = rnew;
+    if (st && it < 64) st->history[it] = rcur;
+    if (!std::isfinite(rcur)) { status = ENP_ERR_NONFINITE; h->err = "non-finite residual"; break; }
+  }
+  cudaStreamSynchronize(h->stream);
+  if (st) {
+    st->iterations = it;
+    st->krylov_iterations = kry_total;
+    st->residual_norm = rcur;
+    st->converged = (status == ENP_OK) ? 1 : 0;
+  }
+  cleanup();
+  return status;
+}

@@ -371,3 +371,36 @@ def test_element_subset_rows_match_full():
     np.testing.assert_array_equal(part[:, el], full[:, el])
     mask = np.ones(P.E, bool); mask[el] = False
     assert np.all(part[:, mask] == 0)
+
+
+# ------------------------------------------------------------ c_m, blocks
+@pytest.mark.parametrize("cfg", ["cube_n2_p2", "channel_n1"])
+def test_recovered_cm_satisfies_electroneutrality(cfg):
+    """Eq. electroneutrality: sum_{k=1}^{m} z_k c_k = 0 with c_m from Eq. substitution."""
+    P = W.config(cfg)
+    u = W.random_state(P, 3)
+    cm = oracle.recover_cm(P, u)
+    uu = u.reshape(P.n_fields, -1)
+    total = sum(P.z[k] * uu[k + 1] for k in range(P.m - 1)) + P.z[P.m - 1] * cm
+    assert np.abs(total).max() < 1e-14 * np.abs(uu[1:]).max()
+
+
+def test_block_diagonal_and_block_solve_are_consistent():
+    """The diagonal blocks equal the element-local Jacobian with the neighbours'
+    unknowns frozen: J applied to a vector supported on one element, restricted
+    to that element's rows, equals the block times the vector."""
+    P = W.config("cube_n3_p2")
+    orc = oracle.Oracle(P)
+    u = W.random_state(P, 3)
+    blocks = orc.block_diagonal(u)
+    e = 13
+    rng = np.random.default_rng(1)
+    v = np.zeros(P.n_dof).reshape(P.n_fields, P.E, P.Np)
+    v[:, e] = rng.standard_normal((P.n_fields, P.Np))
+    jv = orc.jvp(u, v.reshape(-1)).reshape(P.n_fields, P.E, P.Np)
+    np.testing.assert_allclose(jv[:, e].reshape(-1), blocks[e] @ v[:, e].reshape(-1),
+                               rtol=1e-12, atol=1e-14)
+    x = rng.standard_normal(P.n_dof)
+    y = orc.block_jacobi_apply(blocks, x).reshape(P.n_fields, P.E, P.Np)
+    np.testing.assert_allclose(blocks[e] @ y[:, e].reshape(-1),
+                               x.reshape(P.n_fields, P.E, P.Np)[:, e].reshape(-1), rtol=1e-10)
