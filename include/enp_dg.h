@@ -236,6 +236,27 @@ typedef struct {
 enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* opts,
                             enp_newton_stats* stats);
 
+/* enp_inner_product without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc,
+ * such as a host application that owns all device memory through its own pool,
+ * or a latency-critical loop that cannot afford cudaMalloc's cost and implicit
+ * device synchronisation. It needs no handle.
+ *   out[b] = <x_b, y_b> for b < batch, x and y device arrays [batch][n],
+ *   out a device array of batch doubles; asynchronous on `stream` (a
+ *   cudaStream_t, may be 0). Same reduction order as enp_inner_product.
+ * The partial sums live in one fixed array of ENP_NOALLOC_MAX_BATCH x 608
+ * doubles in the library's static device memory, held by every GPU that loads
+ * the library until the process exits. batch > ENP_NOALLOC_MAX_BATCH returns
+ * ENP_ERR_INVALID_ARG without launching anything.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * All calls share the array, and it keeps the last call's contents (each call
+ * writes every entry it reads, so nothing needs clearing): calls that overlap
+ * on the GPU (on different streams, or from different threads) race. */
+#define ENP_NOALLOC_MAX_BATCH 32
+enp_status enp_inner_product_noalloc(const double* x, const double* y, long long n, int batch,
+                                     double* out, void* stream);
+
 /* Message of the last failed call on this handle ("" if none). The pointer is
  * owned by the handle and valid until the next call on it. */
 const char* enp_last_error(enp_handle h);

@@ -22,7 +22,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libenp_dg.so")
-SOURCES = ["enp_api.cu", "op_f64.cu", "op_f32.cu", "enp_solver.cu"]
+SOURCES = ["enp_api.cu", "op_f64.cu", "op_f32.cu", "enp_solver.cu", "enp_noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC",
               "--expt-relaxed-constexpr"]
@@ -153,8 +153,11 @@ _PROTOS = [
     ("enp_fgmres_solve", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_fgmres_solve_f32", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_newton_solve", _I, [_V, _V, _V, _V]),
+    ("enp_inner_product_noalloc", _I, [_V, _V, _LL, _I, _V, _V]),
     ("enp_last_error", ctypes.c_char_p, [_V]),
 ]
+
+NOALLOC_MAX_BATCH = 32
 
 
 def load(path: str | None = None):
