@@ -2,12 +2,16 @@
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl native|reference]
 
-A step is one pass of the operator rows over one synthetic state of the
-workload (inputs resident in HBM): R(u), J(u)v and J(u)^T w in FP64 and the
-single-precision J(u)v of the mixed-precision inner solve. `value` counts
-degrees of freedom times operator applications per second (GDOF/s), summed over
-ranks. Each step is timed with CUDA events on the launching stream; between
-steps a 512 MB buffer is written to flush the 129 MB L2 (outside the events).
+A step is one pass of the hot path over one synthetic state of the workload
+(inputs resident in HBM): R(u), J(u)v and J(u)^T w in FP64, the single-precision
+J(u)v of the mixed-precision inner solve, one block-Jacobi apply (FP32-stored
+inverses), the c_m recovery and one device inner product. `value` counts
+degrees of freedom times operator applications (R, J v FP64, J^T w, J v FP32,
+block apply) per second, in GDOF/s, summed over ranks. Each step is timed with
+CUDA events on the launching stream; between steps a 512 MB buffer is written
+to flush the 129 MB L2 (outside the events). The block-Jacobi setup, FGMRES and
+Newton rows run in a full solve of the cube16_p3 workload after the timed
+steps, FP64 and mixed precision, reported under `solve`.
 
 Extra keys: per-operator throughput (`ops`), the roofline of the dominant kernel
 (`roofline`), the CPU oracle on a bounded sample (`cpu_baseline`), the same
@@ -168,6 +172,39 @@ def cpu_baseline(prob, budget_s=12.0):
                       f"repeats) of {prob.name} ({prob.E} elements), {t_ops:.1f} s of CPU time"}
 
 
+def run_solves(enp, W, name):
+    """Newton with backtracking line search and block-Jacobi-preconditioned
+    FGMRES(50) (inner rtol 1e-3, as in the paper) from c = c_in, Phi = 0 to
+    ||R|| <= 1e-10 ||R_0||: FP64 throughout, then mixed (FP32 inner operator and
+    Krylov vectors, BF16 block inverses assembled in FP32) with the FP64 outer
+    residual. Wall time on the device, and the error of the mixed solution."""
+    import torch
+    prob = W.config(name)
+    op = enp.Operator(prob)
+    u0 = np.zeros((prob.n_fields, prob.E, prob.Np))
+    for k in range(1, prob.n_fields):
+        u0[k] = prob.c_in[k - 1]
+    out, sols = {"workload": name, "n_dof": prob.n_dof, "rtol": 1e-10}, {}
+    for label, kw in (("fp64", dict(bj_storage=enp.BJ_F64, mixed=False)),
+                      ("mixed", dict(bj_storage=enp.BJ_BF16, mixed=True))):
+        u = torch.tensor(u0.reshape(-1), device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.newton_solve(u, max_it=30, rtol=1e-10, krylov_restart=50, krylov_max_it=4000,
+                             krylov_rtol=1e-3, raise_on_fail=False, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sols[label] = u.cpu().numpy()
+        out[label] = {"seconds": dt, "newton_iterations": st["iterations"],
+                      "krylov_iterations": st["krylov_iterations"],
+                      "converged": bool(st["converged"]),
+                      "final_relative_residual": st["residual_norm"] / st["initial_norm"]}
+    out["mixed_vs_fp64_relative_error"] = float(
+        np.linalg.norm(sols["mixed"] - sols["fp64"]) / np.linalg.norm(sols["fp64"]))
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
@@ -204,6 +241,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--solve-workload", default="cube16_p3")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -234,11 +273,18 @@ def main():
     v = torch.tensor(W.random_vector(prob, 3), device="cuda")
     w = torch.tensor(W.random_vector(prob, 4), device="cuda")
     u32, v32 = u.float(), v.float()
-    r, jv, jtw = (torch.empty_like(u) for _ in range(3))
+    r, jv, jtw, z = (torch.empty_like(u) for _ in range(4))
     jv32 = torch.empty_like(u32)
+    cm = torch.empty(prob.E * prob.Np, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ops = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32"]
-    launches_per_step = len(ops)
+    op.block_jacobi_setup(u, enp.BJ_F32)   # preconditioner set up once, outside the steps
+    ops = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32", "bj_apply_f32", "recover_cm",
+           "inner_product"]
+    applications = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32", "bj_apply_f32"]
+    launches = {"residual_f64": 1, "jvp_f64": 1, "vjp_f64": 1, "jvp_f32": 1, "bj_apply_f32": 1,
+                "recover_cm": 1, "inner_product": 2}
+    launches_per_step = sum(launches.values())
+    ip_out = np.zeros(1)
 
     def run_op(name):
         if name == "residual_f64":
@@ -247,8 +293,16 @@ def main():
             op.jvp(u, v, out=jv)
         elif name == "vjp_f64":
             op.vjp(u, w, out=jtw)
-        else:
+        elif name == "jvp_f32":
             op.jvp_f32(u32, v32, out=jv32)
+        elif name == "bj_apply_f32":
+            op.block_jacobi_apply(v, out=z)
+        elif name == "recover_cm":
+            op.recover_cm(u, out=cm)
+        else:
+            # enp_inner_product synchronises (it returns a host value): timed as its
+            # device reduction (two launches) plus the copy of one double
+            ip_out[:] = op.inner_product(jv, jv)
 
     ev = {nm: [torch.cuda.Event(enable_timing=True) for _ in range(2)] for nm in ops}
     t_ops = {nm: 0.0 for nm in ops}
@@ -291,7 +345,7 @@ def main():
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    units = n * len(ops)
+    units = n * len(applications)
     value = world * units / (ms_step * 1e-3) / 1e9
 
     per_op = {nm: {"ms": t_ops[nm] / args.steps,
@@ -317,6 +371,14 @@ def main():
             "hbm_achieved_GBs": hbm_bytes / dom_s / 1e9, "hbm_peak_GBs": hbm,
             "hbm_frac": hbm_bytes / dom_s / 1e9 / hbm, "hbm_peak_kind": hbm_kind,
             "flops_per_launch": fl, "algorithmic_bytes_per_launch": hbm_bytes}
+    nb = prob.n_fields * prob.Np
+    bj_bytes = prob.E * (nb * nb * 4 + 2 * nb * 8)  # FP32 inverse + FP64 x in, y out
+    bj_s = t_ops["bj_apply_f32"] / args.steps * 1e-3
+    roof_hbm = {"bound": "hbm", "kernel": "bj_apply_kernel<float,float,double>",
+                "achieved": bj_bytes / bj_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": bj_bytes / bj_s / 1e9 / hbm, "peak_kind": hbm_kind,
+                "bytes_per_launch": bj_bytes,
+                "traffic": TRAFFIC.get((kh, "bj_apply_f32", prob.name))}
     f32_fl = contraction_flops(prob.dim, prob.p, prob.n_fields, "jvp") * prob.E
     f32_s = t_ops["jvp_f32"] / args.steps * 1e-3
     per_op["jvp_f32"]["fp32_TFLOPs"] = f32_fl / f32_s / 1e12
@@ -328,6 +390,7 @@ def main():
     hu, hv, hw = (x.cpu().pin_memory() for x in (u, v, w))
     hr, hj, ht = (torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3))
     hj32 = torch.empty(n, dtype=torch.float32).pin_memory()
+    hz = torch.empty(n, dtype=torch.float64).pin_memory()
     du, dv, dw = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
 
     def e2e_step():
@@ -336,8 +399,10 @@ def main():
         op.residual(du, out=r); op.jvp(du, dv, out=jv); op.vjp(du, dw, out=jtw)
         du32, dv32 = du.float(), dv.float()
         op.jvp_f32(du32, dv32, out=jv32)
+        op.block_jacobi_apply(dv, out=z)
         hr.copy_(r, non_blocking=True); hj.copy_(jv, non_blocking=True)
         ht.copy_(jtw, non_blocking=True); hj32.copy_(jv32, non_blocking=True)
+        hz.copy_(z, non_blocking=True)
 
     for _ in range(3):
         e2e_step()
@@ -354,9 +419,13 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e = {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
-           "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 3 * n * 8 + n * 4,
+           "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 4 * n * 8 + n * 4,
            "ms_per_step": e2e_ms}
 
+    del flush
+    solve = None
+    if rank == 0 and not args.no_solve:
+        solve = run_solves(enp, W, args.solve_workload)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(prob)
@@ -368,9 +437,12 @@ def main():
                 "config": {"workload": prob.name, "elements": prob.E, "p": prob.p,
                            "fields": prob.n_fields, "n_dof": prob.n_dof,
                            "n_dof_incl_cm": prob.n_dof // prob.n_fields * (prob.n_fields + 1),
-                           "step": "R f64 + J v f64 + J^T w f64 + J v f32",
+                           "step": "R f64, J v f64, J^T w f64, J v f32, block-Jacobi apply "
+                                   "(FP32 inverses), c_m recovery, inner product",
+                           "applications_per_step": len(applications),
                            "l2": "flushed between steps (512 MB write)"},
-                "ops": per_op, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "ops": per_op, "roofline": roof, "roofline_hbm": roof_hbm, "solve": solve,
+                "cpu_baseline": cb, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "kernel_hash": kh}
         print(json.dumps(line), flush=True)

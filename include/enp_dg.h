@@ -172,9 +172,11 @@ enp_status enp_inner_product(enp_handle h, const double* x, const double* y, dou
 enp_status enp_block_diagonal(enp_handle h, const double* u, double* blocks);
 
 /* Assemble and invert the element-diagonal blocks of J(u) (Gauss-Jordan with
- * partial pivoting; FP64 arithmetic for storage 0, FP32 otherwise) and keep
- * the inverses in handle-owned memory, stored as 0 = FP64, 1 = FP32, 2 = BF16.
- * Synchronises. Errors: NONFINITE if a block is singular or not finite. */
+ * partial pivoting) and keep the inverses in handle-owned memory, stored as
+ * 0 = FP64, 1 = FP32, 2 = BF16. Storage 0 assembles and inverts in FP64; 1 and 2
+ * assemble (with the FP32 operator) and invert in FP32: the preconditioner of
+ * a flexible Krylov method need not be exact. Synchronises.
+ * Errors: NONFINITE if a block is singular or not finite. */
 enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage);
 
 /* y = P^{-1} x with P the block diagonal of the last setup. x, y: [batch][m][E][Np]. */

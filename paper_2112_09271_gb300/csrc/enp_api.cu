@@ -15,6 +15,34 @@ using enp::Tables;
 
 namespace {
 
+// The physical coefficients of P in arithmetic type T (see PhysT).
+template <class T>
+void fill_phys(const OpParams& P, enp::PhysT<T>& o) {
+  std::memset(&o, 0, sizeof(o));
+  const int m = P.m;
+  for (int k = 0; k < enp::kMaxSpecies; ++k) {
+    o.D[k] = (T)P.D[k]; o.cin[k] = (T)P.cin[k]; o.mig[k] = (T)P.mig[k];
+    o.acoef[k] = (T)P.acoef[k]; o.kcoef[k] = (T)P.kcoef[k]; o.z[k] = (T)P.z[k];
+    o.zratio[k] = (T)(-P.z[k] / P.z[m - 1]);
+  }
+  o.neg_inv_zm = (T)(-1.0 / P.z[m - 1]);
+  for (int i = 0; i < 8; ++i) o.vp[i] = (T)P.vp[i];
+  o.vel_coef = (T)P.vel_coef;
+  o.vel_kind = P.vel_kind;
+  o.velA = (int)P.vp[0];
+  o.velN = (int)P.vp[1];
+  o.J0 = (T)P.J0; o.e1 = (T)P.e1; o.e2 = (T)P.e2;
+  o.gam = (T)P.gam; o.gam1 = (T)(P.gam - 1.0); o.inv_cref = (T)P.inv_cref;
+  o.ox_species_scale = (T)P.ox_species_scale; o.ox_charge_scale = (T)P.ox_charge_scale;
+  for (int j = 0; j < 4; ++j) o.phiapp[j] = (T)P.phiapp[j];
+  o.J0axis = P.J0axis;
+  o.J0lo = (T)P.J0lo;
+  o.J0half = (T)(0.5 * (P.J0hi - P.J0lo));
+  o.J0inv_half = P.J0hi > P.J0lo ? (T)(1.0 / (0.5 * (P.J0hi - P.J0lo))) : (T)0;
+  o.cip = (T)P.cip;
+  o.bv_ox = P.bv_ox;
+}
+
 enp_status fail(enp_handle h, enp_status s, const std::string& msg) {
   if (h) h->err = msg;
   return s;
@@ -253,6 +281,8 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
   P.F = ph->F;
   P.vel_kind = ph->velocity_kind;
   for (int i = 0; i < 8; ++i) P.vp[i] = ph->vel_params[i];
+  P.vel_coef = ph->velocity_kind == ENP_VEL_PLATE
+                   ? 6.0 * ph->vel_params[4] / (ph->vel_params[3] * ph->vel_params[3]) : 0.0;
   P.bv_ox = ph->bv_oxidant;
   P.J0 = ph->bv_J0;
   P.e1 = ph->bv_alpha1 * ph->bv_n * ph->F / ph->RT;
@@ -266,6 +296,8 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
   P.cip = disc->C_IP;
   P.src = nullptr; P.dirv = nullptr; P.phiapp_batch = nullptr;
   P.batch_stride = (long long)P.NF * P.E * P.Np;
+  fill_phys<double>(P, P.pd);
+  fill_phys<float>(P, P.pf);
   h->batch = disc->batch;
   h->n_dof = P.batch_stride;
   h->stream = (cudaStream_t)stream;
@@ -286,6 +318,9 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
   if (e == cudaSuccess) e = cudaMemcpy(h->d_tab, &h->htab, sizeof(Tables), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload tables"); enp_dg_destroy(h); return s; }
   P.btag = h->d_btag;
+  e = enp::prepare_tables<double>(P.p, h->htab);
+  if (e == cudaSuccess) e = enp::prepare_tables<float>(P.p, h->htab);
+  if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload constant tables"); enp_dg_destroy(h); return s; }
   *out = h;
   return ENP_OK;
 }

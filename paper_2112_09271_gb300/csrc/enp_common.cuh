@@ -23,6 +23,20 @@ enum OpMode : int { kResidual = 0, kJvp = 1, kVjp = 2, kBlockCol = 3 };
 
 enum FaceTag : int { kInterior = 0, kWall = 1, kInlet = 2, kOutlet = 3, kDirichlet = 4, kElectrode0 = 5 };
 
+// Physical coefficients in the arithmetic type T of a kernel, converted once on
+// the host so that the pointwise code does no FP64 conversions in FP32 kernels.
+template <class T>
+struct PhysT {
+  T D[kMaxSpecies], cin[kMaxSpecies], mig[kMaxSpecies], acoef[kMaxSpecies], kcoef[kMaxSpecies],
+      z[kMaxSpecies], zratio[kMaxSpecies];   // zratio_k = -z_k / z_m
+  T neg_inv_zm;                               // -1 / z_m
+  T vp[8], vel_coef;
+  T J0, e1, e2, gam, gam1, inv_cref, ox_species_scale, ox_charge_scale, phiapp[4];
+  T J0lo, J0half, J0inv_half;                 // profile: r = (x - lo - half) / half
+  T cip;
+  int vel_kind, velA, velN, bv_ox, J0axis;
+};
+
 // Everything the operator kernels read besides the vectors. Passed by value.
 struct OpParams {
   int dim, ne[3], E, NF, m, p, n, q, Np, Nq, Nfq, NBF;
@@ -36,6 +50,7 @@ struct OpParams {
   double F;
   int vel_kind;               // 0 constant, 1 plate (Poiseuille)
   double vp[8];
+  double vel_coef;            // plate flow: 6 u_avg / H^2
   // Butler-Volmer (Eq. bv), nondimensional exponent factors alpha_i n F / RT
   int bv_ox;                  // species index of the oxidant, -1 none
   double J0, e1, e2, gam, inv_cref, ox_species_scale, ox_charge_scale, phiapp[4];
@@ -46,7 +61,13 @@ struct OpParams {
   const double* dirv;         // device [NF][NBF][Nfq] or null
   const double* phiapp_batch; // device [batch][4] or null (per-operating-point phi_app)
   long long batch_stride;     // entries per operating point (NF * E * Np)
+  PhysT<double> pd;           // the coefficients above, in each kernel arithmetic type
+  PhysT<float> pf;
 };
+
+template <class R> __host__ __device__ __forceinline__ const PhysT<R>& phys(const OpParams& p);
+template <> __host__ __device__ __forceinline__ const PhysT<double>& phys<double>(const OpParams& p) { return p.pd; }
+template <> __host__ __device__ __forceinline__ const PhysT<float>& phys<float>(const OpParams& p) { return p.pf; }
 
 // Basis tables for one polynomial degree, built on the host.
 struct Tables {

@@ -15,6 +15,11 @@ cudaError_t launch_op(int mode, const OpParams& prm, const Tables* tabs, const R
 
 bool shape_supported(int dim, int p, int nf);
 
+// Upload the degree-p basis tables to the constant memory the kernels of type R
+// read (current device).
+template <class R>
+cudaError_t prepare_tables(int p, const Tables& t);
+
 }  // namespace enp
 
 struct enp_solver_ext;

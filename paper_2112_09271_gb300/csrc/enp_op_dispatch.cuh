@@ -4,12 +4,41 @@
 #pragma once
 #include "enp_internal.h"
 #include "enp_operator.cuh"
+#include "enp_operator3d.cuh"
 
 namespace enp {
+
+// Hexahedra: the thread-per-pencil kernel, EB elements per block sized so that
+// a block's shared memory stays near 96 KB.
+template <int P, int NF, int MODE, class R>
+static cudaError_t launch_3d(const OpParams& prm, const R* u, const R* v, R* out, int batch,
+                             cudaStream_t stream) {
+  using S3 = Smem3<P, NF, MODE>;
+  constexpr size_t per_el = (size_t)S3::total * sizeof(R);
+  constexpr int EBr = (int)((96 * 1024) / per_el);
+  constexpr int EB = EBr < 1 ? 1 : (EBr > 8 ? 8 : EBr);
+  constexpr int NT = (P + 2) * (P + 2);
+  const size_t smem = (size_t)EB * per_el;
+  auto kern = op3d_kernel<P, NF, MODE, EB, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((prm.E + EB - 1) / EB, batch);
+  kern<<<grid, EB * NT, smem, stream>>>(prm, u, v, out);
+  return cudaGetLastError();
+}
 
 template <int DIM, int P, int NF, int MODE, class R>
 static cudaError_t launch_one(const OpParams& prm, const Tables* tabs, const R* u, const R* v,
                               R* out, int batch, cudaStream_t stream) {
+  if constexpr (DIM == 3) {
+    (void)tabs;
+    return launch_3d<P, NF, MODE, R>(prm, u, v, out, batch, stream);
+  }
   using M = WarpSmem<DIM, P, NF, MODE>;
   constexpr size_t per_warp = (size_t)M::total * sizeof(R);
   constexpr int WPB = per_warp * 4 <= 96 * 1024 ? 4 : (per_warp * 2 <= 110 * 1024 ? 2 : 1);
@@ -45,6 +74,13 @@ static cudaError_t launch_nf(int mode, const OpParams& prm, const Tables* t, con
   if (prm.NF == 2) return launch_mode<DIM, P, 2, R>(mode, prm, t, u, v, out, batch, s);
   if (prm.NF == 3) return launch_mode<DIM, P, 3, R>(mode, prm, t, u, v, out, batch, s);
   return cudaErrorInvalidConfiguration;
+}
+
+// Upload the degree-p tables to this translation unit's constant memory on
+// the current device (idempotent: the tables depend on p only).
+template <class R>
+cudaError_t prepare_tables(int p, const Tables& t) {
+  return upload_const_tables(p, t);
 }
 
 template <class R>

@@ -55,46 +55,46 @@ struct TabSmem {
 
 // ----------------------------------------------------------------- physics
 template <class R>
-__device__ __forceinline__ void velocity(const OpParams& p, const R* x, R* uv) {
+__device__ __forceinline__ void velocity(const PhysT<R>& p, const R* x, R* uv) {
   uv[0] = uv[1] = uv[2] = R(0);
   if (p.vel_kind == 0) {
-    uv[0] = R(p.vp[0]); uv[1] = R(p.vp[1]); uv[2] = R(p.vp[2]);
+    uv[0] = p.vp[0]; uv[1] = p.vp[1]; uv[2] = p.vp[2];
   } else {  // plate flow u_A = 6 u_avg s (H - s) / H^2 (Sec. 5.2)
-    const int A = (int)p.vp[0], Nn = (int)p.vp[1];
-    const R s = x[Nn] - R(p.vp[2]), H = R(p.vp[3]);
-    uv[A] = R(6.0 * p.vp[4]) * s * (H - s) / (H * H);
+    const int A = p.velA, Nn = p.velN;
+    const R s = x[Nn] - p.vp[2], H = p.vp[3];
+    uv[A] = p.vel_coef * s * (H - s);
   }
 }
 
+// J_0 = 3/5 Jbar [2 - ((t - w/2)/(w/2))^2] (Sec. 5.2), or constant.
 template <class R>
-__device__ __forceinline__ R exchange_current(const OpParams& p, const R* x) {
-  if (p.J0axis < 0) return R(p.J0);
-  const R w = R(p.J0hi - p.J0lo), t = x[p.J0axis] - R(p.J0lo);
-  const R r = (t - R(0.5) * w) / (R(0.5) * w);
-  return R(0.6 * p.J0) * (R(2) - r * r);
+__device__ __forceinline__ R exchange_current(const PhysT<R>& p, const R* x) {
+  if (p.J0axis < 0) return p.J0;
+  const R r = (x[p.J0axis] - p.J0lo - p.J0half) * p.J0inv_half;
+  return R(0.6) * p.J0 * (R(2) - r * r);
 }
 
 // Volume flux at one point (Eq. NPDG and Eq. chargeDG volume terms): the
 // coefficient Sf of phi_i and the vector Gf multiplying grad phi_i.
 template <int NF, int DIM, class S, class R>
-__device__ __forceinline__ void volume_flux(const OpParams& p, const S* c, const S (*g)[3],
+__device__ __forceinline__ void volume_flux(const PhysT<R>& p, const S* c, const S (*g)[3],
                                             const R* uv, S* Sf, S (*Gf)[3]) {
   S kap = S(R(0));
 #pragma unroll
-  for (int k = 0; k < NF - 1; ++k) kap += R(p.kcoef[k]) * c[k + 1];
+  for (int k = 0; k < NF - 1; ++k) kap += p.kcoef[k] * c[k + 1];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     S acc = kap * g[0][d];
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) acc += R(p.acoef[k]) * g[k + 1][d];
+    for (int k = 0; k < NF - 1; ++k) acc += p.acoef[k] * g[k + 1][d];
     Gf[0][d] = acc;
   }
 #pragma unroll
   for (int k = 0; k < NF - 1; ++k)
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      const S qk = uv[d] - R(p.mig[k]) * g[0][d];
-      Gf[k + 1][d] = R(p.D[k]) * g[k + 1][d] - c[k + 1] * qk;
+      const S qk = uv[d] - p.mig[k] * g[0][d];
+      Gf[k + 1][d] = p.D[k] * g[k + 1][d] - c[k + 1] * qk;
     }
 #pragma unroll
   for (int f = 0; f < NF; ++f) Sf[f] = S(R(0));
@@ -104,12 +104,12 @@ __device__ __forceinline__ void volume_flux(const OpParams& p, const S* c, const
 // gradients GW_f (the w field at the point), the coefficients of phi_j and
 // grad phi_j for the columns (J^T w).
 template <int NF, int DIM, class R>
-__device__ __forceinline__ void volume_flux_adjoint(const OpParams& p, const R* c, const R (*g)[3],
+__device__ __forceinline__ void volume_flux_adjoint(const PhysT<R>& p, const R* c, const R (*g)[3],
                                                     const R* uv, const R (*GW)[3], R* chat,
                                                     R (*ghat)[3]) {
   R kap = R(0);
 #pragma unroll
-  for (int k = 0; k < NF - 1; ++k) kap += R(p.kcoef[k]) * c[k + 1];
+  for (int k = 0; k < NF - 1; ++k) kap += p.kcoef[k] * c[k + 1];
   R g0GW0 = R(0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) g0GW0 += g[0][d] * GW[0][d];
@@ -117,7 +117,7 @@ __device__ __forceinline__ void volume_flux_adjoint(const OpParams& p, const R* 
   for (int d = 0; d < DIM; ++d) {
     R acc = kap * GW[0][d];
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) acc += R(p.mig[k]) * c[k + 1] * GW[k + 1][d];
+    for (int k = 0; k < NF - 1; ++k) acc += p.mig[k] * c[k + 1] * GW[k + 1][d];
     ghat[0][d] = acc;
   }
   chat[0] = R(0);
@@ -126,10 +126,10 @@ __device__ __forceinline__ void volume_flux_adjoint(const OpParams& p, const R* 
     R qG = R(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      qG += (uv[d] - R(p.mig[k]) * g[0][d]) * GW[k + 1][d];
-      ghat[k + 1][d] = R(p.acoef[k]) * GW[0][d] + R(p.D[k]) * GW[k + 1][d];
+      qG += (uv[d] - p.mig[k] * g[0][d]) * GW[k + 1][d];
+      ghat[k + 1][d] = p.acoef[k] * GW[0][d] + p.D[k] * GW[k + 1][d];
     }
-    chat[k + 1] = R(p.kcoef[k]) * g0GW0 - qG;
+    chat[k + 1] = p.kcoef[k] * g0GW0 - qG;
   }
 }
 
@@ -139,7 +139,7 @@ __device__ __forceinline__ void volume_flux_adjoint(const OpParams& p, const R* 
 // normal) on this side; cp, dp on the other side. Returns the coefficient Sf
 // of phi_i and Tf of grad phi_i . n. Upwind reading: {c q}.n + |{q}.n|/2 [[c]].
 template <int NF, class S, class R>
-__device__ __forceinline__ void face_interior_flux(const OpParams& p, const S* cm, const S* dm,
+__device__ __forceinline__ void face_interior_flux(const PhysT<R>& p, const S* cm, const S* dm,
                                                    const S* cp, const S* dp, R un, R delta,
                                                    S* Sf, S* Tf) {
   S kapm = S(R(0)), kapp = S(R(0));
@@ -147,7 +147,7 @@ __device__ __forceinline__ void face_interior_flux(const OpParams& p, const S* c
 #pragma unroll
   for (int k = 0; k < NF - 1; ++k) {
     const int f = k + 1;
-    const R Dk = R(p.D[k]), mg = R(p.mig[k]), ak = R(p.acoef[k]);
+    const R Dk = p.D[k], mg = p.mig[k], ak = p.acoef[k];
     const S jc = cm[f] - cp[f];
     const S qnm = un - mg * dm[0];
     const S qnp = un - mg * dp[0];
@@ -155,8 +155,8 @@ __device__ __forceinline__ void face_interior_flux(const OpParams& p, const S* c
     Tf[f] = R(-0.5) * Dk * jc;
     Sf[f] = R(-0.5) * Dk * (dm[f] + dp[f]) + (Dk * delta) * jc +
             R(0.5) * (cm[f] * qnm + cp[f] * qnp) + R(0.5) * absv(qa) * jc;
-    kapm += R(p.kcoef[k]) * cm[f];
-    kapp += R(p.kcoef[k]) * cp[f];
+    kapm += p.kcoef[k] * cm[f];
+    kapp += p.kcoef[k] * cp[f];
     T0 += R(-0.5) * ak * jc;
     S0 += R(-0.5) * ak * (dm[f] + dp[f]);
   }
@@ -169,19 +169,19 @@ __device__ __forceinline__ void face_interior_flux(const OpParams& p, const S* c
 // given the weighted test traces Sh (value) and Th (normal derivative).
 // Accumulates into (acm, adm) for this side and (acp, adp) for the other side.
 template <int NF, class R>
-__device__ __forceinline__ void face_interior_adjoint(const OpParams& p, const R* cm, const R* dm,
+__device__ __forceinline__ void face_interior_adjoint(const PhysT<R>& p, const R* cm, const R* dm,
                                                       const R* cp, const R* dp, R un, R delta,
                                                       const R* Sh, const R* Th, R* acm, R* adm,
                                                       R* acp, R* adp) {
   R kapm = R(0), kapp = R(0);
 #pragma unroll
-  for (int k = 0; k < NF - 1; ++k) { kapm += R(p.kcoef[k]) * cm[k + 1]; kapp += R(p.kcoef[k]) * cp[k + 1]; }
+  for (int k = 0; k < NF - 1; ++k) { kapm += p.kcoef[k] * cm[k + 1]; kapp += p.kcoef[k] * cp[k + 1]; }
   const R jphi = cm[0] - cp[0];
   const R S0 = Sh[0], T0 = Th[0];
 #pragma unroll
   for (int k = 0; k < NF - 1; ++k) {
     const int f = k + 1;
-    const R Dk = R(p.D[k]), mg = R(p.mig[k]), ak = R(p.acoef[k]), kc = R(p.kcoef[k]);
+    const R Dk = p.D[k], mg = p.mig[k], ak = p.acoef[k], kc = p.kcoef[k];
     const R jc = cm[f] - cp[f];
     const R qnm = un - mg * dm[0], qnp = un - mg * dp[0];
     const R qa = R(0.5) * (qnm + qnp);
@@ -210,50 +210,50 @@ __device__ __forceinline__ void face_interior_adjoint(const OpParams& p, const R
 
 // Concentration of the Butler-Volmer oxidant (Eq. substitution if it is c_m).
 template <int NF, class S, class R>
-__device__ __forceinline__ S oxidant_conc(const OpParams& p, const S* c) {
+__device__ __forceinline__ S oxidant_conc(const PhysT<R>& p, const S* c) {
   if (p.bv_ox < NF - 1) return c[p.bv_ox + 1];
   S s = S(R(0));
 #pragma unroll
-  for (int k = 0; k < NF - 1; ++k) s += R(p.z[k]) * c[k + 1];
-  return R(-1.0 / p.z[NF - 1]) * s;
+  for (int k = 0; k < NF - 1; ++k) s += p.z[k] * c[k + 1];
+  return p.neg_inv_zm * s;
 }
 
 // Own-row flux on a boundary face (the boundary integrals of Eq. NPDG and
 // Eq. chargeDG; DIRICHLET is the Nitsche form of the interior terms with the
 // exterior state g, used for manufactured solutions).
 template <int NF, class S, class R>
-__device__ __forceinline__ void face_boundary_flux(const OpParams& p, int tag, const S* cm,
+__device__ __forceinline__ void face_boundary_flux(const PhysT<R>& p, int tag, const S* cm,
                                                    const S* dm, const R* g, R un, R delta,
                                                    const R* x, R phiapp, S* Sf, S* Tf) {
 #pragma unroll
   for (int f = 0; f < NF; ++f) { Sf[f] = S(R(0)); Tf[f] = S(R(0)); }
   if (tag == kInlet) {
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) Sf[k + 1] = S(un * R(p.cin[k]));
+    for (int k = 0; k < NF - 1; ++k) Sf[k + 1] = S(un * p.cin[k]);
   } else if (tag == kOutlet) {
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) Sf[k + 1] = (un - R(p.mig[k]) * dm[0]) * cm[k + 1];
+    for (int k = 0; k < NF - 1; ++k) Sf[k + 1] = (un - p.mig[k] * dm[0]) * cm[k + 1];
   } else if (tag >= kElectrode0) {
     if (p.bv_ox < 0) return;
     const S co = oxidant_conc<NF, S, R>(p, cm);
     const S eta = phiapp - cm[0];
-    S r = R(p.inv_cref) * co;
-    if (p.gam != 1.0) r = powv(r, R(p.gam));
-    const S Jn = exchange_current(p, x) * (expv(R(p.e1) * eta) - r * expv(R(-p.e2) * eta));
-    if (p.bv_ox < NF - 1) Sf[p.bv_ox + 1] = R(p.ox_species_scale) * Jn;
-    Sf[0] = R(p.ox_charge_scale) * Jn;
+    S r = p.inv_cref * co;
+    if (p.gam != 1.0) r = powv(r, p.gam);
+    const S Jn = exchange_current(p, x) * (expv(p.e1 * eta) - r * expv((-p.e2) * eta));
+    if (p.bv_ox < NF - 1) Sf[p.bv_ox + 1] = p.ox_species_scale * Jn;
+    Sf[0] = p.ox_charge_scale * Jn;
   } else if (tag == kDirichlet) {
     S kap = S(R(0)), T0 = S(R(0)), S0 = S(R(0));
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) {
       const int f = k + 1;
-      const R Dk = R(p.D[k]), ak = R(p.acoef[k]);
+      const R Dk = p.D[k], ak = p.acoef[k];
       const S jc = cm[f] - g[f];
-      const S qn = un - R(p.mig[k]) * dm[0];
+      const S qn = un - p.mig[k] * dm[0];
       Tf[f] = (-Dk) * jc;
       Sf[f] = (-Dk) * dm[f] + (Dk * delta) * jc + R(0.5) * (cm[f] + g[f]) * qn +
               R(0.5) * absv(qn) * jc;
-      kap += R(p.kcoef[k]) * cm[f];
+      kap += p.kcoef[k] * cm[f];
       T0 += (-ak) * jc;
       S0 += (-ak) * dm[f];
     }
@@ -265,14 +265,14 @@ __device__ __forceinline__ void face_boundary_flux(const OpParams& p, int tag, c
 
 // Adjoint of the linearised boundary own-row flux (this side only).
 template <int NF, class R>
-__device__ __forceinline__ void face_boundary_adjoint(const OpParams& p, int tag, const R* cm,
+__device__ __forceinline__ void face_boundary_adjoint(const PhysT<R>& p, int tag, const R* cm,
                                                       const R* dm, const R* g, R un, R delta,
                                                       const R* x, R phiapp, const R* Sh,
                                                       const R* Th, R* acm, R* adm) {
   if (tag == kOutlet) {
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) {
-      const R mg = R(p.mig[k]);
+      const R mg = p.mig[k];
       acm[k + 1] += (un - mg * dm[0]) * Sh[k + 1];
       adm[0] += -mg * cm[k + 1] * Sh[k + 1];
     }
@@ -280,35 +280,35 @@ __device__ __forceinline__ void face_boundary_adjoint(const OpParams& p, int tag
     if (p.bv_ox < 0) return;
     const R co = oxidant_conc<NF, R, R>(p, cm);
     const R eta = phiapp - cm[0];
-    const R E1 = expv(R(p.e1) * eta), E2 = expv(R(-p.e2) * eta);
-    R r = R(p.inv_cref) * co, drdc = R(p.inv_cref);
-    if (p.gam != 1.0) {
+    const R E1 = expv(p.e1 * eta), E2 = expv((-p.e2) * eta);
+    R r = p.inv_cref * co, drdc = p.inv_cref;
+    if (p.gam != R(1)) {
       const R rb = r;
-      r = powv(rb, R(p.gam));
-      drdc = R(p.gam) * powv(rb, R(p.gam - 1.0)) * R(p.inv_cref);
+      r = powv(rb, p.gam);
+      drdc = p.gam * powv(rb, p.gam1) * p.inv_cref;
     }
     const R J0 = exchange_current(p, x);
-    const R dJdphi = J0 * (-R(p.e1) * E1 - r * R(p.e2) * E2);
+    const R dJdphi = J0 * (-p.e1 * E1 - r * p.e2 * E2);
     const R dJdco = -J0 * E2 * drdc;
-    R Jh = R(p.ox_charge_scale) * Sh[0];
-    if (p.bv_ox < NF - 1) Jh += R(p.ox_species_scale) * Sh[p.bv_ox + 1];
+    R Jh = p.ox_charge_scale * Sh[0];
+    if (p.bv_ox < NF - 1) Jh += p.ox_species_scale * Sh[p.bv_ox + 1];
     acm[0] += Jh * dJdphi;
     if (p.bv_ox < NF - 1) {
       acm[p.bv_ox + 1] += Jh * dJdco;
     } else {
 #pragma unroll
-      for (int k = 0; k < NF - 1; ++k) acm[k + 1] += Jh * dJdco * R(-p.z[k] / p.z[NF - 1]);
+      for (int k = 0; k < NF - 1; ++k) acm[k + 1] += Jh * dJdco * p.zratio[k];
     }
   } else if (tag == kDirichlet) {
     R kap = R(0);
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) kap += R(p.kcoef[k]) * cm[k + 1];
+    for (int k = 0; k < NF - 1; ++k) kap += p.kcoef[k] * cm[k + 1];
     const R jphi = cm[0] - g[0];
     const R S0 = Sh[0], T0 = Th[0];
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) {
       const int f = k + 1;
-      const R Dk = R(p.D[k]), mg = R(p.mig[k]), ak = R(p.acoef[k]), kc = R(p.kcoef[k]);
+      const R Dk = p.D[k], mg = p.mig[k], ak = p.acoef[k], kc = p.kcoef[k];
       const R jc = cm[f] - g[f];
       const R qn = un - mg * dm[0];
       const R sg = qn > R(0) ? R(1) : (qn < R(0) ? R(-1) : R(0));
@@ -401,6 +401,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
           const R* __restrict__ v, R* __restrict__ out) {
   constexpr bool kBlk = MODE == kBlockCol;
   constexpr int MODEc = kBlk ? kJvp : MODE;  // the arithmetic of the column pass is J v
+  const PhysT<R>& ph = phys<R>(prm);
   using S = Shape<DIM, P, NF>;
   using M = WarpSmem<DIM, P, NF, MODE>;
   constexpr int N = S::N, Q = S::Q, NN = S::NN, NQ = S::NQ, FQ = S::FQ;
@@ -495,7 +496,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
     R xp[3] = {lo[0] + R(0.5) * (tX[kx] + R(1)) * h[0], lo[1] + R(0.5) * (tX[ky] + R(1)) * h[1],
                DIM == 3 ? lo[2] + R(0.5) * (tX[kz] + R(1)) * h[2] : R(0)};
     R uv[3];
-    velocity(prm, xp, uv);
+    velocity(ph, xp, uv);
     const R w = tW[kx] * tW[ky] * (DIM == 3 ? tW[kz] : R(1)) * detJ;
     R sc[3];
 #pragma unroll
@@ -511,7 +512,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
     R outS[NF], outG[NF][3];
     if (MODEc == kResidual) {
       R Sf[NF], Gf[NF][3];
-      volume_flux<NF, DIM, R, R>(prm, c0, g0, uv, Sf, Gf);
+      volume_flux<NF, DIM, R, R>(ph, c0, g0, uv, Sf, Gf);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         outS[f] = Sf[f] - (prm.src ? R(prm.src[((long long)f * prm.E + e) * NQ + pt]) : R(0));
@@ -535,7 +536,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
 #pragma unroll
           for (int a = 0; a < 3; ++a) gt[f][a] = Tan<R>(g0[f][a], g1[f][a]);
         }
-        volume_flux<NF, DIM, Tan<R>, R>(prm, ct, gt, uv, Sf, Gf);
+        volume_flux<NF, DIM, Tan<R>, R>(ph, ct, gt, uv, Sf, Gf);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           outS[f] = Sf[f].d;
@@ -543,7 +544,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
           for (int a = 0; a < 3; ++a) outG[f][a] = Gf[f][a].d;
         }
       } else {
-        volume_flux_adjoint<NF, DIM, R>(prm, c0, g0, uv, g1, outS, outG);
+        volume_flux_adjoint<NF, DIM, R>(ph, c0, g0, uv, g1, outS, outG);
         (void)c1;
       }
     }
@@ -641,12 +642,12 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
     // pointwise face fluxes
     R area = R(1);
     if (DIM == 3) area = R(0.25) * h[b0] * h[b1]; else area = R(0.5) * h[b0];
-    const R delta = R(prm.cip * P * P) / (boundary ? diag : R(0.5) * (diag + diagn));
+    const R delta = ph.cip * R(P * P) / (boundary ? diag : R(0.5) * (diag + diagn));
     const R sca = R(2) / h[a] * nrm;           // reference -> physical normal derivative, this side
     const R scn = boundary ? R(0) : R(2) / hn * nrm;  // other side, along this side's normal
     const R phiapp = (tag >= kElectrode0)
         ? (prm.phiapp_batch ? R(prm.phiapp_batch[bidx * 4 + (tag - kElectrode0)])
-                            : R(prm.phiapp[tag - kElectrode0]))
+                            : ph.phiapp[tag - kElectrode0])
         : R(0);
     for (int pt = lane; pt < FQ; pt += 32) {
       const int k1 = pt % Q, k2 = DIM == 3 ? pt / Q : 0;
@@ -655,7 +656,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
       xp[b0] = lo[b0] + R(0.5) * (tX[k1] + R(1)) * h[b0];
       if (DIM == 3) xp[b1] = lo[b1] + R(0.5) * (tX[k2] + R(1)) * h[b1]; else xp[2] = R(0);
       R uv[3];
-      velocity(prm, xp, uv);
+      velocity(ph, xp, uv);
       const R un = uv[a] * nrm;
       const R w = tW[k1] * (DIM == 3 ? tW[k2] : R(1)) * area;
       R cm[NF], dm[NF], cp[NF], dp[NF];
@@ -675,8 +676,8 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
                    ? R(prm.dirv[((long long)f * prm.NBF + bface) * prm.Nfq + pt]) : R(0);
       R oS[NF], oT[NF];
       if (MODEc == kResidual) {
-        if (boundary) face_boundary_flux<NF, R, R>(prm, tag, cm, dm, g, un, delta, xp, phiapp, oS, oT);
-        else face_interior_flux<NF, R, R>(prm, cm, dm, cp, dp, un, delta, oS, oT);
+        if (boundary) face_boundary_flux<NF, R, R>(ph, tag, cm, dm, g, un, delta, xp, phiapp, oS, oT);
+        else face_interior_flux<NF, R, R>(ph, cm, dm, cp, dp, un, delta, oS, oT);
       } else {
         R cm1[NF], dm1[NF], cp1[NF], dp1[NF];
 #pragma unroll
@@ -695,8 +696,8 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
             tm[f] = Tan<R>(cm[f], cm1[f]); tdm[f] = Tan<R>(dm[f], dm1[f]);
             tp[f] = Tan<R>(cp[f], cp1[f]); tdp[f] = Tan<R>(dp[f], dp1[f]);
           }
-          if (boundary) face_boundary_flux<NF, Tan<R>, R>(prm, tag, tm, tdm, g, un, delta, xp, phiapp, Sf, Tf);
-          else face_interior_flux<NF, Tan<R>, R>(prm, tm, tdm, tp, tdp, un, delta, Sf, Tf);
+          if (boundary) face_boundary_flux<NF, Tan<R>, R>(ph, tag, tm, tdm, g, un, delta, xp, phiapp, Sf, Tf);
+          else face_interior_flux<NF, Tan<R>, R>(ph, tm, tdm, tp, tdp, un, delta, Sf, Tf);
 #pragma unroll
           for (int f = 0; f < NF; ++f) { oS[f] = Sf[f].d; oT[f] = Tf[f].d; }
         } else {
@@ -707,9 +708,9 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
 #pragma unroll
           for (int f = 0; f < NF; ++f) { Sh[f] = cm1[f]; Th[f] = dm1[f]; acm[f] = adm[f] = acp[f] = adp[f] = R(0); }
           if (boundary) {
-            face_boundary_adjoint<NF, R>(prm, tag, cm, dm, g, un, delta, xp, phiapp, Sh, Th, acm, adm);
+            face_boundary_adjoint<NF, R>(ph, tag, cm, dm, g, un, delta, xp, phiapp, Sh, Th, acm, adm);
           } else {
-            face_interior_adjoint<NF, R>(prm, cm, dm, cp, dp, un, delta, Sh, Th, acm, adm, acp, adp);
+            face_interior_adjoint<NF, R>(ph, cm, dm, cp, dp, un, delta, Sh, Th, acm, adm, acp, adp);
             R ncm[NF], ndm[NF], ncp[NF], ndp[NF], bcm[NF], bdm[NF], bcp[NF], bdp[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -717,7 +718,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
               Sh[f] = cp1[f]; Th[f] = -dp1[f];
               bcm[f] = bdm[f] = bcp[f] = bdp[f] = R(0);
             }
-            face_interior_adjoint<NF, R>(prm, ncm, ndm, ncp, ndp, -un, delta, Sh, Th, bcm, bdm, bcp, bdp);
+            face_interior_adjoint<NF, R>(ph, ncm, ndm, ncp, ndp, -un, delta, Sh, Th, bcm, bdm, bcp, bdp);
 #pragma unroll
             for (int f = 0; f < NF; ++f) { acm[f] += bcp[f]; adm[f] -= bdp[f]; }
           }

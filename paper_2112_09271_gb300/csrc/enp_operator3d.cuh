@@ -1,0 +1,456 @@
+// The CNP DG operator on hexahedra, thread-per-pencil layout (sm_103a).
+//
+// Same arithmetic as op_kernel (enp_operator.cuh: R(u), J(u)v, J(u)^T w and
+// block columns of Eq. NPDG / Eq. chargeDG), organised for throughput:
+//  * Q x Q threads per element, EB elements per thread block;
+//  * every 1D contraction is done by one thread per pencil: it loads the
+//    pencil into registers and forms all outputs with the basis table in
+//    __constant__ memory at compile-time indices (the table entries become
+//    FMA operands, no loads);
+//  * each stage runs over all fields and vectors of the element at once, so a
+//    stage costs one __syncthreads;
+//  * the pointwise physics (volume and faces) is the one op_kernel uses.
+#pragma once
+#include <type_traits>
+
+#include "enp_operator.cuh"
+
+namespace enp {
+
+constexpr int kTabSz = 96;  // per degree: B (Q*N), Dq (Q*Q), dL (2N), wq (Q), xq (Q)
+static __constant__ double c_tabd[kMaxP + 1][kTabSz];
+static __constant__ float c_tabf[kMaxP + 1][kTabSz];
+
+// Upload the tables of degree p to this translation unit's constant banks on
+// the current device.
+static inline cudaError_t upload_const_tables(int p, const Tables& t) {
+  const int n = p + 1, q = p + 2;
+  double d[kTabSz] = {0};
+  float f[kTabSz] = {0};
+  int o = 0;
+  for (int i = 0; i < q * n; ++i) d[o++] = t.B[i];
+  for (int i = 0; i < q * q; ++i) d[o++] = t.Dq[i];
+  for (int i = 0; i < 2 * n; ++i) d[o++] = t.dL[i];
+  for (int i = 0; i < q; ++i) d[o++] = t.wq[i];
+  for (int i = 0; i < q; ++i) d[o++] = t.xq[i];
+  for (int i = 0; i < kTabSz; ++i) f[i] = (float)d[i];
+  cudaError_t e = cudaMemcpyToSymbol(c_tabd, d, sizeof(d), sizeof(d) * p);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tabf, f, sizeof(f), sizeof(f) * p);
+  return e;
+}
+
+template <int P, class R>
+__device__ __forceinline__ R ctab(int i) {
+  if constexpr (std::is_same<R, double>::value) return c_tabd[P][i];
+  else return c_tabf[P][i];
+}
+template <int P> struct TabOff {
+  static constexpr int N = P + 1, Q = P + 2;
+  static constexpr int B = 0, Dq = Q * N, dL = Q * N + Q * Q, W = dL + 2 * N, X = W + Q;
+};
+
+// One thread per pencil: out = M in along direction DIR of a 3D array with
+// input extents (E0, E1, E2); M is the B table (TAB 0, ROWS x COLS = Q x N, or
+// its transpose) or the Dq table (TAB 1, Q x Q). CNT arrays (stride IN_ST in
+// the input, OUT_ST in the output) are processed, pencils shared over the
+// NT threads of the element.
+template <int P, int E0, int E1, int E2, int DIR, int TAB, bool TRANS, bool ACC, int CNT,
+          int IN_ST, int OUT_ST, class R>
+__device__ __forceinline__ void pencil(const R* __restrict__ in, R* __restrict__ out, int tid,
+                                       int NT) {
+  using T = TabOff<P>;
+  constexpr int COLS = DIR == 0 ? E0 : (DIR == 1 ? E1 : E2);
+  constexpr int ROWS = TAB == 0 ? (TRANS ? T::N : T::Q) : T::Q;
+  constexpr int O0 = DIR == 0 ? ROWS : E0, O1 = DIR == 1 ? ROWS : E1, O2 = DIR == 2 ? ROWS : E2;
+  constexpr int IS = DIR == 0 ? 1 : (DIR == 1 ? E0 : E0 * E1);
+  constexpr int OS = DIR == 0 ? 1 : (DIR == 1 ? O0 : O0 * O1);
+  constexpr int PA = DIR == 0 ? O1 : O0;          // pencil index ranges over the other dims
+  constexpr int PB = DIR == 2 ? O1 : O2;
+  constexpr int NP = PA * PB;
+#pragma unroll 1
+  for (int w = tid; w < NP * CNT; w += NT) {
+    const int c = w / NP, pp = w % NP;
+    const int ia = pp % PA, ib = pp / PA;
+    int ibase, obase;
+    if (DIR == 0) { ibase = E0 * (ia + E1 * ib); obase = O0 * (ia + O1 * ib); }
+    else if (DIR == 1) { ibase = ia + E0 * E1 * ib; obase = ia + O0 * O1 * ib; }
+    else { ibase = ia + E0 * ib; obase = ia + O0 * ib; }
+    const R* src = in + c * IN_ST + ibase;
+    R* dst = out + c * OUT_ST + obase;
+    R x[COLS];
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) x[k] = src[k * IS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      R acc = ACC ? dst[r * OS] : R(0);
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        int idx;
+        if (TAB == 0) idx = T::B + (TRANS ? k * T::N + r : r * T::N + k);
+        else idx = T::Dq + (TRANS ? k * T::Q + r : r * T::Q + k);
+        acc = mad(ctab<P, R>(idx), x[k], acc);
+      }
+      dst[r * OS] = acc;
+    }
+  }
+}
+
+template <int P, int NF, int MODE>
+struct Smem3 {
+  static constexpr int N = P + 1, Q = P + 2;
+  static constexpr int NN = N * N * N, NQ = Q * Q * Q, FN = N * N, FQ = Q * Q;
+  static constexpr int NV = MODE == kResidual ? 1 : 2;
+  static constexpr int NA = NV * NF;                     // arrays carried through the volume
+  static constexpr int kX = NA * NN;                     // element data
+  static constexpr int kOut = NF * NN;                   // rows
+  static constexpr int kT1 = NA * Q * N * N;             // after the x contraction
+  static constexpr int kT2 = NA * Q * Q * N;             // after the y contraction
+  static constexpr int kPts = NA * 4 * NQ;               // values + 3 gradients
+  static constexpr int kFace = NA * NN                    // neighbour data
+                               + 2 * NA * 2 * FN          // layer values + normal derivatives
+                               + 2 * NA * 2 * Q * N       // after the first face contraction
+                               + 2 * NA * 2 * FQ          // traces at face points
+                               + 2 * NF * FQ              // face coefficients
+                               + 2 * NF * Q * N           // transposed, first stage
+                               + 2 * NF * FN;             // transposed, at face nodes
+  static constexpr int kVol = kT1 + kT2 + kPts;
+  static constexpr int kWork = kVol > kFace ? kVol : kFace;
+  static constexpr int total = kX + kOut + kWork;
+};
+
+template <int P, int NF, int MODE, int EB, class R>
+__global__ void __launch_bounds__(EB * (P + 2) * (P + 2))
+op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v,
+            R* __restrict__ out) {
+  using S = Smem3<P, NF, MODE>;
+  using TO = TabOff<P>;
+  constexpr int N = S::N, Q = S::Q, NN = S::NN, NQ = S::NQ, FN = S::FN, FQ = S::FQ;
+  constexpr int NV = S::NV, NA = S::NA, NT = Q * Q;
+  constexpr bool kBlk = MODE == kBlockCol;
+  constexpr int MODEc = kBlk ? kJvp : MODE;
+  const PhysT<R>& ph = phys<R>(prm);
+  extern __shared__ __align__(16) unsigned char smem3_raw[];
+  const int es = threadIdx.x / NT, tid = threadIdx.x % NT;
+  R* base = reinterpret_cast<R*>(smem3_raw) + es * S::total;
+  R* XA = base;                 // [NA][NN]
+  R* RO = XA + S::kX;           // [NF][NN]
+  R* WK = RO + S::kOut;
+  const int e = blockIdx.x * EB + es;
+  const bool valid = e < prm.E;
+  const int ee = valid ? e : prm.E - 1;   // invalid slots shadow a valid element, write nothing
+  const int col = kBlk ? (int)blockIdx.y : -1;
+  const long long boff = kBlk ? 0 : (long long)blockIdx.y * prm.batch_stride;
+  const int bidx = kBlk ? 0 : (int)blockIdx.y;
+  const long long EN = (long long)prm.E * NN;
+
+  int idx[3];
+  idx[0] = ee % prm.ne[0];
+  idx[1] = (ee / prm.ne[0]) % prm.ne[1];
+  idx[2] = ee / (prm.ne[0] * prm.ne[1]);
+  R lo[3], h[3], sc[3];
+  R diag2 = R(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = R(prm.xv[a][idx[a]]);
+    h[a] = R(prm.xv[a][idx[a] + 1]) - lo[a];
+    sc[a] = R(2) / h[a];
+    diag2 += h[a] * h[a];
+  }
+  const R diag = sqrt(diag2);
+  const R detJ = R(0.125) * h[0] * h[1] * h[2];
+
+  for (int t = tid; t < NF * NN; t += NT) {
+    const int f = t / NN, i = t % NN;
+    const long long gi = boff + f * EN + (long long)ee * NN + i;
+    XA[t] = u[gi];
+    if (NV == 2) XA[NF * NN + t] = kBlk ? R(t == col ? 1 : 0) : v[gi];
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- volume
+  R* T1 = WK;                   // [NA][N][N][Q]
+  R* T2 = T1 + S::kT1;          // [NA][N][Q][Q]
+  R* PT = T2 + S::kT2;          // [NA][4][NQ]
+  pencil<P, N, N, N, 0, 0, false, false, NA, NN, Q * N * N>(XA, T1, tid, NT);
+  __syncthreads();
+  pencil<P, Q, N, N, 1, 0, false, false, NA, Q * N * N, Q * Q * N>(T1, T2, tid, NT);
+  __syncthreads();
+  pencil<P, Q, Q, N, 2, 0, false, false, NA, Q * Q * N, 4 * NQ>(T2, PT, tid, NT);
+  __syncthreads();
+  pencil<P, Q, Q, Q, 0, 1, false, false, NA, 4 * NQ, 4 * NQ>(PT, PT + NQ, tid, NT);
+  pencil<P, Q, Q, Q, 1, 1, false, false, NA, 4 * NQ, 4 * NQ>(PT, PT + 2 * NQ, tid, NT);
+  pencil<P, Q, Q, Q, 2, 1, false, false, NA, 4 * NQ, 4 * NQ>(PT, PT + 3 * NQ, tid, NT);
+  __syncthreads();
+
+  {
+    const int kx = tid % Q, ky = tid / Q;
+    const R wxy = ctab<P, R>(TO::W + kx) * ctab<P, R>(TO::W + ky) * detJ;
+    R xp[3];
+    xp[0] = lo[0] + R(0.5) * (ctab<P, R>(TO::X + kx) + R(1)) * h[0];
+    xp[1] = lo[1] + R(0.5) * (ctab<P, R>(TO::X + ky) + R(1)) * h[1];
+#pragma unroll 1
+    for (int kz = 0; kz < Q; ++kz) {
+      const int pt = kx + Q * (ky + Q * kz);
+      xp[2] = lo[2] + R(0.5) * (ctab<P, R>(TO::X + kz) + R(1)) * h[2];
+      R uv[3];
+      velocity(ph, xp, uv);
+      const R w = wxy * ctab<P, R>(TO::W + kz);
+      R c0[NF], g0[NF][3];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const R* V = PT + f * 4 * NQ;
+        c0[f] = V[pt];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g0[f][a] = V[(1 + a) * NQ + pt] * sc[a];
+      }
+      R oS[NF], oG[NF][3];
+      if (MODEc == kResidual) {
+        volume_flux<NF, 3, R, R>(ph, c0, g0, uv, oS, oG);
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          oS[f] -= prm.src ? R(prm.src[((long long)f * prm.E + ee) * NQ + pt]) : R(0);
+      } else {
+        R c1[NF], g1[NF][3];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const R* V = PT + (NF + f) * 4 * NQ;
+          c1[f] = V[pt];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) g1[f][a] = V[(1 + a) * NQ + pt] * sc[a];
+        }
+        if (MODEc == kJvp) {
+          Tan<R> ct[NF], gt[NF][3], Sf[NF], Gf[NF][3];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            ct[f] = Tan<R>(c0[f], c1[f]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) gt[f][a] = Tan<R>(g0[f][a], g1[f][a]);
+          }
+          volume_flux<NF, 3, Tan<R>, R>(ph, ct, gt, uv, Sf, Gf);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            oS[f] = Sf[f].d;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) oG[f][a] = Gf[f][a].d;
+          }
+        } else {
+          volume_flux_adjoint<NF, 3, R>(ph, c0, g0, uv, g1, oS, oG);
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        R* V = PT + ((NV - 1) * NF + f) * 4 * NQ;
+        V[pt] = w * oS[f];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) V[(1 + a) * NQ + pt] = w * sc[a] * oG[f][a];
+      }
+    }
+  }
+  __syncthreads();
+  R* PO = PT + (NV - 1) * NF * 4 * NQ;   // the NF output point arrays
+  pencil<P, Q, Q, Q, 0, 1, true, true, NF, 4 * NQ, 4 * NQ>(PO + NQ, PO, tid, NT);
+  __syncthreads();
+  pencil<P, Q, Q, Q, 1, 1, true, true, NF, 4 * NQ, 4 * NQ>(PO + 2 * NQ, PO, tid, NT);
+  __syncthreads();
+  pencil<P, Q, Q, Q, 2, 1, true, true, NF, 4 * NQ, 4 * NQ>(PO + 3 * NQ, PO, tid, NT);
+  __syncthreads();
+  pencil<P, Q, Q, Q, 2, 0, true, false, NF, 4 * NQ, Q * Q * N>(PO, T2, tid, NT);
+  __syncthreads();
+  pencil<P, Q, Q, N, 1, 0, true, false, NF, Q * Q * N, Q * N * N>(T2, T1, tid, NT);
+  __syncthreads();
+  pencil<P, Q, N, N, 0, 0, true, false, NF, Q * N * N, NN>(T1, RO, tid, NT);
+  __syncthreads();
+
+  // ---------------------------------------------------------------- faces
+  R* XN = WK;                                  // [NA][NN] neighbour data
+  R* FL = XN + NA * NN;                        // [2 sides][NA][2][FN] layer values, derivatives
+  R* F1 = FL + 2 * NA * 2 * FN;                // [2][NA][2][Q][N]
+  R* TR = F1 + 2 * NA * 2 * Q * N;             // [2][NA][2][FQ]
+  R* FC = TR + 2 * NA * 2 * FQ;                // [2][NF][FQ]: S then T coefficients
+  R* G1 = FC + 2 * NF * FQ;                    // [2][NF][N][Q]
+  R* G2 = G1 + 2 * NF * Q * N;                 // [2][NF][FN]
+  const int stride[3] = {1, prm.ne[0], prm.ne[0] * prm.ne[1]};
+#pragma unroll 1
+  for (int s = 0; s < 6; ++s) {
+    const int a = s >> 1, hi = s & 1;
+    const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+    const R nrm = hi ? R(1) : R(-1);
+    const bool boundary = hi ? (idx[a] == prm.ne[a] - 1) : (idx[a] == 0);
+    int tag = kInterior, bface = -1;
+    R hn = h[a], diagn = diag;
+    if (boundary) {
+      const int loc = idx[b0] + prm.ne[b0] * idx[b1];
+      bface = prm.side_off[s] + loc;
+      tag = prm.btag[bface];
+    } else {
+      const int en = ee + (hi ? stride[a] : -stride[a]);
+      int in3[3] = {idx[0], idx[1], idx[2]};
+      in3[a] += hi ? 1 : -1;
+      R d2 = R(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const R hc = R(prm.xv[c][in3[c] + 1]) - R(prm.xv[c][in3[c]]);
+        d2 += hc * hc;
+        if (c == a) hn = hc;
+      }
+      diagn = sqrt(d2);
+      for (int t = tid; t < NF * NN; t += NT) {
+        const int f = t / NN, i = t % NN;
+        const long long gi = boff + f * EN + (long long)en * NN + i;
+        XN[t] = u[gi];
+        if (NV == 2) XN[NF * NN + t] = kBlk ? R(0) : v[gi];
+      }
+    }
+    const bool active = !(tag == kWall || (tag == kInlet && MODEc != kResidual));
+    __syncthreads();
+    // layer values and reference normal derivatives at the face nodes
+    const int lay = hi ? N - 1 : 0, layo = hi ? 0 : N - 1;
+    const int nsides = boundary ? 1 : 2;
+    for (int w = tid; w < nsides * NA * FN; w += NT) {
+      const int side = w / (NA * FN), r = w % (NA * FN), arr = r / FN, j = r % FN;
+      const int j1 = j % N, j2 = j / N;
+      const R* X = (side == 0 ? XA : XN) + arr * NN;
+      const int L = side == 0 ? lay : layo;
+      const int dsel = side == 0 ? hi : 1 - hi;
+      R d = R(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        d = mad(ctab<P, R>(TO::dL + dsel * N + k), X[face_node<3, N>(a, k, j1, j2)], d);
+      R* o = FL + ((side * NA + arr) * 2) * FN;
+      o[j] = X[face_node<3, N>(a, L, j1, j2)];
+      o[FN + j] = d;
+    }
+    __syncthreads();
+    // 2D interpolation to the face Gauss points: along b0, then b1. Both sides
+    // are always processed so that every thread reaches every barrier; on a
+    // boundary face the second side holds stale values that are never read.
+    pencil<P, N, N, 1, 0, 0, false, false, 4 * NA, FN, Q * N>(FL, F1, tid, NT);
+    __syncthreads();
+    pencil<P, Q, N, 1, 1, 0, false, false, 4 * NA, Q * N, FQ>(F1, TR, tid, NT);
+    __syncthreads();
+    // pointwise face fluxes, one thread per face point
+    {
+      const R area = R(0.25) * h[b0] * h[b1];
+      const R delta = ph.cip * R(P * P) / (boundary ? diag : R(0.5) * (diag + diagn));
+      const R sca = sc[a] * nrm;
+      const R scn = R(2) / hn * nrm;
+      const R phiapp = (tag >= kElectrode0)
+          ? (prm.phiapp_batch ? R(prm.phiapp_batch[bidx * 4 + (tag - kElectrode0)])
+                              : ph.phiapp[tag - kElectrode0])
+          : R(0);
+      const int pt = tid;  // NT == FQ
+      const int k1 = pt % Q, k2 = pt / Q;
+      R xp[3];
+      xp[a] = hi ? lo[a] + h[a] : lo[a];
+      xp[b0] = lo[b0] + R(0.5) * (ctab<P, R>(TO::X + k1) + R(1)) * h[b0];
+      xp[b1] = lo[b1] + R(0.5) * (ctab<P, R>(TO::X + k2) + R(1)) * h[b1];
+      R uv[3];
+      velocity(ph, xp, uv);
+      const R un = uv[a] * nrm;
+      const R w = ctab<P, R>(TO::W + k1) * ctab<P, R>(TO::W + k2) * area;
+      auto trv = [&](int side, int vv, int f, int comp) -> R {
+        return TR[(((side * NA) + vv * NF + f) * 2 + comp) * FQ + pt];
+      };
+      R cm[NF], dm[NF], cp[NF], dp[NF], g[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        cm[f] = trv(0, 0, f, 0);
+        dm[f] = trv(0, 0, f, 1) * sca;
+        cp[f] = boundary ? R(0) : trv(1, 0, f, 0);
+        dp[f] = boundary ? R(0) : trv(1, 0, f, 1) * scn;
+        g[f] = (tag == kDirichlet && prm.dirv)
+                   ? R(prm.dirv[((long long)f * prm.NBF + bface) * prm.Nfq + pt]) : R(0);
+      }
+      R oS[NF], oT[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) { oS[f] = R(0); oT[f] = R(0); }
+      if (active) {
+        if (MODEc == kResidual) {
+          if (boundary) face_boundary_flux<NF, R, R>(ph, tag, cm, dm, g, un, delta, xp, phiapp, oS, oT);
+          else face_interior_flux<NF, R, R>(ph, cm, dm, cp, dp, un, delta, oS, oT);
+        } else {
+          R cm1[NF], dm1[NF], cp1[NF], dp1[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            cm1[f] = trv(0, 1, f, 0);
+            dm1[f] = trv(0, 1, f, 1) * sca;
+            cp1[f] = boundary ? R(0) : trv(1, 1, f, 0);
+            dp1[f] = boundary ? R(0) : trv(1, 1, f, 1) * scn;
+          }
+          if (MODEc == kJvp) {
+            Tan<R> tm[NF], tdm[NF], tp[NF], tdp[NF], Sf[NF], Tf[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              tm[f] = Tan<R>(cm[f], cm1[f]); tdm[f] = Tan<R>(dm[f], dm1[f]);
+              tp[f] = Tan<R>(cp[f], cp1[f]); tdp[f] = Tan<R>(dp[f], dp1[f]);
+            }
+            if (boundary) face_boundary_flux<NF, Tan<R>, R>(ph, tag, tm, tdm, g, un, delta, xp, phiapp, Sf, Tf);
+            else face_interior_flux<NF, Tan<R>, R>(ph, tm, tdm, tp, tdp, un, delta, Sf, Tf);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) { oS[f] = Sf[f].d; oT[f] = Tf[f].d; }
+          } else {
+            R Sh[NF], Th[NF], acm[NF], adm[NF], acp[NF], adp[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) { Sh[f] = cm1[f]; Th[f] = dm1[f]; acm[f] = adm[f] = acp[f] = adp[f] = R(0); }
+            if (boundary) {
+              face_boundary_adjoint<NF, R>(ph, tag, cm, dm, g, un, delta, xp, phiapp, Sh, Th, acm, adm);
+            } else {
+              face_interior_adjoint<NF, R>(ph, cm, dm, cp, dp, un, delta, Sh, Th, acm, adm, acp, adp);
+              R ncm[NF], ndm[NF], ncp[NF], ndp[NF], bcm[NF], bdm[NF], bcp[NF], bdp[NF];
+#pragma unroll
+              for (int f = 0; f < NF; ++f) {
+                ncm[f] = cp[f]; ndm[f] = -dp[f]; ncp[f] = cm[f]; ndp[f] = -dm[f];
+                Sh[f] = cp1[f]; Th[f] = -dp1[f];
+                bcm[f] = bdm[f] = bcp[f] = bdp[f] = R(0);
+              }
+              face_interior_adjoint<NF, R>(ph, ncm, ndm, ncp, ndp, -un, delta, Sh, Th, bcm, bdm, bcp, bdp);
+#pragma unroll
+              for (int f = 0; f < NF; ++f) { acm[f] += bcp[f]; adm[f] -= bdp[f]; }
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) { oS[f] = acm[f]; oT[f] = adm[f]; }
+          }
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        FC[f * FQ + pt] = w * oS[f];
+        FC[(NF + f) * FQ + pt] = w * sca * oT[f];
+      }
+    }
+    __syncthreads();
+    // transposed 2D contraction back to the face nodes, then into the rows
+    pencil<P, Q, Q, 1, 1, 0, true, false, 2 * NF, FQ, Q * N>(FC, G1, tid, NT);
+    __syncthreads();
+    pencil<P, Q, N, 1, 0, 0, true, false, 2 * NF, Q * N, FN>(G1, G2, tid, NT);
+    __syncthreads();
+    for (int w = tid; w < NF * FN; w += NT) {
+      const int f = w / FN, j = w % FN, j1 = j % N, j2 = j / N;
+      R* Rf = RO + f * NN;
+      const R sv = G2[f * FN + j], tv = G2[(NF + f) * FN + j];
+      if (active) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          R add = ctab<P, R>(TO::dL + hi * N + k) * tv;
+          if (k == lay) add += sv;
+          Rf[face_node<3, N>(a, k, j1, j2)] += add;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (valid) {
+    if (kBlk) {
+      const long long nb = NF * NN;
+      for (int t = tid; t < NF * NN; t += NT) out[((long long)e * nb + t) * nb + col] = RO[t];
+    } else {
+      for (int t = tid; t < NF * NN; t += NT) {
+        const int f = t / NN, i = t % NN;
+        out[boff + f * EN + (long long)e * NN + i] = RO[t];
+      }
+    }
+  }
+}
+
+}  // namespace enp

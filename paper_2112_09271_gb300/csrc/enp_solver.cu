@@ -166,8 +166,8 @@ __global__ void count_nonfinite(const double* __restrict__ x, long long n, int* 
 // (SMEM = true) else in global memory. Row swaps are undone at the end as
 // column swaps in reverse order. A zero or non-finite pivot sets *singular.
 // The inverse is written transposed (out[e][c][r] = inv[r][c]) in type TS.
-template <class T, class TS, bool SMEM>
-__global__ void gj_invert(const double* __restrict__ blocks, T* __restrict__ work, TS* __restrict__ out,
+template <class T, class TS, bool SMEM, class TB>
+__global__ void gj_invert(const TB* __restrict__ blocks, T* __restrict__ work, TS* __restrict__ out,
                           int n, int* __restrict__ singular) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const long long e = blockIdx.x;
@@ -180,7 +180,7 @@ __global__ void gj_invert(const double* __restrict__ blocks, T* __restrict__ wor
   __shared__ int s_p;
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const double* src = blocks + e * nn;
+  const TB* src = blocks + e * nn;
   for (long long t = tid; t < nn; t += nt) A[t] = (T)src[t];
   if (tid == 0) s_bad = 0;
   __syncthreads();
@@ -293,7 +293,10 @@ struct SolverState {
   // block-Jacobi
   int nb = 0;
   int storage = -1;               // 0 f64, 1 f32, 2 bf16
-  double* blocks = nullptr;       // [batch][E][nb][nb] assembled blocks (FP64)
+  double* blocks = nullptr;       // [batch][E][nb][nb] assembled blocks (FP64 setup)
+  float* blocks32 = nullptr;      // [batch][E][nb][nb] assembled blocks (FP32 setup)
+  float* u32 = nullptr;           // the linearisation point in FP32
+  size_t blocks32_count = 0, u32_count = 0;
   void* binv = nullptr;           // [batch][E][nb][nb] inverse, transposed, in `storage`
   void* gj_work = nullptr;        // global work for blocks too large for shared memory
   size_t gj_work_bytes = 0;
@@ -364,6 +367,7 @@ void enp_solver_free(enp_handle h) {
   if (!h || !h->solver) return;
   SolverState& S = h->solver->s;
   cudaFree(S.blocks); cudaFree(S.binv); cudaFree(S.gj_work); cudaFree(S.d_flag);
+  cudaFree(S.blocks32); cudaFree(S.u32);
   cudaFree(S.part); cudaFree(S.dsmall); cudaFree(S.V);
   delete h->solver;
   h->solver = nullptr;
@@ -416,13 +420,8 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
   const int nb = P.NF * P.Np;
   const long long nblk = (long long)h->batch * P.E;
   const size_t nn = (size_t)nb * nb;
+  const bool f64 = storage == 0;  // FP64 storage: FP64 assembly and inversion; else FP32
   cudaError_t e;
-  if (!S.blocks || S.nb != nb) {
-    cudaFree(S.blocks);
-    S.blocks = nullptr;
-    e = cudaMalloc(&S.blocks, sizeof(double) * nn * nblk);
-    if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc blocks");
-  }
   const size_t esz = storage == 0 ? 8 : (storage == 1 ? 4 : 2);
   if (!S.binv || S.nb != nb || S.storage != storage) {
     cudaFree(S.binv);
@@ -430,17 +429,38 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     e = cudaMalloc(&S.binv, esz * nn * nblk);
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc block inverses");
   }
-  S.nb = nb;
-  S.storage = storage;
   if (!S.d_flag) {
     e = cudaMalloc(&S.d_flag, sizeof(int));
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc flag");
   }
-  enp_status st = enp_block_diagonal(h, u, S.blocks);
-  if (st != ENP_OK) return st;
+  if (f64) {
+    if (!S.blocks || S.nb != nb) {
+      cudaFree(S.blocks);
+      S.blocks = nullptr;
+      e = cudaMalloc(&S.blocks, sizeof(double) * nn * nblk);
+      if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc blocks");
+    }
+    S.nb = nb;
+    enp_status st = enp_block_diagonal(h, u, S.blocks);
+    if (st != ENP_OK) return st;
+  } else {
+    const long long ntot = h->n_dof * h->batch;
+    if ((e = ensure(&S.blocks32, S.blocks32_count, nn * nblk)) != cudaSuccess ||
+        (e = ensure(&S.u32, S.u32_count, (size_t)ntot)) != cudaSuccess)
+      return cuda_err(h, e, "cudaMalloc FP32 blocks");
+    S.nb = nb;
+    enp::convert_kernel<double, float><<<grid_for(ntot), 256, 0, h->stream>>>(u, S.u32, ntot);
+    const long long bsz = (long long)P.E * nb * nb;
+    for (int b = 0; b < h->batch; ++b) {
+      OpParams Pb = P;
+      if (P.phiapp_batch) Pb.phiapp_batch = P.phiapp_batch + 4 * b;
+      e = enp::launch_op<float>(enp::kBlockCol, Pb, h->d_tab, S.u32 + b * P.batch_stride, nullptr,
+                                S.blocks32 + b * bsz, nb, h->stream);
+      if (e != cudaSuccess) return cuda_err(h, e, "FP32 block columns");
+    }
+  }
+  S.storage = storage;
   cudaMemsetAsync(S.d_flag, 0, sizeof(int), h->stream);
-  // the factorisation runs in FP64 for FP64 storage, else in FP32
-  const bool f64 = storage == 0;
   const size_t telt = f64 ? 8 : 4;
   const size_t smem_full = telt * (nn + nb) + sizeof(int) * nb;
   const bool in_smem = smem_full <= 200 * 1024;
@@ -450,19 +470,24 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc inversion work");
   }
   const size_t smem = in_smem ? smem_full : telt * nb + sizeof(int) * nb;
-#define ENP_GJ(T, TS, SM)                                                                        \
+#define ENP_GJ(T, TS, SM, TB, SRC)                                                              \
   {                                                                                             \
-    auto k = enp::gj_invert<T, TS, SM>;                                                         \
+    auto k = enp::gj_invert<T, TS, SM, TB>;                                                     \
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
     if (e == cudaSuccess) {                                                                     \
-      k<<<(unsigned)nblk, threads, smem, h->stream>>>(S.blocks, (T*)S.gj_work, (TS*)S.binv, nb, \
+      k<<<(unsigned)nblk, threads, smem, h->stream>>>(SRC, (T*)S.gj_work, (TS*)S.binv, nb,      \
                                                       S.d_flag);                                \
       e = cudaGetLastError();                                                                   \
     }                                                                                           \
   }
-  if (storage == 0) { if (in_smem) ENP_GJ(double, double, true) else ENP_GJ(double, double, false) }
-  else if (storage == 1) { if (in_smem) ENP_GJ(float, float, true) else ENP_GJ(float, float, false) }
-  else { if (in_smem) ENP_GJ(float, __nv_bfloat16, true) else ENP_GJ(float, __nv_bfloat16, false) }
+  if (storage == 0) {
+    if (in_smem) ENP_GJ(double, double, true, double, S.blocks) else ENP_GJ(double, double, false, double, S.blocks)
+  } else if (storage == 1) {
+    if (in_smem) ENP_GJ(float, float, true, float, S.blocks32) else ENP_GJ(float, float, false, float, S.blocks32)
+  } else {
+    if (in_smem) ENP_GJ(float, __nv_bfloat16, true, float, S.blocks32)
+    else ENP_GJ(float, __nv_bfloat16, false, float, S.blocks32)
+  }
 #undef ENP_GJ
   if (e != cudaSuccess) return cuda_err(h, e, "block inversion");
   int flag = 0;

@@ -3,3 +3,4 @@
 #include "enp_op_dispatch.cuh"
 template cudaError_t enp::launch_op<float>(int, const OpParams&, const Tables*, const float*,
                                            const float*, float*, int, cudaStream_t);
+template cudaError_t enp::prepare_tables<float>(int, const Tables&);

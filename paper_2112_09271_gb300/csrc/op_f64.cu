@@ -2,3 +2,4 @@
 #include "enp_op_dispatch.cuh"
 template cudaError_t enp::launch_op<double>(int, const OpParams&, const Tables*, const double*,
                                             const double*, double*, int, cudaStream_t);
+template cudaError_t enp::prepare_tables<double>(int, const Tables&);
