@@ -13,6 +13,8 @@
 //  * Newton's method with backtracking line search on ||R|| (Sec. 4).
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -51,7 +53,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Partial sums of nd dot products <V_i, w> (i < nd) over each batch item:
-// part[b][i][block]. V_i = V + i * vstride. Fixed reduction order.
+// part[b][i][block]. V_i = V + i * vstride. Each thread accumulates in the
+// vector's own precision (FP32 vectors: FP32, no conversions on the FP64 pipe),
+// then the warp and block trees run in FP64. Fixed reduction order.
 template <class T>
 __global__ void __launch_bounds__(kRedThreads)
 multidot_partial(const T* __restrict__ V, long long vstride, int nd, const T* __restrict__ w,
@@ -62,20 +66,20 @@ multidot_partial(const T* __restrict__ V, long long vstride, int nd, const T* __
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = 0; i0 < nd; i0 += 32) {
     const int ni = min(32, nd - i0);
-    double acc[32];
+    T acc[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 32; ++i) acc[i] = T(0);
     for (long long k = blockIdx.x * (long long)kRedThreads + threadIdx.x; k < n;
          k += (long long)gridDim.x * kRedThreads) {
-      const double wk = (double)wb[k];
+      const T wk = wb[k];
 #pragma unroll
       for (int i = 0; i < 32; ++i)
-        if (i < ni) acc[i] += (double)V[(i0 + i) * vstride + b * bstride + k] * wk;
+        if (i < ni) acc[i] += V[(i0 + i) * vstride + b * bstride + k] * wk;
     }
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       if (i >= ni) break;
-      double s = warp_sum(acc[i]);
+      double s = warp_sum((double)acc[i]);
       if (lane == 0) red[warp][i] = s;
     }
     __syncthreads();
@@ -99,44 +103,53 @@ __global__ void finish_partials(const double* __restrict__ part, int nparts, int
   if (threadIdx.x == 0) out[i] = s;
 }
 
-// w[b] -= sum_i V_i[b] h[b][i]  (h on the device, [batch][nd])
+// w[b] -= sum_i V_i[b] h[b][i]  (h on the device, [batch][nd], nd <= 256),
+// in the vector's precision with the coefficients staged once per block.
 template <class T>
 __global__ void multi_axpy(const T* __restrict__ V, long long vstride, int nd,
                            const double* __restrict__ h, T* __restrict__ w, long long n,
                            long long bstride) {
+  __shared__ T hs[256];
   const int b = blockIdx.y;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) hs[i] = (T)h[b * nd + i];
+  __syncthreads();
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    double acc = (double)w[b * bstride + k];
-    for (int i = 0; i < nd; ++i) acc -= h[b * nd + i] * (double)V[i * vstride + b * bstride + k];
-    w[b * bstride + k] = (T)acc;
+    T acc = w[b * bstride + k];
+    for (int i = 0; i < nd; ++i) acc -= hs[i] * V[i * vstride + b * bstride + k];
+    w[b * bstride + k] = acc;
   }
 }
 
-// y[b] = sum_{i<nd} V_i[b] c[b * cstride + i] (+ y[b] if accumulate)
+// y[b] = sum_{i<nd} V_i[b] c[b * cstride + i] (+ y[b] if accumulate), nd <= 256
 template <class T, class TY>
 __global__ void combine(const T* __restrict__ V, long long vstride, int nd,
                         const double* __restrict__ c, int cstride, TY* __restrict__ y,
                         long long n, long long bstride, int accumulate) {
+  __shared__ T cs_[256];
   const int b = blockIdx.y;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) cs_[i] = (T)c[b * cstride + i];
+  __syncthreads();
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    double acc = accumulate ? (double)y[b * bstride + k] : 0.0;
-    for (int i = 0; i < nd; ++i) acc += c[b * cstride + i] * (double)V[i * vstride + b * bstride + k];
+    T acc = accumulate ? (T)y[b * bstride + k] : T(0);
+    for (int i = 0; i < nd; ++i) acc += cs_[i] * V[i * vstride + b * bstride + k];
     y[b * bstride + k] = (TY)acc;
   }
 }
 
-// y[b] = a[b] * x[b] (+ beta * y) with per-batch scalars on the device
+// y[b] = a[b] * x[b] (+ beta * y) with per-batch scalars on the device, in the
+// precision of TY
 template <class TX, class TY>
 __global__ void scale_copy(const TX* __restrict__ x, const double* __restrict__ a, double beta,
                            TY* __restrict__ y, long long n, long long bstride) {
   const int b = blockIdx.y;
+  const TY ab = (TY)a[b], bb = (TY)beta;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    double v = a[b] * (double)x[b * bstride + k];
-    if (beta != 0.0) v += beta * (double)y[b * bstride + k];
-    y[b * bstride + k] = (TY)v;
+    TY v = ab * (TY)x[b * bstride + k];
+    if (beta != 0.0) v += bb * y[b * bstride + k];
+    y[b * bstride + k] = v;
   }
 }
 
@@ -158,6 +171,104 @@ __global__ void count_nonfinite(const double* __restrict__ x, long long n, int* 
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x)
     if (!isfinite(x[k])) { atomicOr(flag, 1); return; }
+}
+
+// ------------------------------------------------------------------ FGMRES state
+// Per operating point b, on the device: H [m+1][m] (column j built in
+// iteration j), g [m+1], cs, sn [m], hcol [m+1], scalars. One thread per b.
+struct KrylovDev {
+  double *H, *g, *cs, *sn, *hcol, *dh, *hn2, *inv, *beta, *bn2, *tol, *resn, *coef;
+  int* jconv;   // -2 done before the cycle, -1 running, j converged at iteration j
+};
+
+__global__ void krylov_tolerance(KrylovDev K, int B, double rtol, double atol) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  K.tol[b] = fmax(rtol * sqrt(K.bn2[b]), atol);
+}
+
+// Start of a cycle: beta = ||r0||, g = beta e1, scale factor 1/beta, done flags.
+__global__ void krylov_cycle_init(KrylovDev K, int B, int m, int* any_running, int* nonfinite) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double beta = sqrt(K.dh[b]);
+  K.beta[b] = beta;
+  K.resn[b] = beta;
+  if (!isfinite(beta)) atomicOr(nonfinite, 1);
+  for (int i = 0; i <= m; ++i) K.g[(long long)b * (m + 1) + i] = 0.0;
+  K.g[(long long)b * (m + 1)] = beta;
+  const bool done = !(beta > K.tol[b]);
+  K.jconv[b] = done ? -2 : -1;
+  K.inv[b] = done ? 0.0 : 1.0 / beta;
+  if (!done) atomicOr(any_running, 1);
+}
+
+__global__ void krylov_hcol_add(KrylovDev K, int B, int m, int nd, int first) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * nd) return;
+  const int b = t / nd, i = t % nd;
+  const double v = K.dh[t];
+  K.hcol[(long long)b * (m + 1) + i] = first ? v : K.hcol[(long long)b * (m + 1) + i] + v;
+}
+
+// Iteration j of Arnoldi with Givens rotations, for every running point.
+__global__ void krylov_givens(KrylovDev K, int B, int m, int j, int* nonfinite) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double hn = sqrt(K.hn2[b]);
+  if (K.jconv[b] != -1) { K.inv[b] = 0.0; return; }
+  double* H = K.H + (long long)b * (m + 1) * m;
+  double* g = K.g + (long long)b * (m + 1);
+  double* cs = K.cs + (long long)b * m;
+  double* sn = K.sn + (long long)b * m;
+  const double* hc = K.hcol + (long long)b * (m + 1);
+  for (int r = 0; r <= j; ++r) H[(long long)r * m + j] = hc[r];
+  H[(long long)(j + 1) * m + j] = hn;
+  for (int r = 0; r < j; ++r) {
+    const double a = H[(long long)r * m + j], c = H[(long long)(r + 1) * m + j];
+    H[(long long)r * m + j] = cs[r] * a + sn[r] * c;
+    H[(long long)(r + 1) * m + j] = -sn[r] * a + cs[r] * c;
+  }
+  const double a = H[(long long)j * m + j], c = H[(long long)(j + 1) * m + j];
+  const double rr = hypot(a, c);
+  cs[j] = rr > 0 ? a / rr : 1.0;
+  sn[j] = rr > 0 ? c / rr : 0.0;
+  H[(long long)j * m + j] = rr;
+  H[(long long)(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  const double res = fabs(g[j + 1]);
+  K.resn[b] = res;
+  if (!isfinite(res)) atomicOr(nonfinite, 1);
+  if (res <= K.tol[b] || hn == 0.0) K.jconv[b] = j;
+  K.inv[b] = (hn > 0 && K.jconv[b] == -1) ? 1.0 / hn : 0.0;
+}
+
+// Back substitution for the update coefficients of every point (columns beyond
+// its convergence iteration are zero).
+__global__ void krylov_solve_upper(KrylovDev K, int B, int m, int jm) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const int jc = K.jconv[b];
+  const int ji = jc == -2 ? 0 : (jc >= 0 ? jc + 1 : jm);
+  const double* H = K.H + (long long)b * (m + 1) * m;
+  const double* g = K.g + (long long)b * (m + 1);
+  double* y = K.coef + (long long)b * m;
+  for (int r = m - 1; r >= ji; --r) y[r] = 0.0;
+  for (int r = ji - 1; r >= 0; --r) {
+    double s = g[r];
+    for (int c = r + 1; c < ji; ++c) s -= H[(long long)r * m + c] * y[c];
+    const double d = H[(long long)r * m + r];
+    y[r] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+// r = b - r (batched, elementwise)
+template <class T>
+__global__ void b_minus(const T* __restrict__ b, T* __restrict__ r, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    r[k] = b[k] - r[k];
 }
 
 // ------------------------------------------------------------------ block inverse
@@ -270,10 +381,20 @@ __global__ void bj_apply_kernel(const TS* __restrict__ BT, const TV* __restrict_
   __syncthreads();
   const TS* B = BT + ((long long)b * E + e) * (long long)n * n;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    TA acc = TA(0);
-    for (int c = 0; c < n; ++c) acc += (TA)B[(long long)c * n + r] * xs[c];
+    // eight independent partial sums keep eight loads per thread in flight
+    TA acc[8] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    int c = 0;
+    for (; c + 8 <= n; c += 8) {
+      TS bv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bv[k] = B[(long long)(c + k) * n + r];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] += (TA)bv[k] * xs[c + k];
+    }
+    for (; c < n; ++c) acc[0] += (TA)B[(long long)c * n + r] * xs[c];
+    const TA s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     const int f = r / Np, i = r % Np;
-    y[b * bstride + f * EN + e * Np + i] = (TV)acc;
+    y[b * bstride + f * EN + e * Np + i] = (TV)s;
   }
 }
 
@@ -542,7 +663,11 @@ extern "C" enp_status enp_block_jacobi_apply(enp_handle h, const double* x, doub
 // Solves J(u_lin) x = b (right-preconditioned by the block-Jacobi inverse set
 // up last; identity if none) for every operating point of the batch. TV is the
 // Krylov vector type: double (FP64 operator) or float (FP32 operator, inner
-// solve of the mixed-precision Newton method).
+// solve of the mixed-precision Newton method). The Hessenberg matrix, the
+// Givens rotations and the scale factors stay on the device; the host reads the
+// convergence flags every kCheckEvery iterations and once per cycle.
+constexpr int kCheckEvery = 8;
+
 template <class TV>
 static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
                              const enp_krylov_opts* o, enp_krylov_stats* st) {
@@ -557,80 +682,71 @@ static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
   const size_t vbytes = sizeof(TV) * ntot;
   const size_t need = vbytes * (size_t)(m + 1) + vbytes * (size_t)m;
   if (S.krylov_bytes < need) {
-    cudaFree(S.V); S.V = nullptr; S.Z = nullptr; S.krylov_bytes = 0;
+    cudaFree(S.V); S.V = nullptr; S.krylov_bytes = 0;
     e = cudaMalloc(&S.V, need);
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc Krylov basis");
     S.krylov_bytes = need;
   }
-  TV* V = (TV*)S.V;                       // [m+1][B][n]
-  TV* Z = (TV*)((char*)S.V + vbytes * (m + 1));  // [m][B][n]
-  const long long vs = ntot;             // stride between basis vectors
-  e = small(h, (size_t)B * (2 * (m + 2)) + (size_t)B * m);
+  TV* V = (TV*)S.V;                                  // [m+1][B][n]
+  TV* Z = (TV*)((char*)S.V + vbytes * (m + 1));      // [m][B][n]
+  const long long vs = ntot;
+  // device small arrays
+  const size_t nH = (size_t)B * (m + 1) * m, nG = (size_t)B * (m + 1), nM = (size_t)B * m;
+  const size_t nsmall = nH + 2 * nG + 2 * nM + nM + (size_t)B * (m + 1) + 7 * (size_t)B + 4;
+  e = small(h, nsmall);
   if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc small");
-  double* dh = S.dsmall;                          // [B][m+1] projections
-  double* dc = S.dsmall + (size_t)B * (m + 2);    // [B][m+1] per-batch scalars
-  double* dcoef = S.dsmall + (size_t)B * 2 * (m + 2);  // [B][m] update coefficients
-  std::vector<double> H((size_t)B * (m + 1) * m), g((size_t)B * (m + 1)), cs((size_t)B * m),
-      sn((size_t)B * m), hh((size_t)B * (m + 1)), beta0(B, 0.0), resn(B, 0.0), bnorm(B, 0.0);
-  std::vector<int> done(B, 0), jconv(B, m);
+  double* q = S.dsmall;
+  enp::KrylovDev K;
+  K.H = q; q += nH;
+  K.g = q; q += nG;
+  K.hcol = q; q += nG;
+  K.cs = q; q += nM;
+  K.sn = q; q += nM;
+  K.coef = q; q += nM;
+  K.dh = q; q += (size_t)B * (m + 1);
+  K.hn2 = q; q += B;
+  K.inv = q; q += B;
+  K.beta = q; q += B;
+  K.bn2 = q; q += B;
+  K.tol = q; q += B;
+  K.resn = q; q += B;
+  int* flags = reinterpret_cast<int*>(q); q += B;   // jconv
+  int* dflag = reinterpret_cast<int*>(q);           // [0] any running, [1] non-finite
+  K.jconv = flags;
   const int gx = grid_for(n);
   dim3 gv(gx, B);
+  const int tb = std::min(B, 256), gbk = (B + tb - 1) / tb;
   auto apply_A = [&](const TV* in, TV* outv) -> cudaError_t {
     return enp::launch_op<TV>(enp::kJvp, P, h->d_tab, ulin, in, outv, B, h->stream);
   };
-  auto dots = [&](const TV* Vb, int nd, const TV* w, std::vector<double>& hostv) -> cudaError_t {
-    cudaError_t er = multidot<TV>(h, Vb, vs, nd, w, dh);
-    if (er != cudaSuccess) return er;
-    hostv.assign((size_t)B * nd, 0.0);
-    er = cudaMemcpyAsync(hostv.data(), dh, sizeof(double) * B * nd, cudaMemcpyDeviceToHost, h->stream);
-    if (er != cudaSuccess) return er;
-    return cudaStreamSynchronize(h->stream);
-  };
-  std::vector<double> tmp;
-  // ||b||
-  if ((e = dots(b, 1, b, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres norm");
-  for (int i = 0; i < B; ++i) bnorm[i] = std::sqrt(tmp[i]);
+  std::vector<int> hj(B);
+  std::vector<double> hres(B), hb(B);
+  int hflag[2] = {0, 0};
+  // ||b|| and the tolerances
+  if ((e = multidot<TV>(h, b, 0, 1, b, K.bn2)) != cudaSuccess) return cuda_err(h, e, "fgmres norm");
+  enp::krylov_tolerance<<<gbk, tb, 0, h->stream>>>(K, B, o->rtol, o->atol);
   int total_it = 0;
-  bool all_done = false;
   double first_norm = -1.0;
-  for (int cycle = 0; !all_done && total_it < o->max_it; ++cycle) {
-    // r0 = b - A x  -> V_0
+  bool all_done = false, nonfinite = false;
+  while (!all_done && total_it < o->max_it) {
+    // r0 = b - A x -> V0
     if ((e = apply_A(x, V)) != cudaSuccess) return cuda_err(h, e, "fgmres A x");
-    std::vector<double> one(B, -1.0);
-    // V0 = b - V0
-    {
-      std::vector<double> ones(B, 1.0);
-      cudaMemcpyAsync(dc, one.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
-      enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, dc, 0.0, V, n, n);
-      cudaMemcpyAsync(dc, ones.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
-      enp::combine<TV, TV><<<gv, 256, 0, h->stream>>>(b, 0, 1, dc, 1, V, n, n, 1);
-    }
-    if ((e = dots(V, 1, V, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres r0");
-    for (int i = 0; i < B; ++i) {
-      beta0[i] = std::sqrt(tmp[i]);
-      if (first_norm < 0) resn[i] = beta0[i];
-    }
+    enp::b_minus<TV><<<grid_for(ntot), 256, 0, h->stream>>>(b, V, ntot);
+    if ((e = multidot<TV>(h, V, 0, 1, V, K.dh)) != cudaSuccess) return cuda_err(h, e, "fgmres r0");
+    cudaMemsetAsync(dflag, 0, 2 * sizeof(int), h->stream);
+    enp::krylov_cycle_init<<<gbk, tb, 0, h->stream>>>(K, B, m, dflag, dflag + 1);
+    cudaMemcpyAsync(hflag, dflag, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(hres.data(), K.resn, B * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_err(h, e, "fgmres sync");
+    if (hflag[1]) { nonfinite = true; break; }
     if (first_norm < 0) {
       first_norm = 0;
-      for (int i = 0; i < B; ++i) first_norm = std::max(first_norm, beta0[i]);
+      for (int i = 0; i < B; ++i) first_norm = std::max(first_norm, hres[i]);
     }
-    std::vector<double> inv(B);
-    all_done = true;
-    for (int i = 0; i < B; ++i) {
-      double tol = std::max(o->rtol * bnorm[i], o->atol);
-      done[i] = !(beta0[i] > tol);
-      if (!std::isfinite(beta0[i])) { h->err = "non-finite residual in FGMRES"; return ENP_ERR_NONFINITE; }
-      inv[i] = done[i] ? 0.0 : 1.0 / beta0[i];
-      all_done = all_done && done[i];
-      resn[i] = beta0[i];
-    }
-    if (all_done) break;
-    cudaMemcpyAsync(dc, inv.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
-    enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, dc, 0.0, V, n, n);
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    for (int i = 0; i < B; ++i) { g[(size_t)i * (m + 1)] = beta0[i]; jconv[i] = -1; }
+    if (!hflag[0]) { all_done = true; break; }
+    enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, K.inv, 0.0, V, n, n);
     int j = 0;
+    bool cycle_done = false;
     for (; j < m && total_it < o->max_it; ++j) {
       TV* vj = V + j * vs;
       TV* zj = Z + j * vs;
@@ -639,96 +755,55 @@ static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
       else e = cudaMemcpyAsync(zj, vj, vbytes, cudaMemcpyDeviceToDevice, h->stream);
       if (e != cudaSuccess) return cuda_err(h, e, "fgmres precondition");
       if ((e = apply_A(zj, w)) != cudaSuccess) return cuda_err(h, e, "fgmres A z");
-      // classical Gram-Schmidt, twice
-      std::vector<double> hsum((size_t)B * (j + 1), 0.0);
-      for (int pass = 0; pass < 2; ++pass) {
-        if ((e = dots(V, j + 1, w, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres dots");
-        cudaMemcpyAsync(dh, tmp.data(), sizeof(double) * B * (j + 1), cudaMemcpyHostToDevice, h->stream);
-        enp::multi_axpy<TV><<<gv, 256, 0, h->stream>>>(V, vs, j + 1, dh, w, n, n);
-        for (size_t t = 0; t < hsum.size(); ++t) hsum[t] += tmp[t];
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        if ((e = multidot<TV>(h, V, vs, j + 1, w, K.dh)) != cudaSuccess) return cuda_err(h, e, "fgmres dots");
+        enp::krylov_hcol_add<<<(B * (j + 1) + 127) / 128, 128, 0, h->stream>>>(K, B, m, j + 1, pass == 0);
+        enp::multi_axpy<TV><<<gv, 256, 0, h->stream>>>(V, vs, j + 1, K.dh, w, n, n);
       }
-      if ((e = dots(w, 1, w, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres norm w");
+      if ((e = multidot<TV>(h, w, 0, 1, w, K.hn2)) != cudaSuccess) return cuda_err(h, e, "fgmres norm w");
+      enp::krylov_givens<<<gbk, tb, 0, h->stream>>>(K, B, m, j, dflag + 1);
+      enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(w, K.inv, 0.0, w, n, n);
       ++total_it;
-      std::vector<double> invn(B);
-      bool alldone_now = true;
-      for (int i = 0; i < B; ++i) {
-        double* Hi = &H[(size_t)i * (m + 1) * m];
-        double* gi = &g[(size_t)i * (m + 1)];
-        double* csi = &cs[(size_t)i * m];
-        double* sni = &sn[(size_t)i * m];
-        const double hn = std::sqrt(tmp[i]);
-        invn[i] = (hn > 0 && jconv[i] < 0) ? 1.0 / hn : 0.0;
-        if (jconv[i] >= 0) continue;  // this operating point already converged
-        for (int r = 0; r <= j; ++r) Hi[(size_t)r * m + j] = hsum[(size_t)i * (j + 1) + r];
-        Hi[(size_t)(j + 1) * m + j] = hn;
-        for (int r = 0; r < j; ++r) {  // apply previous rotations
-          double a = Hi[(size_t)r * m + j], bb = Hi[(size_t)(r + 1) * m + j];
-          Hi[(size_t)r * m + j] = csi[r] * a + sni[r] * bb;
-          Hi[(size_t)(r + 1) * m + j] = -sni[r] * a + csi[r] * bb;
-        }
-        double a = Hi[(size_t)j * m + j], bb = Hi[(size_t)(j + 1) * m + j];
-        double rr = std::hypot(a, bb);
-        csi[j] = rr > 0 ? a / rr : 1.0;
-        sni[j] = rr > 0 ? bb / rr : 0.0;
-        Hi[(size_t)j * m + j] = rr;
-        Hi[(size_t)(j + 1) * m + j] = 0.0;
-        gi[j + 1] = -sni[j] * gi[j];
-        gi[j] = csi[j] * gi[j];
-        resn[i] = std::fabs(gi[j + 1]);
-        if (!std::isfinite(resn[i])) { h->err = "non-finite value in FGMRES"; return ENP_ERR_NONFINITE; }
-        double tol = std::max(o->rtol * bnorm[i], o->atol);
-        if (resn[i] <= tol || hn == 0.0) jconv[i] = j;
-        alldone_now = alldone_now && jconv[i] >= 0;
+      if ((j + 1) % kCheckEvery == 0 || j + 1 == m || total_it >= o->max_it) {
+        cudaMemcpyAsync(hj.data(), K.jconv, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        cudaMemcpyAsync(hflag + 1, dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_err(h, e, "fgmres sync");
+        if (hflag[1]) { nonfinite = true; break; }
+        cycle_done = true;
+        for (int i = 0; i < B; ++i) cycle_done = cycle_done && hj[i] != -1;
+        if (cycle_done) { ++j; break; }
       }
-      cudaMemcpyAsync(dc, invn.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
-      enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(w, dc, 0.0, w, n, n);
-      if (alldone_now) { ++j; break; }
     }
-    // x += Z y, y from the triangular system of each operating point
+    if (nonfinite) break;
     const int jm = j;
-    std::vector<double> coef((size_t)B * m, 0.0);
-    for (int i = 0; i < B; ++i) {
-      const int ji = jconv[i] >= 0 ? jconv[i] + 1 : jm;
-      const double* Hi = &H[(size_t)i * (m + 1) * m];
-      const double* gi = &g[(size_t)i * (m + 1)];
-      for (int r = ji - 1; r >= 0; --r) {
-        double s = gi[r];
-        for (int c = r + 1; c < ji; ++c) s -= Hi[(size_t)r * m + c] * coef[(size_t)i * m + c];
-        coef[(size_t)i * m + r] = Hi[(size_t)r * m + r] != 0 ? s / Hi[(size_t)r * m + r] : 0.0;
-      }
-    }
-    cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * B * m, cudaMemcpyHostToDevice, h->stream);
-    enp::combine<TV, TV><<<gv, 256, 0, h->stream>>>(Z, vs, jm, dcoef, m, x, n, n, 1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_err(h, e, "fgmres update");
-    all_done = true;
-    for (int i = 0; i < B; ++i) all_done = all_done && jconv[i] >= 0;
-    if (all_done) {
-      // true residual check of the final iterate
-      if ((e = apply_A(x, V)) != cudaSuccess) return cuda_err(h, e, "fgmres final A x");
-      std::vector<double> minus1(B, -1.0), ones(B, 1.0);
-      cudaMemcpyAsync(dc, minus1.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
-      enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, dc, 0.0, V, n, n);
-      cudaMemcpyAsync(dc, ones.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
-      enp::combine<TV, TV><<<gv, 256, 0, h->stream>>>(b, 0, 1, dc, 1, V, n, n, 1);
-      if ((e = dots(V, 1, V, tmp)) != cudaSuccess) return cuda_err(h, e, "fgmres final r");
-      for (int i = 0; i < B; ++i) resn[i] = std::sqrt(tmp[i]);
-    }
+    enp::krylov_solve_upper<<<gbk, tb, 0, h->stream>>>(K, B, m, jm);
+    enp::combine<TV, TV><<<gv, 256, 0, h->stream>>>(Z, vs, jm, K.coef, m, x, n, n, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(h, e, "fgmres update");
+    all_done = cycle_done;
   }
+  if (nonfinite) { h->err = "non-finite value in FGMRES"; return ENP_ERR_NONFINITE; }
+  // true residual of the final iterate
+  if ((e = apply_A(x, V)) != cudaSuccess) return cuda_err(h, e, "fgmres final A x");
+  enp::b_minus<TV><<<grid_for(ntot), 256, 0, h->stream>>>(b, V, ntot);
+  if ((e = multidot<TV>(h, V, 0, 1, V, K.dh)) != cudaSuccess) return cuda_err(h, e, "fgmres final r");
+  std::vector<double> hr2(B), htol(B), hbn(B);
+  cudaMemcpyAsync(hr2.data(), K.dh, B * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(htol.data(), K.tol, B * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(hbn.data(), K.bn2, B * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_err(h, e, "fgmres sync");
   double worst_rel = 0.0, worst = 0.0;
-  bool conv = true;
+  bool conv = all_done;
   for (int i = 0; i < B; ++i) {
-    double tol = std::max(o->rtol * bnorm[i], o->atol);
-    // the true residual may exceed the recurrence estimate by rounding
-    if (!(resn[i] <= tol * 1.0001 + 0.0)) conv = false;
-    worst = std::max(worst, resn[i]);
-    worst_rel = std::max(worst_rel, bnorm[i] > 0 ? resn[i] / bnorm[i] : resn[i]);
+    const double r = std::sqrt(hr2[i]), bn = std::sqrt(hbn[i]);
+    if (!(r <= htol[i] * 1.0001)) conv = false;  // the true residual, not the estimate
+    worst = std::max(worst, r);
+    worst_rel = std::max(worst_rel, bn > 0 ? r / bn : r);
   }
   if (st) {
     st->iterations = total_it;
     st->residual_norm = worst;
     st->relative_residual = worst_rel;
-    st->initial_norm = first_norm;
+    st->initial_norm = first_norm < 0 ? 0.0 : first_norm;
     st->converged = conv ? 1 : 0;
   }
   if (!conv) { h->err = "FGMRES reached max_it"; return ENP_ERR_NOT_CONVERGED; }
