@@ -310,8 +310,14 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
     e = cudaMemcpy(h->d_xv[a], mesh->coords[a], sizeof(double) * (P.ne[a] + 1), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload coords"); enp_dg_destroy(h); return s; }
     P.xv[a] = h->d_xv[a];
+    std::vector<float> cf(mesh->coords[a], mesh->coords[a] + P.ne[a] + 1);
+    e = cudaMalloc(&h->d_xvf[a], sizeof(float) * (P.ne[a] + 1));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->d_xvf[a], cf.data(), sizeof(float) * (P.ne[a] + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload coords (FP32)"); enp_dg_destroy(h); return s; }
+    P.xvf[a] = h->d_xvf[a];
   }
-  for (int a = dim; a < 3; ++a) P.xv[a] = nullptr;
+  for (int a = dim; a < 3; ++a) { P.xv[a] = nullptr; P.xvf[a] = nullptr; }
   e = cudaMalloc(&h->d_btag, tags.size());
   if (e == cudaSuccess) e = cudaMemcpy(h->d_btag, tags.data(), tags.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_tab, sizeof(Tables));
@@ -328,7 +334,7 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
 enp_status enp_dg_destroy(enp_handle h) {
   if (!h) return ENP_ERR_INVALID_ARG;
   enp_solver_free(h);
-  for (int a = 0; a < 3; ++a) cudaFree(h->d_xv[a]);
+  for (int a = 0; a < 3; ++a) { cudaFree(h->d_xv[a]); cudaFree(h->d_xvf[a]); }
   cudaFree(h->d_btag);
   cudaFree(h->d_tab);
   cudaFree(h->d_src);

@@ -42,6 +42,7 @@ struct OpParams {
   int dim, ne[3], E, NF, m, p, n, q, Np, Nq, Nfq, NBF;
   int side_off[7];
   const double* xv[3];        // device: per-axis vertex coordinates
+  const float* xvf[3];        // the same in FP32, for FP32 kernels
   const uint8_t* btag;        // device: boundary tags, side-major
   // physics (Sec. 2): mu_k = D_k / RT; migration coefficient z_k mu_k F;
   // a_k = F z_k (D_k - D_m); kappa_k so that kappa = sum_k kappa_k c_k (Eq. charge2)
@@ -66,6 +67,10 @@ struct OpParams {
 };
 
 template <class R> __host__ __device__ __forceinline__ const PhysT<R>& phys(const OpParams& p);
+// Vertex coordinate i of axis a in the kernel's arithmetic type.
+template <class R> __device__ __forceinline__ R vertex(const OpParams& p, int a, int i);
+template <> __device__ __forceinline__ double vertex<double>(const OpParams& p, int a, int i) { return p.xv[a][i]; }
+template <> __device__ __forceinline__ float vertex<float>(const OpParams& p, int a, int i) { return p.xvf[a][i]; }
 template <> __host__ __device__ __forceinline__ const PhysT<double>& phys<double>(const OpParams& p) { return p.pd; }
 template <> __host__ __device__ __forceinline__ const PhysT<float>& phys<float>(const OpParams& p) { return p.pf; }
 

@@ -30,6 +30,7 @@ struct enp_dg {
   enp::Tables htab{};
   enp::Tables* d_tab = nullptr;
   double* d_xv[3] = {nullptr, nullptr, nullptr};
+  float* d_xvf[3] = {nullptr, nullptr, nullptr};
   uint8_t* d_btag = nullptr;
   double* d_src = nullptr;
   double* d_dir = nullptr;

@@ -443,8 +443,8 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a < DIM) {
-      lo[a] = R(prm.xv[a][idx[a]]);
-      h[a] = R(prm.xv[a][idx[a] + 1]) - lo[a];
+      lo[a] = vertex<R>(prm, a, idx[a]);
+      h[a] = vertex<R>(prm, a, idx[a] + 1) - lo[a];
       diag2 += h[a] * h[a];
     } else { lo[a] = R(0); h[a] = R(1); }
   }
@@ -614,7 +614,7 @@ op_kernel(const OpParams prm, const Tables* __restrict__ tabs, const R* __restri
       R d2 = R(0);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        const R hc = R(prm.xv[c][in[c] + 1]) - R(prm.xv[c][in[c]]);
+        const R hc = vertex<R>(prm, c, in[c] + 1) - vertex<R>(prm, c, in[c]);
         d2 += hc * hc;
         if (c == a) hn = hc;
       }

@@ -55,15 +55,18 @@ template <int P> struct TabOff {
 // the input, OUT_ST in the output) are processed, pencils shared over the
 // NT threads of the element.
 template <int P, int E0, int E1, int E2, int DIR, int TAB, bool TRANS, bool ACC, int CNT,
-          int IN_ST, int OUT_ST, class R>
+          int IN_ST, int OUT_ST, class R, int IX = E0, int OX = -1>
 __device__ __forceinline__ void pencil(const R* __restrict__ in, R* __restrict__ out, int tid,
                                        int NT) {
+  // IX: input row stride along dimension 0 (>= E0, padded arrays); OX: output row
+  // stride (default: the output extent of dimension 0).
   using T = TabOff<P>;
   constexpr int COLS = DIR == 0 ? E0 : (DIR == 1 ? E1 : E2);
   constexpr int ROWS = TAB == 0 ? (TRANS ? T::N : T::Q) : T::Q;
   constexpr int O0 = DIR == 0 ? ROWS : E0, O1 = DIR == 1 ? ROWS : E1, O2 = DIR == 2 ? ROWS : E2;
-  constexpr int IS = DIR == 0 ? 1 : (DIR == 1 ? E0 : E0 * E1);
-  constexpr int OS = DIR == 0 ? 1 : (DIR == 1 ? O0 : O0 * O1);
+  constexpr int OXX = OX < 0 ? O0 : OX;
+  constexpr int IS = DIR == 0 ? 1 : (DIR == 1 ? IX : IX * E1);
+  constexpr int OS = DIR == 0 ? 1 : (DIR == 1 ? OXX : OXX * O1);
   constexpr int PA = DIR == 0 ? O1 : O0;          // pencil index ranges over the other dims
   constexpr int PB = DIR == 2 ? O1 : O2;
   constexpr int NP = PA * PB;
@@ -72,9 +75,9 @@ __device__ __forceinline__ void pencil(const R* __restrict__ in, R* __restrict__
     const int c = w / NP, pp = w % NP;
     const int ia = pp % PA, ib = pp / PA;
     int ibase, obase;
-    if (DIR == 0) { ibase = E0 * (ia + E1 * ib); obase = O0 * (ia + O1 * ib); }
-    else if (DIR == 1) { ibase = ia + E0 * E1 * ib; obase = ia + O0 * O1 * ib; }
-    else { ibase = ia + E0 * ib; obase = ia + O0 * ib; }
+    if (DIR == 0) { ibase = IX * (ia + E1 * ib); obase = OXX * (ia + O1 * ib); }
+    else if (DIR == 1) { ibase = ia + IX * E1 * ib; obase = ia + OXX * O1 * ib; }
+    else { ibase = ia + IX * ib; obase = ia + OXX * ib; }
     const R* src = in + c * IN_ST + ibase;
     R* dst = out + c * OUT_ST + obase;
     R x[COLS];
@@ -95,27 +98,53 @@ __device__ __forceinline__ void pencil(const R* __restrict__ in, R* __restrict__
   }
 }
 
+// Nodal arrays are stored with the x row padded to an odd length, so that
+// threads working on neighbouring x-pencils hit different shared-memory banks.
+template <int N> struct Pad { static constexpr int X = (N % 2 == 0) ? N + 1 : N; };
+template <int N>
+__device__ __forceinline__ int padded_node(int i) {  // lexicographic node -> padded offset
+  const int ix = i % N, iyz = i / N;
+  return ix + Pad<N>::X * iyz;
+}
+template <int N>
+__device__ __forceinline__ int face_node_pad(int a, int k, int j1, int j2) {
+  constexpr int X = Pad<N>::X;
+  if (a == 0) return k + X * (j1 + N * j2);
+  if (a == 1) return j1 + X * (k + N * j2);
+  return j1 + X * (j2 + N * k);
+}
+
 template <int P, int NF, int MODE>
 struct Smem3 {
   static constexpr int N = P + 1, Q = P + 2;
+  static constexpr int NX = Pad<N>::X;                   // padded x row of nodal arrays
   static constexpr int NN = N * N * N, NQ = Q * Q * Q, FN = N * N, FQ = Q * Q;
+  static constexpr int NNP = NX * N * N;                 // padded nodal array
+  static constexpr int FNP = NX * N;                     // padded face-node array
   static constexpr int NV = MODE == kResidual ? 1 : 2;
   static constexpr int NA = NV * NF;                     // arrays carried through the volume
-  static constexpr int kX = NA * NN;                     // element data
-  static constexpr int kOut = NF * NN;                   // rows
+  static constexpr int kX = NA * NNP;                    // element data
+  static constexpr int kOut = NF * NNP;                  // rows
   static constexpr int kT1 = NA * Q * N * N;             // after the x contraction
   static constexpr int kT2 = NA * Q * Q * N;             // after the y contraction
   static constexpr int kPts = NA * 4 * NQ;               // values + 3 gradients
-  static constexpr int kFace = NA * NN                    // neighbour data
-                               + 2 * NA * 2 * FN          // layer values + normal derivatives
+  static constexpr int kFace = NA * NNP                   // neighbour data
+                               + 2 * NA * 2 * FNP         // layer values + normal derivatives
                                + 2 * NA * 2 * Q * N       // after the first face contraction
                                + 2 * NA * 2 * FQ          // traces at face points
                                + 2 * NF * FQ              // face coefficients
                                + 2 * NF * Q * N           // transposed, first stage
-                               + 2 * NF * FN;             // transposed, at face nodes
-  static constexpr int kVol = kT1 + kT2 + kPts;
+                               + 2 * NF * FNP;            // transposed, at face nodes
+  // T1 is dead once T2 is formed, so it shares space with the point arrays
+  static constexpr int kVol = kT2 + (kPts > kT1 ? kPts : kT1);
   static constexpr int kWork = kVol > kFace ? kVol : kFace;
-  static constexpr int total = kX + kOut + kWork;
+  static constexpr int raw = kX + kOut + kWork;
+  // stride between element regions: congruent to the element's thread count
+  // modulo the bank count (32 words), so that a warp spanning two elements
+  // keeps consecutive threads on consecutive banks
+  static constexpr int kBankWords = 32;
+  static constexpr int total = raw + ((Q * Q - raw % kBankWords) % kBankWords + kBankWords) % kBankWords;
+  static constexpr int kPrefetch = (NA * NN + Q * Q - 1) / (Q * Q);  // neighbour values per thread
 };
 
 template <int P, int NF, int MODE, int EB, class R>
@@ -125,15 +154,16 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   using S = Smem3<P, NF, MODE>;
   using TO = TabOff<P>;
   constexpr int N = S::N, Q = S::Q, NN = S::NN, NQ = S::NQ, FN = S::FN, FQ = S::FQ;
-  constexpr int NV = S::NV, NA = S::NA, NT = Q * Q;
+  constexpr int NX = S::NX, NNP = S::NNP, FNP = S::FNP;
+  constexpr int NV = S::NV, NA = S::NA, NT = Q * Q, PF = S::kPrefetch;
   constexpr bool kBlk = MODE == kBlockCol;
   constexpr int MODEc = kBlk ? kJvp : MODE;
   const PhysT<R>& ph = phys<R>(prm);
   extern __shared__ __align__(16) unsigned char smem3_raw[];
   const int es = threadIdx.x / NT, tid = threadIdx.x % NT;
   R* base = reinterpret_cast<R*>(smem3_raw) + es * S::total;
-  R* XA = base;                 // [NA][NN]
-  R* RO = XA + S::kX;           // [NF][NN]
+  R* XA = base;                 // [NA][NNP] padded nodal arrays
+  R* RO = XA + S::kX;           // [NF][NNP]
   R* WK = RO + S::kOut;
   const int e = blockIdx.x * EB + es;
   const bool valid = e < prm.E;
@@ -151,8 +181,8 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   R diag2 = R(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    lo[a] = R(prm.xv[a][idx[a]]);
-    h[a] = R(prm.xv[a][idx[a] + 1]) - lo[a];
+    lo[a] = vertex<R>(prm, a, idx[a]);
+    h[a] = vertex<R>(prm, a, idx[a] + 1) - lo[a];
     sc[a] = R(2) / h[a];
     diag2 += h[a] * h[a];
   }
@@ -162,16 +192,37 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   for (int t = tid; t < NF * NN; t += NT) {
     const int f = t / NN, i = t % NN;
     const long long gi = boff + f * EN + (long long)ee * NN + i;
-    XA[t] = u[gi];
-    if (NV == 2) XA[NF * NN + t] = kBlk ? R(t == col ? 1 : 0) : v[gi];
+    const int pi = f * NNP + padded_node<N>(i);
+    XA[pi] = u[gi];
+    if (NV == 2) XA[NF * NNP + pi] = kBlk ? R(t == col ? 1 : 0) : v[gi];
   }
+  // neighbour data of a face, fetched into registers one face ahead so that the
+  // global loads overlap the computation of the previous stage
+  const int stride[3] = {1, prm.ne[0], prm.ne[0] * prm.ne[1]};
+  R pf[PF];
+  auto prefetch = [&](int s) {
+    const int a = s >> 1, hi = s & 1;
+    const bool bnd = hi ? (idx[a] == prm.ne[a] - 1) : (idx[a] == 0);
+    if (bnd) return;
+    const int en = ee + (hi ? stride[a] : -stride[a]);
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+      const int t = tid + k * NT;
+      if (t < NA * NN) {
+        const int vv = t / (NF * NN), r = t % (NF * NN), f = r / NN, i = r % NN;
+        const long long gi = boff + f * EN + (long long)en * NN + i;
+        pf[k] = vv == 0 ? u[gi] : (kBlk ? R(0) : v[gi]);
+      }
+    }
+  };
+  prefetch(0);
   __syncthreads();
 
   // ---------------------------------------------------------------- volume
-  R* T1 = WK;                   // [NA][N][N][Q]
-  R* T2 = T1 + S::kT1;          // [NA][N][Q][Q]
+  R* T2 = WK;                   // [NA][N][Q][Q]
   R* PT = T2 + S::kT2;          // [NA][4][NQ]
-  pencil<P, N, N, N, 0, 0, false, false, NA, NN, Q * N * N>(XA, T1, tid, NT);
+  R* T1 = PT;                   // [NA][N][N][Q], dead before PT is written
+  pencil<P, N, N, N, 0, 0, false, false, NA, NNP, Q * N * N, R, NX>(XA, T1, tid, NT);
   __syncthreads();
   pencil<P, Q, N, N, 1, 0, false, false, NA, Q * N * N, Q * Q * N>(T1, T2, tid, NT);
   __syncthreads();
@@ -256,20 +307,20 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   __syncthreads();
   pencil<P, Q, Q, Q, 2, 0, true, false, NF, 4 * NQ, Q * Q * N>(PO, T2, tid, NT);
   __syncthreads();
-  pencil<P, Q, Q, N, 1, 0, true, false, NF, Q * Q * N, Q * N * N>(T2, T1, tid, NT);
+  R* T1b = PT;  // the point arrays are dead once T2 holds the z-transposed values
+  pencil<P, Q, Q, N, 1, 0, true, false, NF, Q * Q * N, Q * N * N>(T2, T1b, tid, NT);
   __syncthreads();
-  pencil<P, Q, N, N, 0, 0, true, false, NF, Q * N * N, NN>(T1, RO, tid, NT);
+  pencil<P, Q, N, N, 0, 0, true, false, NF, Q * N * N, NNP, R, Q, NX>(T1b, RO, tid, NT);
   __syncthreads();
 
   // ---------------------------------------------------------------- faces
-  R* XN = WK;                                  // [NA][NN] neighbour data
-  R* FL = XN + NA * NN;                        // [2 sides][NA][2][FN] layer values, derivatives
-  R* F1 = FL + 2 * NA * 2 * FN;                // [2][NA][2][Q][N]
+  R* XN = WK;                                  // [NA][NNP] neighbour data
+  R* FL = XN + NA * NNP;                       // [2 sides][NA][2][FNP] layer values, derivatives
+  R* F1 = FL + 2 * NA * 2 * FNP;               // [2][NA][2][Q][N]
   R* TR = F1 + 2 * NA * 2 * Q * N;             // [2][NA][2][FQ]
   R* FC = TR + 2 * NA * 2 * FQ;                // [2][NF][FQ]: S then T coefficients
   R* G1 = FC + 2 * NF * FQ;                    // [2][NF][N][Q]
-  R* G2 = G1 + 2 * NF * Q * N;                 // [2][NF][FN]
-  const int stride[3] = {1, prm.ne[0], prm.ne[0] * prm.ne[1]};
+  R* G2 = G1 + 2 * NF * Q * N;                 // [2][NF][FNP]
 #pragma unroll 1
   for (int s = 0; s < 6; ++s) {
     const int a = s >> 1, hi = s & 1;
@@ -283,24 +334,26 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
       bface = prm.side_off[s] + loc;
       tag = prm.btag[bface];
     } else {
-      const int en = ee + (hi ? stride[a] : -stride[a]);
       int in3[3] = {idx[0], idx[1], idx[2]};
       in3[a] += hi ? 1 : -1;
       R d2 = R(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const R hc = R(prm.xv[c][in3[c] + 1]) - R(prm.xv[c][in3[c]]);
+        const R hc = vertex<R>(prm, c, in3[c] + 1) - vertex<R>(prm, c, in3[c]);
         d2 += hc * hc;
         if (c == a) hn = hc;
       }
       diagn = sqrt(d2);
-      for (int t = tid; t < NF * NN; t += NT) {
-        const int f = t / NN, i = t % NN;
-        const long long gi = boff + f * EN + (long long)en * NN + i;
-        XN[t] = u[gi];
-        if (NV == 2) XN[NF * NN + t] = kBlk ? R(0) : v[gi];
+#pragma unroll
+      for (int k = 0; k < PF; ++k) {
+        const int t = tid + k * NT;
+        if (t < NA * NN) {
+          const int arr = t / NN, i = t % NN;
+          XN[arr * NNP + padded_node<N>(i)] = pf[k];
+        }
       }
     }
+    if (s < 5) prefetch(s + 1);
     const bool active = !(tag == kWall || (tag == kInlet && MODEc != kResidual));
     __syncthreads();
     // layer values and reference normal derivatives at the face nodes
@@ -309,22 +362,23 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
     for (int w = tid; w < nsides * NA * FN; w += NT) {
       const int side = w / (NA * FN), r = w % (NA * FN), arr = r / FN, j = r % FN;
       const int j1 = j % N, j2 = j / N;
-      const R* X = (side == 0 ? XA : XN) + arr * NN;
+      const R* X = (side == 0 ? XA : XN) + arr * NNP;
       const int L = side == 0 ? lay : layo;
       const int dsel = side == 0 ? hi : 1 - hi;
       R d = R(0);
 #pragma unroll
       for (int k = 0; k < N; ++k)
-        d = mad(ctab<P, R>(TO::dL + dsel * N + k), X[face_node<3, N>(a, k, j1, j2)], d);
-      R* o = FL + ((side * NA + arr) * 2) * FN;
-      o[j] = X[face_node<3, N>(a, L, j1, j2)];
-      o[FN + j] = d;
+        d = mad(ctab<P, R>(TO::dL + dsel * N + k), X[face_node_pad<N>(a, k, j1, j2)], d);
+      R* o = FL + ((side * NA + arr) * 2) * FNP;
+      const int jp = j1 + NX * j2;
+      o[jp] = X[face_node_pad<N>(a, L, j1, j2)];
+      o[FNP + jp] = d;
     }
     __syncthreads();
     // 2D interpolation to the face Gauss points: along b0, then b1. Both sides
     // are always processed so that every thread reaches every barrier; on a
     // boundary face the second side holds stale values that are never read.
-    pencil<P, N, N, 1, 0, 0, false, false, 4 * NA, FN, Q * N>(FL, F1, tid, NT);
+    pencil<P, N, N, 1, 0, 0, false, false, 4 * NA, FNP, Q * N, R, NX>(FL, F1, tid, NT);
     __syncthreads();
     pencil<P, Q, N, 1, 1, 0, false, false, 4 * NA, Q * N, FQ>(F1, TR, tid, NT);
     __syncthreads();
@@ -422,18 +476,19 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
     // transposed 2D contraction back to the face nodes, then into the rows
     pencil<P, Q, Q, 1, 1, 0, true, false, 2 * NF, FQ, Q * N>(FC, G1, tid, NT);
     __syncthreads();
-    pencil<P, Q, N, 1, 0, 0, true, false, 2 * NF, Q * N, FN>(G1, G2, tid, NT);
+    pencil<P, Q, N, 1, 0, 0, true, false, 2 * NF, Q * N, FNP, R, Q, NX>(G1, G2, tid, NT);
     __syncthreads();
     for (int w = tid; w < NF * FN; w += NT) {
       const int f = w / FN, j = w % FN, j1 = j % N, j2 = j / N;
-      R* Rf = RO + f * NN;
-      const R sv = G2[f * FN + j], tv = G2[(NF + f) * FN + j];
+      R* Rf = RO + f * NNP;
+      const int jp = j1 + NX * j2;
+      const R sv = G2[f * FNP + jp], tv = G2[(NF + f) * FNP + jp];
       if (active) {
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           R add = ctab<P, R>(TO::dL + hi * N + k) * tv;
           if (k == lay) add += sv;
-          Rf[face_node<3, N>(a, k, j1, j2)] += add;
+          Rf[face_node_pad<N>(a, k, j1, j2)] += add;
         }
       }
     }
@@ -443,11 +498,12 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   if (valid) {
     if (kBlk) {
       const long long nb = NF * NN;
-      for (int t = tid; t < NF * NN; t += NT) out[((long long)e * nb + t) * nb + col] = RO[t];
+      for (int t = tid; t < NF * NN; t += NT)
+        out[((long long)e * nb + t) * nb + col] = RO[(t / NN) * NNP + padded_node<N>(t % NN)];
     } else {
       for (int t = tid; t < NF * NN; t += NT) {
         const int f = t / NN, i = t % NN;
-        out[boff + f * EN + (long long)e * NN + i] = RO[t];
+        out[boff + f * EN + (long long)e * NN + i] = RO[f * NNP + padded_node<N>(i)];
       }
     }
   }
