@@ -238,6 +238,22 @@ typedef struct {
 enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* opts,
                             enp_newton_stats* stats);
 
+/* Number of parameters theta of enp_param_jacobian / enp_param_vjp: 2m + 3,
+ * ordered (D_1..D_m, c_in_1..c_in_{m-1}, phi_app of electrodes 0..3). */
+enp_status enp_param_count(enp_handle h, int* n_theta);
+
+/* dR/dtheta_j for every parameter j, exactly (the residual evaluated with
+ * forward-tangent coefficients): D_k enters through D_k, z_k mu_k F, a_km and
+ * kappa (Eq. NE, Eq. charge2), c_in through the inlet term and phi_app through
+ * Butler-Volmer (Eq. bv). The paper has no derivative with respect to its
+ * parameters; this is the parameter Jacobian of Eq. NPDG / Eq. chargeDG.
+ * dRdtheta: device [n_theta][batch][m][E][Np]. Hexahedra only (UNSUPPORTED in 2D). */
+enp_status enp_param_jacobian(enp_handle h, const double* u, double* dRdtheta);
+
+/* dtheta[b][j] = <w_b, dR_b/dtheta_j>: the parameter part of the adjoint.
+ * w: device [batch][m][E][Np]; dtheta: host [batch][n_theta]. Synchronises. */
+enp_status enp_param_vjp(enp_handle h, const double* u, const double* w, double* dtheta);
+
 /* enp_inner_product without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc,
  * such as a host application that owns all device memory through its own pool,

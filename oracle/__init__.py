@@ -61,6 +61,7 @@ def _load():
         lib.oracle_residual.argtypes = [P, P, P, P, P, I, P]
         lib.oracle_jvp.argtypes = [P, P, P, P, P, P, I, P]
         lib.oracle_vjp_entries.argtypes = [P, P, P, P, P, P, I, P]
+        lib.oracle_param_jacobian.argtypes = [P, P, P, P, I, P]
         lib.oracle_jacobian_coo.restype = LL
         lib.oracle_jacobian_coo.argtypes = [P, P, P, P, P, P, P, LL]
         _lib = lib
@@ -159,6 +160,17 @@ class Oracle:
         out = np.zeros(len(cols))
         self._lib.oracle_vjp_entries(self.h, _ptr(u), _ptr(w), _ptr(self.src),
                                      _ptr(self.dirichlet), _ptr(cols), len(cols), _ptr(out))
+        return out
+
+    def param_jacobian(self, u):
+        """dR/dtheta [n_theta, N] for theta = (D_1..D_m, c_in_1..c_in_{m-1},
+        phi_app_0..phi_app_3), one dual sweep per parameter."""
+        nt = 2 * self.prob.m + 3
+        out = np.zeros((nt, self.N))
+        u = _f64(u)
+        for j in range(nt):
+            self._lib.oracle_param_jacobian(self.h, _ptr(u), _ptr(self.src), _ptr(self.dirichlet),
+                                            j, _ptr(out[j]))
         return out
 
     def jacobian(self, u):

@@ -165,6 +165,9 @@ struct Problem {
   int J0axis = -1; double J0lo = 0, J0hi = 1;
   int p = 1, n = 2, q = 3, Np = 8, Nq = 27, Nfq = 9; double cip = 10.0;
   std::vector<double> xgl, wgl, xnode;
+  // parameter carrying the unit tangent in a dual evaluation, -1 none;
+  // theta = (D_1..D_m, c_in_1..c_in_{m-1}, phi_app_0..phi_app_3)
+  int theta_seed = -1;
 };
 
 inline int side_axis(int s) { return s / 2; }
@@ -253,20 +256,36 @@ void state_at(const Problem& P, int e, const double* phi, const double* gphi,
   }
 }
 
-// mu_k = D_k / RT (Eq. NE); a_k = F z_k (D_k - D_m); kappa as in Eq. charge2.
+// Physical coefficients as scalars of type T (a dual number carries the unit
+// tangent of the seeded parameter). mu_k = D_k / RT (Eq. NE);
+// a_k = F z_k (D_k - D_m); kappa = sum_{k<m} z_k (z_k mu_k - z_m mu_m) F^2 c_k (Eq. charge2).
+template <class T> T seeded(double v, bool on);
+template <> double seeded<double>(double v, bool) { return v; }
+template <> Dual seeded<Dual>(double v, bool on) { return Dual(v, on ? 1.0 : 0.0); }
+
+template <class T> T D_of(const Problem& P, int k) { return seeded<T>(P.D[k], P.theta_seed == k); }
+template <class T> T mig_of(const Problem& P, int k) {  // z_k mu_k F
+  return T(P.z[k] * P.F / P.RT) * D_of<T>(P, k);
+}
+template <class T> T a_of(const Problem& P, int k) {
+  return T(P.F * P.z[k]) * (D_of<T>(P, k) - D_of<T>(P, P.m - 1));
+}
+template <class T> T kc_of(const Problem& P, int k) {  // coefficient of c_k in kappa
+  return T(P.z[k] * P.F * P.F / P.RT) * (T(P.z[k]) * D_of<T>(P, k) - T(P.z[P.m - 1]) * D_of<T>(P, P.m - 1));
+}
+template <class T> T cin_of(const Problem& P, int k) {
+  return seeded<T>(P.cin[k], P.theta_seed == P.m + k);
+}
+template <class T> T phiapp_of(const Problem& P, int j) {
+  return seeded<T>(P.phiapp[j], P.theta_seed == 2 * P.m - 1 + j);
+}
+
 template <class T>
 T kappa_of(const Problem& P, const T* val) {
-  int m = P.m;
-  double zm = P.z[m - 1], mum = P.D[m - 1] / P.RT;
   T kap = T(0.0);
-  for (int k = 0; k < m - 1; ++k) {
-    double muk = P.D[k] / P.RT;
-    kap += T(P.z[k] * (P.z[k] * muk - zm * mum) * P.F * P.F) * val[k + 1];
-  }
+  for (int k = 0; k < P.m - 1; ++k) kap += kc_of<T>(P, k) * val[k + 1];
   return kap;
 }
-inline double a_coef(const Problem& P, int k) { return P.F * P.z[k] * (P.D[k] - P.D[P.m - 1]); }
-inline double mig_coef(const Problem& P, int k) { return P.z[k] * (P.D[k] / P.RT) * P.F; }
 
 // Butler-Volmer current J_n (Eq. bv) at a point of electrode j.
 template <class T>
@@ -280,7 +299,7 @@ T bv_current(const Problem& P, int j, const double* x, const T* val) {
     co = T(-1.0 / P.z[m - 1]) * s;
   }
   double fac = P.nel * P.F / P.RT;
-  T eta = T(P.phiapp[j]) - val[0];
+  T eta = phiapp_of<T>(P, j) - val[0];
   T ratio = co * T(1.0 / P.cref);
   T ratio_g = (P.gam == 1.0) ? ratio : pow(ratio, P.gam);
   return T(exchange_current(P, x)) * (exp(T(P.a1 * fac) * eta) - ratio_g * exp(T(-P.a2 * fac) * eta));
@@ -317,13 +336,13 @@ void element_rows(const Problem& P, int K, const T* u, const double* src, const 
         T kap = kappa_of(P, s.val);
         for (int d = 0; d < 3; ++d) {
           T gch = kap * s.grad[0][d];
-          for (int k = 0; k < P.m - 1; ++k) gch += T(a_coef(P, k)) * s.grad[k + 1][d];
+          for (int k = 0; k < P.m - 1; ++k) gch += a_of<T>(P, k) * s.grad[k + 1][d];
           G[0][d] = gch;
         }
         for (int k = 0; k < P.m - 1; ++k) {
           for (int d = 0; d < 3; ++d) {
-            T qk = T(uv[d]) - T(mig_coef(P, k)) * s.grad[0][d];
-            G[k + 1][d] = T(P.D[k]) * s.grad[k + 1][d] - s.val[k + 1] * qk;
+            T qk = T(uv[d]) - mig_of<T>(P, k) * s.grad[0][d];
+            G[k + 1][d] = D_of<T>(P, k) * s.grad[k + 1][d] - s.val[k + 1] * qk;
           }
         }
         for (int f = 0; f < NF; ++f)
@@ -384,31 +403,31 @@ void element_rows(const Problem& P, int K, const T* u, const double* src, const 
           // mass conservation rows, interior faces of Eq. NPDG
           for (int k = 0; k < P.m - 1; ++k) {
             int f = k + 1;
-            double Dk = P.D[k], mk = mig_coef(P, k);
+            T Dk = D_of<T>(P, k), mk = mig_of<T>(P, k);
             T jc = sm.val[f] - sp.val[f];
-            T qnm = T(un) - T(mk) * dnm[0];
-            T qnp = T(un) - T(mk) * dnp[0];
+            T qnm = T(un) - mk * dnm[0];
+            T qnp = T(un) - mk * dnp[0];
             T qavg = T(0.5) * (qnm + qnp);
-            Tn[f] += T(-0.5 * Dk) * jc;
-            S[f] += T(-0.5 * Dk) * (dnm[f] + dnp[f]) + T(Dk * delta) * jc
+            Tn[f] += T(-0.5) * Dk * jc;
+            S[f] += T(-0.5) * Dk * (dnm[f] + dnp[f]) + Dk * T(delta) * jc
                   + T(0.5) * (sm.val[f] * qnm + sp.val[f] * qnp) + T(0.5) * absval(qavg) * jc;
           }
           // charge conservation rows, interior faces of Eq. chargeDG
           T kapm = kappa_of(P, sm.val), kapp = kappa_of(P, sp.val);
           T jphi = sm.val[0] - sp.val[0];
           for (int k = 0; k < P.m - 1; ++k) {
-            int f = k + 1; double ak = a_coef(P, k);
-            Tn[0] += T(-0.5 * ak) * (sm.val[f] - sp.val[f]);
-            S[0] += T(-0.5 * ak) * (dnm[f] + dnp[f]);
+            int f = k + 1; T ak = a_of<T>(P, k);
+            Tn[0] += T(-0.5) * ak * (sm.val[f] - sp.val[f]);
+            S[0] += T(-0.5) * ak * (dnm[f] + dnp[f]);
           }
           Tn[0] += T(-0.5) * kapm * jphi;
           S[0] += T(-0.5) * (kapm * dnm[0] + kapp * dnp[0])
                 + T(0.5 * delta) * (kapm + kapp) * jphi;
         } else if (tag == TAG_INLET) {
-          for (int k = 0; k < P.m - 1; ++k) S[k + 1] += T(un * P.cin[k]);
+          for (int k = 0; k < P.m - 1; ++k) S[k + 1] += T(un) * cin_of<T>(P, k);
         } else if (tag == TAG_OUTLET) {
           for (int k = 0; k < P.m - 1; ++k) {
-            T qn = T(un) - T(mig_coef(P, k)) * dnm[0];
+            T qn = T(un) - mig_of<T>(P, k) * dnm[0];
             S[k + 1] += qn * sm.val[k + 1];
           }
         } else if (tag >= TAG_ELECTRODE0) {
@@ -421,19 +440,19 @@ void element_rows(const Problem& P, int K, const T* u, const double* src, const 
             gv[f] = dirv ? dirv[((size_t)f * P.NBF + bface) * P.Nfq + fpt] : 0.0;
           for (int k = 0; k < P.m - 1; ++k) {
             int f = k + 1;
-            double Dk = P.D[k], mk = mig_coef(P, k);
+            T Dk = D_of<T>(P, k), mk = mig_of<T>(P, k);
             T jc = sm.val[f] - T(gv[f]);
-            T qn = T(un) - T(mk) * dnm[0];
-            Tn[f] += T(-Dk) * jc;
-            S[f] += T(-Dk) * dnm[f] + T(Dk * delta) * jc
+            T qn = T(un) - mk * dnm[0];
+            Tn[f] += -Dk * jc;
+            S[f] += -Dk * dnm[f] + Dk * T(delta) * jc
                   + T(0.5) * (sm.val[f] + T(gv[f])) * qn + T(0.5) * absval(qn) * jc;
           }
           T kap = kappa_of(P, sm.val);
           T jphi = sm.val[0] - T(gv[0]);
           for (int k = 0; k < P.m - 1; ++k) {
-            int f = k + 1; double ak = a_coef(P, k);
-            Tn[0] += T(-ak) * (sm.val[f] - T(gv[f]));
-            S[0] += T(-ak) * dnm[f];
+            int f = k + 1; T ak = a_of<T>(P, k);
+            Tn[0] += -ak * (sm.val[f] - T(gv[f]));
+            S[0] += -ak * dnm[f];
           }
           Tn[0] += T(-1.0) * kap * jphi;
           S[0] += T(-1.0) * kap * dnm[0] + T(delta) * kap * jphi;
@@ -699,6 +718,29 @@ int oracle_vjp_entries(void* h, const double* u, const double* w, const double* 
       }
       ud[c].d = 0.0;
       out[t] = acc;
+    }
+  }
+  return 0;
+}
+
+// dR/dtheta_j on every row, exactly: one dual sweep with the unit tangent on
+// parameter j of theta = (D_1..D_m, c_in_1..c_in_{m-1}, phi_app_0..phi_app_3).
+int oracle_param_jacobian(void* h, const double* u, const double* src, const double* dirv,
+                          int j, double* out) {
+  Problem P = *static_cast<Problem*>(h);
+  if (j < 0 || j >= 2 * P.m + 3) return -1;
+  P.theta_seed = j;
+  size_t N = (size_t)P.NF * P.E * P.Np;
+  std::vector<Dual> ud(N);
+  for (size_t i = 0; i < N; ++i) ud[i] = Dual(u[i], 0.0);
+#pragma omp parallel
+  {
+    std::vector<Dual> rows(P.NF * P.Np);
+#pragma omp for schedule(dynamic, 4)
+    for (int K = 0; K < P.E; ++K) {
+      element_rows<Dual>(P, K, ud.data(), src, dirv, rows.data());
+      for (int f = 0; f < P.NF; ++f)
+        for (int i = 0; i < P.Np; ++i) out[((size_t)f * P.E + K) * P.Np + i] = rows[f * P.Np + i].d;
     }
   }
   return 0;

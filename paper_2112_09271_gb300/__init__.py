@@ -153,6 +153,9 @@ _PROTOS = [
     ("enp_fgmres_solve", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_fgmres_solve_f32", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_newton_solve", _I, [_V, _V, _V, _V]),
+    ("enp_param_count", _I, [_V, ctypes.POINTER(_I)]),
+    ("enp_param_jacobian", _I, [_V, _V, _V]),
+    ("enp_param_vjp", _I, [_V, _V, _V, _V]),
     ("enp_inner_product_noalloc", _I, [_V, _V, _LL, _I, _V, _V]),
     ("enp_last_error", ctypes.c_char_p, [_V]),
 ]
@@ -383,9 +386,63 @@ class Operator:
         out["status"] = rc
         return out
 
+    @property
+    def n_theta(self):
+        c = ctypes.c_int()
+        self._check(self._lib.enp_param_count(self.h, ctypes.byref(c)))
+        return c.value
+
+    def param_jacobian(self, u, out=None):
+        """dR/dtheta for theta = (D_1..D_m, c_in_1..c_in_{m-1}, phi_app_0..3):
+        a CUDA tensor [n_theta, batch * m * E * Np]."""
+        import torch
+        nt = self.n_theta
+        out = torch.empty((nt, self.n), dtype=torch.float64, device="cuda") if out is None else out
+        self._check(self._lib.enp_param_jacobian(self.h, _dptr(u, torch.float64),
+                                                 _dptr(out, torch.float64)))
+        return out
+
+    def param_vjp(self, u, w):
+        """<w, dR/dtheta_j> per operating point: numpy [batch, n_theta]."""
+        import torch
+        out = np.zeros((self.batch, self.n_theta))
+        self._check(self._lib.enp_param_vjp(self.h, _dptr(u, torch.float64),
+                                            _dptr(w, torch.float64),
+                                            ctypes.c_void_p(out.ctypes.data)))
+        return out
+
     def vjp(self, u, w, out=None):
         import torch
         out = self._new(torch.float64) if out is None else out
         self._check(self._lib.enp_vjp(self.h, _dptr(u, torch.float64), _dptr(w, torch.float64),
                                       _dptr(out, torch.float64)))
         return out
+
+
+def residual_function(op):
+    """A torch.autograd.Function for u -> R(u) with the operator ``op``: the
+    forward pass runs enp_residual, the backward pass enp_vjp (J(u)^T g) and
+    enp_param_vjp (the gradient with respect to theta, returned through the
+    ``theta`` input, a tensor of n_theta entries whose value is not used: the
+    parameters live in the handle). Element-local recomputation, no stored
+    quadrature-point state."""
+    import torch
+
+    class _Residual(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u, theta):
+            ctx.save_for_backward(u)
+            return op.residual(u.detach().contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            (u,) = ctx.saved_tensors
+            g = g.contiguous()
+            gu = op.vjp(u.detach().contiguous(), g) if ctx.needs_input_grad[0] else None
+            gt = None
+            if ctx.needs_input_grad[1]:
+                d = op.param_vjp(u.detach().contiguous(), g).sum(axis=0)
+                gt = torch.tensor(d, dtype=torch.float64, device=u.device)
+            return gu, gt
+
+    return _Residual.apply

@@ -41,6 +41,13 @@ void fill_phys(const OpParams& P, enp::PhysT<T>& o) {
   o.J0inv_half = P.J0hi > P.J0lo ? (T)(1.0 / (0.5 * (P.J0hi - P.J0lo))) : (T)0;
   o.cip = (T)P.cip;
   o.bv_ox = P.bv_ox;
+  const double zm = P.z[m - 1];
+  for (int k = 0; k < enp::kMaxSpecies; ++k) {
+    o.dmig[k] = (T)(P.z[k] * P.F / P.RT);
+    o.da[k] = (T)(P.F * P.z[k]);
+    o.dkc_own[k] = (T)(P.z[k] * P.z[k] * P.F * P.F / P.RT);
+    o.dkc_m[k] = (T)(-P.z[k] * zm * P.F * P.F / P.RT);
+  }
 }
 
 enp_status fail(enp_handle h, enp_status s, const std::string& msg) {
@@ -279,6 +286,7 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
     P.kcoef[k] = ph->z[k] * (ph->z[k] * muk - zm * mum) * ph->F * ph->F;  // kappa coefficient
   }
   P.F = ph->F;
+  P.RT = ph->RT;
   P.vel_kind = ph->velocity_kind;
   for (int i = 0; i < 8; ++i) P.vp[i] = ph->vel_params[i];
   P.vel_coef = ph->velocity_kind == ENP_VEL_PLATE
@@ -298,6 +306,8 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
   P.batch_stride = (long long)P.NF * P.E * P.Np;
   fill_phys<double>(P, P.pd);
   fill_phys<float>(P, P.pf);
+  P.batch = disc->batch;
+  P.n_theta = 2 * P.m + 3;
   h->batch = disc->batch;
   h->n_dof = P.batch_stride;
   h->stream = (cudaStream_t)stream;
@@ -473,6 +483,21 @@ enp_status enp_jvp_f32(enp_handle h, const float* u, const float* v, float* jv) 
   if (!h || !u || !v || !jv) return fail(h, ENP_ERR_INVALID_ARG, "null argument");
   cudaError_t e = enp::launch_op<float>(1, h->prm, h->d_tab, u, v, jv, h->batch, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "operator launch (f32)");
+  return ENP_OK;
+}
+
+enp_status enp_param_count(enp_handle h, int* n_theta) {
+  if (!h || !n_theta) return ENP_ERR_INVALID_ARG;
+  *n_theta = h->prm.n_theta;
+  return ENP_OK;
+}
+
+enp_status enp_param_jacobian(enp_handle h, const double* u, double* dRdtheta) {
+  if (!h || !u || !dRdtheta) return fail(h, ENP_ERR_INVALID_ARG, "null argument");
+  if (h->prm.dim != 3) return fail(h, ENP_ERR_UNSUPPORTED, "dR/dtheta is built for hexahedra");
+  cudaError_t e = enp::launch_op<double>(enp::kParam, h->prm, h->d_tab, u, nullptr, dRdtheta,
+                                         h->batch * h->prm.n_theta, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "parameter Jacobian launch");
   return ENP_OK;
 }
 

@@ -19,7 +19,9 @@ constexpr int kMaxQ = kMaxP + 2;
 // kBlockCol: column blockIdx.y of every element-diagonal block of J(u): the
 // J v pass with v = the local unit vector e_col in every element and the
 // neighbour's tangent set to zero, written to blk[e][row][col].
-enum OpMode : int { kResidual = 0, kJvp = 1, kVjp = 2, kBlockCol = 3 };
+// kParam: dR/dtheta_j for every parameter j (grid.y = batch * n_theta), the
+// residual evaluated with forward-tangent coefficients seeded on theta_j.
+enum OpMode : int { kResidual = 0, kJvp = 1, kVjp = 2, kBlockCol = 3, kParam = 4 };
 
 enum FaceTag : int { kInterior = 0, kWall = 1, kInlet = 2, kOutlet = 3, kDirichlet = 4, kElectrode0 = 5 };
 
@@ -34,6 +36,10 @@ struct PhysT {
   T J0, e1, e2, gam, gam1, inv_cref, ox_species_scale, ox_charge_scale, phiapp[4];
   T J0lo, J0half, J0inv_half;                 // profile: r = (x - lo - half) / half
   T cip;
+  // derivatives of the coefficients with respect to the diffusivities (dR/dtheta):
+  // dmig_k/dD_k = z_k F/RT, da_k/dD_k = F z_k (and -F z_k for D_m),
+  // dkappa_k/dD_k = z_k^2 F^2/RT, dkappa_k/dD_m = -z_k z_m F^2/RT
+  T dmig[kMaxSpecies], da[kMaxSpecies], dkc_own[kMaxSpecies], dkc_m[kMaxSpecies];
   int vel_kind, velA, velN, bv_ox, J0axis;
 };
 
@@ -64,6 +70,9 @@ struct OpParams {
   long long batch_stride;     // entries per operating point (NF * E * Np)
   PhysT<double> pd;           // the coefficients above, in each kernel arithmetic type
   PhysT<float> pf;
+  double RT;
+  int batch;                  // operating points
+  int n_theta;                // parameters of dR/dtheta: D_1..D_m, c_in_1..c_in_{m-1}, phi_app_0..3
 };
 
 template <class R> __host__ __device__ __forceinline__ const PhysT<R>& phys(const OpParams& p);

@@ -64,6 +64,9 @@ static cudaError_t launch_mode(int mode, const OpParams& prm, const Tables* t, c
     case kJvp: return launch_one<DIM, P, NF, kJvp, R>(prm, t, u, v, out, batch, s);
     case kVjp: return launch_one<DIM, P, NF, kVjp, R>(prm, t, u, v, out, batch, s);
     case kBlockCol: return launch_one<DIM, P, NF, kBlockCol, R>(prm, t, u, v, out, batch, s);
+    case kParam:
+      if constexpr (DIM == 3) return launch_one<DIM, P, NF, kParam, R>(prm, t, u, v, out, batch, s);
+      return cudaErrorNotSupported;
   }
   return cudaErrorInvalidValue;
 }

@@ -67,17 +67,17 @@ __device__ __forceinline__ void velocity(const PhysT<R>& p, const R* x, R* uv) {
 }
 
 // J_0 = 3/5 Jbar [2 - ((t - w/2)/(w/2))^2] (Sec. 5.2), or constant.
-template <class R>
-__device__ __forceinline__ R exchange_current(const PhysT<R>& p, const R* x) {
+template <class C, class R>
+__device__ __forceinline__ C exchange_current(const PhysT<C>& p, const R* x) {
   if (p.J0axis < 0) return p.J0;
-  const R r = (x[p.J0axis] - p.J0lo - p.J0half) * p.J0inv_half;
+  const C r = (x[p.J0axis] - p.J0lo - p.J0half) * p.J0inv_half;
   return R(0.6) * p.J0 * (R(2) - r * r);
 }
 
 // Volume flux at one point (Eq. NPDG and Eq. chargeDG volume terms): the
 // coefficient Sf of phi_i and the vector Gf multiplying grad phi_i.
-template <int NF, int DIM, class S, class R>
-__device__ __forceinline__ void volume_flux(const PhysT<R>& p, const S* c, const S (*g)[3],
+template <int NF, int DIM, class S, class R, class C = R>
+__device__ __forceinline__ void volume_flux(const PhysT<C>& p, const S* c, const S (*g)[3],
                                             const R* uv, S* Sf, S (*Gf)[3]) {
   S kap = S(R(0));
 #pragma unroll
@@ -138,8 +138,8 @@ __device__ __forceinline__ void volume_flux_adjoint(const PhysT<R>& p, const R* 
 // cm, dm: values and normal derivatives (along n = this element's outward
 // normal) on this side; cp, dp on the other side. Returns the coefficient Sf
 // of phi_i and Tf of grad phi_i . n. Upwind reading: {c q}.n + |{q}.n|/2 [[c]].
-template <int NF, class S, class R>
-__device__ __forceinline__ void face_interior_flux(const PhysT<R>& p, const S* cm, const S* dm,
+template <int NF, class S, class R, class C = R>
+__device__ __forceinline__ void face_interior_flux(const PhysT<C>& p, const S* cm, const S* dm,
                                                    const S* cp, const S* dp, R un, R delta,
                                                    S* Sf, S* Tf) {
   S kapm = S(R(0)), kapp = S(R(0));
@@ -147,7 +147,7 @@ __device__ __forceinline__ void face_interior_flux(const PhysT<R>& p, const S* c
 #pragma unroll
   for (int k = 0; k < NF - 1; ++k) {
     const int f = k + 1;
-    const R Dk = p.D[k], mg = p.mig[k], ak = p.acoef[k];
+    const C Dk = p.D[k], mg = p.mig[k], ak = p.acoef[k];
     const S jc = cm[f] - cp[f];
     const S qnm = un - mg * dm[0];
     const S qnp = un - mg * dp[0];
@@ -209,8 +209,8 @@ __device__ __forceinline__ void face_interior_adjoint(const PhysT<R>& p, const R
 }
 
 // Concentration of the Butler-Volmer oxidant (Eq. substitution if it is c_m).
-template <int NF, class S, class R>
-__device__ __forceinline__ S oxidant_conc(const PhysT<R>& p, const S* c) {
+template <int NF, class S, class R, class C = R>
+__device__ __forceinline__ S oxidant_conc(const PhysT<C>& p, const S* c) {
   if (p.bv_ox < NF - 1) return c[p.bv_ox + 1];
   S s = S(R(0));
 #pragma unroll
@@ -221,10 +221,10 @@ __device__ __forceinline__ S oxidant_conc(const PhysT<R>& p, const S* c) {
 // Own-row flux on a boundary face (the boundary integrals of Eq. NPDG and
 // Eq. chargeDG; DIRICHLET is the Nitsche form of the interior terms with the
 // exterior state g, used for manufactured solutions).
-template <int NF, class S, class R>
-__device__ __forceinline__ void face_boundary_flux(const PhysT<R>& p, int tag, const S* cm,
+template <int NF, class S, class R, class C = R>
+__device__ __forceinline__ void face_boundary_flux(const PhysT<C>& p, int tag, const S* cm,
                                                    const S* dm, const R* g, R un, R delta,
-                                                   const R* x, R phiapp, S* Sf, S* Tf) {
+                                                   const R* x, C phiapp, S* Sf, S* Tf) {
 #pragma unroll
   for (int f = 0; f < NF; ++f) { Sf[f] = S(R(0)); Tf[f] = S(R(0)); }
   if (tag == kInlet) {
@@ -235,10 +235,10 @@ __device__ __forceinline__ void face_boundary_flux(const PhysT<R>& p, int tag, c
     for (int k = 0; k < NF - 1; ++k) Sf[k + 1] = (un - p.mig[k] * dm[0]) * cm[k + 1];
   } else if (tag >= kElectrode0) {
     if (p.bv_ox < 0) return;
-    const S co = oxidant_conc<NF, S, R>(p, cm);
+    const S co = oxidant_conc<NF, S, R, C>(p, cm);
     const S eta = phiapp - cm[0];
     S r = p.inv_cref * co;
-    if (p.gam != 1.0) r = powv(r, p.gam);
+    if (valof(p.gam) != R(1)) r = powv(r, valof(p.gam));
     const S Jn = exchange_current(p, x) * (expv(p.e1 * eta) - r * expv((-p.e2) * eta));
     if (p.bv_ox < NF - 1) Sf[p.bv_ox + 1] = p.ox_species_scale * Jn;
     Sf[0] = p.ox_charge_scale * Jn;
@@ -247,7 +247,7 @@ __device__ __forceinline__ void face_boundary_flux(const PhysT<R>& p, int tag, c
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) {
       const int f = k + 1;
-      const R Dk = p.D[k], ak = p.acoef[k];
+      const C Dk = p.D[k], ak = p.acoef[k];
       const S jc = cm[f] - g[f];
       const S qn = un - p.mig[k] * dm[0];
       Tf[f] = (-Dk) * jc;
@@ -282,7 +282,7 @@ __device__ __forceinline__ void face_boundary_adjoint(const PhysT<R>& p, int tag
     const R eta = phiapp - cm[0];
     const R E1 = expv(p.e1 * eta), E2 = expv((-p.e2) * eta);
     R r = p.inv_cref * co, drdc = p.inv_cref;
-    if (p.gam != R(1)) {
+    if (valof(p.gam) != R(1)) {
       const R rb = r;
       r = powv(rb, p.gam);
       drdc = p.gam * powv(rb, p.gam1) * p.inv_cref;

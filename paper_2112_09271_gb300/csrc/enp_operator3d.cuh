@@ -114,6 +114,42 @@ __device__ __forceinline__ int face_node_pad(int a, int k, int j1, int j2) {
   return j1 + X * (j2 + N * k);
 }
 
+// The coefficients as forward tangents seeded on parameter j of
+// theta = (D_1..D_m, c_in_1..c_in_{m-1}, phi_app_0..phi_app_3).
+template <class R>
+__device__ PhysT<Tan<R>> seed_phys(const PhysT<R>& p, int m, int j) {
+  PhysT<Tan<R>> q;
+  for (int k = 0; k < kMaxSpecies; ++k) {
+    q.D[k] = Tan<R>(p.D[k]); q.cin[k] = Tan<R>(p.cin[k]); q.mig[k] = Tan<R>(p.mig[k]);
+    q.acoef[k] = Tan<R>(p.acoef[k]); q.kcoef[k] = Tan<R>(p.kcoef[k]); q.z[k] = Tan<R>(p.z[k]);
+    q.zratio[k] = Tan<R>(p.zratio[k]);
+    q.dmig[k] = Tan<R>(p.dmig[k]); q.da[k] = Tan<R>(p.da[k]);
+    q.dkc_own[k] = Tan<R>(p.dkc_own[k]); q.dkc_m[k] = Tan<R>(p.dkc_m[k]);
+  }
+  q.neg_inv_zm = Tan<R>(p.neg_inv_zm);
+  for (int i = 0; i < 8; ++i) q.vp[i] = Tan<R>(p.vp[i]);
+  q.vel_coef = Tan<R>(p.vel_coef);
+  q.J0 = Tan<R>(p.J0); q.e1 = Tan<R>(p.e1); q.e2 = Tan<R>(p.e2);
+  q.gam = Tan<R>(p.gam); q.gam1 = Tan<R>(p.gam1); q.inv_cref = Tan<R>(p.inv_cref);
+  q.ox_species_scale = Tan<R>(p.ox_species_scale); q.ox_charge_scale = Tan<R>(p.ox_charge_scale);
+  for (int i = 0; i < 4; ++i) q.phiapp[i] = Tan<R>(p.phiapp[i]);
+  q.J0lo = Tan<R>(p.J0lo); q.J0half = Tan<R>(p.J0half); q.J0inv_half = Tan<R>(p.J0inv_half);
+  q.cip = Tan<R>(p.cip);
+  q.vel_kind = p.vel_kind; q.velA = p.velA; q.velN = p.velN; q.bv_ox = p.bv_ox; q.J0axis = p.J0axis;
+  if (j < m) {                        // D_j: D, z_j mu_j F, the a_k and kappa coefficients
+    if (j < m - 1) { q.D[j].d = R(1); q.mig[j].d = p.dmig[j]; }
+    for (int k = 0; k < m - 1; ++k) {
+      q.acoef[k].d = (k == j ? p.da[k] : R(0)) - (j == m - 1 ? p.da[k] : R(0));
+      q.kcoef[k].d = (k == j ? p.dkc_own[k] : R(0)) + (j == m - 1 ? p.dkc_m[k] : R(0));
+    }
+  } else if (j < 2 * m - 1) {         // c_in of species j - m
+    q.cin[j - m].d = R(1);
+  } else {                            // phi_app of electrode j - (2m - 1)
+    q.phiapp[j - (2 * m - 1)].d = R(1);
+  }
+  return q;
+}
+
 template <int P, int NF, int MODE>
 struct Smem3 {
   static constexpr int N = P + 1, Q = P + 2;
@@ -121,7 +157,7 @@ struct Smem3 {
   static constexpr int NN = N * N * N, NQ = Q * Q * Q, FN = N * N, FQ = Q * Q;
   static constexpr int NNP = NX * N * N;                 // padded nodal array
   static constexpr int FNP = NX * N;                     // padded face-node array
-  static constexpr int NV = MODE == kResidual ? 1 : 2;
+  static constexpr int NV = (MODE == kResidual || MODE == kParam) ? 1 : 2;
   static constexpr int NA = NV * NF;                     // arrays carried through the volume
   static constexpr int kX = NA * NNP;                    // element data
   static constexpr int kOut = NF * NNP;                  // rows
@@ -168,9 +204,12 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   const int e = blockIdx.x * EB + es;
   const bool valid = e < prm.E;
   const int ee = valid ? e : prm.E - 1;   // invalid slots shadow a valid element, write nothing
+  constexpr bool kPar = MODE == kParam;
   const int col = kBlk ? (int)blockIdx.y : -1;
-  const long long boff = kBlk ? 0 : (long long)blockIdx.y * prm.batch_stride;
-  const int bidx = kBlk ? 0 : (int)blockIdx.y;
+  const int bidx = kBlk ? 0 : (kPar ? (int)blockIdx.y / prm.n_theta : (int)blockIdx.y);
+  const int theta_j = kPar ? (int)blockIdx.y % prm.n_theta : -1;
+  const long long boff = kBlk ? 0 : (long long)bidx * prm.batch_stride;
+  const long long ooff = kPar ? ((long long)theta_j * prm.batch + bidx) * prm.batch_stride : boff;
   const long long EN = (long long)prm.E * NN;
 
   int idx[3];
@@ -255,7 +294,23 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
         for (int a = 0; a < 3; ++a) g0[f][a] = V[(1 + a) * NQ + pt] * sc[a];
       }
       R oS[NF], oG[NF][3];
-      if (MODEc == kResidual) {
+      if (MODEc == kParam) {
+        const PhysT<Tan<R>> pt = seed_phys<R>(ph, NF, theta_j);
+        Tan<R> ct[NF], gt[NF][3], Sf[NF], Gf[NF][3];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          ct[f] = Tan<R>(c0[f]);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) gt[f][a] = Tan<R>(g0[f][a]);
+        }
+        volume_flux<NF, 3, Tan<R>, R, Tan<R>>(pt, ct, gt, uv, Sf, Gf);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          oS[f] = Sf[f].d;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) oG[f][a] = Gf[f][a].d;
+        }
+      } else if (MODEc == kResidual) {
         volume_flux<NF, 3, R, R>(ph, c0, g0, uv, oS, oG);
 #pragma unroll
         for (int f = 0; f < NF; ++f)
@@ -354,7 +409,7 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
       }
     }
     if (s < 5) prefetch(s + 1);
-    const bool active = !(tag == kWall || (tag == kInlet && MODEc != kResidual));
+    const bool active = !(tag == kWall || (tag == kInlet && MODEc != kResidual && MODEc != kParam));
     __syncthreads();
     // layer values and reference normal derivatives at the face nodes
     const int lay = hi ? N - 1 : 0, layo = hi ? 0 : N - 1;
@@ -419,7 +474,23 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
 #pragma unroll
       for (int f = 0; f < NF; ++f) { oS[f] = R(0); oT[f] = R(0); }
       if (active) {
-        if (MODEc == kResidual) {
+        if (MODEc == kParam) {
+          const PhysT<Tan<R>> pt = seed_phys<R>(ph, NF, theta_j);
+          const Tan<R> phit(phiapp, (tag >= kElectrode0 && theta_j == 2 * NF - 1 + tag - kElectrode0)
+                                        ? R(1) : R(0));
+          Tan<R> tm[NF], tdm[NF], tp[NF], tdp[NF], Sf[NF], Tf[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            tm[f] = Tan<R>(cm[f]); tdm[f] = Tan<R>(dm[f]);
+            tp[f] = Tan<R>(cp[f]); tdp[f] = Tan<R>(dp[f]);
+          }
+          if (boundary)
+            face_boundary_flux<NF, Tan<R>, R, Tan<R>>(pt, tag, tm, tdm, g, un, delta, xp, phit, Sf, Tf);
+          else
+            face_interior_flux<NF, Tan<R>, R, Tan<R>>(pt, tm, tdm, tp, tdp, un, delta, Sf, Tf);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) { oS[f] = Sf[f].d; oT[f] = Tf[f].d; }
+        } else if (MODEc == kResidual) {
           if (boundary) face_boundary_flux<NF, R, R>(ph, tag, cm, dm, g, un, delta, xp, phiapp, oS, oT);
           else face_interior_flux<NF, R, R>(ph, cm, dm, cp, dp, un, delta, oS, oT);
         } else {
@@ -503,7 +574,7 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
     } else {
       for (int t = tid; t < NF * NN; t += NT) {
         const int f = t / NN, i = t % NN;
-        out[boff + f * EN + (long long)e * NN + i] = RO[f * NNP + padded_node<N>(i)];
+        out[ooff + f * EN + (long long)e * NN + i] = RO[f * NNP + padded_node<N>(i)];
       }
     }
   }

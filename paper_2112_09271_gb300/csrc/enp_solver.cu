@@ -431,6 +431,8 @@ struct SolverState {
   void* V = nullptr;
   void* Z = nullptr;
   size_t krylov_bytes = 0;
+  double* dRdtheta = nullptr;     // parameter Jacobian workspace [n_theta][batch][n]
+  size_t dRdtheta_count = 0;
 };
 
 }  // namespace
@@ -489,7 +491,7 @@ void enp_solver_free(enp_handle h) {
   SolverState& S = h->solver->s;
   cudaFree(S.blocks); cudaFree(S.binv); cudaFree(S.gj_work); cudaFree(S.d_flag);
   cudaFree(S.blocks32); cudaFree(S.u32);
-  cudaFree(S.part); cudaFree(S.dsmall); cudaFree(S.V);
+  cudaFree(S.part); cudaFree(S.dsmall); cudaFree(S.V); cudaFree(S.dRdtheta);
   delete h->solver;
   h->solver = nullptr;
 }
@@ -922,4 +924,24 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
   }
   cleanup();
   return status;
+}
+
+// dtheta[b][j] = <w_b, dR_b/dtheta_j> for theta = (D_1..D_m, c_in_1..c_in_{m-1},
+// phi_app_0..phi_app_3): the parameter part of the adjoint.
+extern "C" enp_status enp_param_vjp(enp_handle h, const double* u, const double* w,
+                                    double* dtheta) {
+  if (!h || !u || !w || !dtheta) return ENP_ERR_INVALID_ARG;
+  SolverState& S = state_of(h);
+  const int nt = h->prm.n_theta, B = h->batch;
+  const long long n = h->n_dof;
+  cudaError_t e = ensure(&S.dRdtheta, S.dRdtheta_count, (size_t)nt * B * n);
+  if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc parameter Jacobian");
+  enp_status st = enp_param_jacobian(h, u, S.dRdtheta);
+  if (st != ENP_OK) return st;
+  if ((e = small(h, (size_t)B * nt)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc small");
+  if ((e = multidot<double>(h, S.dRdtheta, (long long)B * n, nt, w, S.dsmall)) != cudaSuccess)
+    return cuda_err(h, e, "parameter dots");
+  e = cudaMemcpyAsync(dtheta, S.dsmall, sizeof(double) * B * nt, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "parameter vjp");
 }

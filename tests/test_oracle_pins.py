@@ -404,3 +404,41 @@ def test_block_diagonal_and_block_solve_are_consistent():
     y = orc.block_jacobi_apply(blocks, x).reshape(P.n_fields, P.E, P.Np)
     np.testing.assert_allclose(blocks[e] @ y[:, e].reshape(-1),
                                x.reshape(P.n_fields, P.E, P.Np)[:, e].reshape(-1), rtol=1e-10)
+
+
+# ------------------------------------------------------------ dR/dtheta
+def _perturb(P, j, h):
+    """The problem with parameter j of theta = (D_1..D_m, c_in_1..c_in_{m-1},
+    phi_app_0..3) shifted by h."""
+    m = P.m
+    D, cin, phi = list(P.D), list(P.c_in), list(P.bv_phi_app)
+    if j < m:
+        D[j] += h
+    elif j < 2 * m - 1:
+        cin[j - m] += h
+    else:
+        phi[j - (2 * m - 1)] += h
+    return _with(P, D=D, c_in=cin, bv_phi_app=phi)
+
+
+@pytest.mark.parametrize("cfg", ["cube_n2_p2", "channel_n1"])
+def test_param_jacobian_matches_central_differences(cfg):
+    """The dual sweep seeded on each parameter (D_k through mu_k, a_km and kappa
+    of Eq. NE / Eq. charge2; c_in through the inlet term; phi_app through
+    Eq. bv) against central differences of R in that parameter."""
+    P = W.config(cfg)
+    tags = [t.copy() for t in P.tags]
+    tags[0][:] = W.INLET  # inlet, outlet and both electrodes present
+    P = _with(P, tags=tags)
+    u = W.random_state(P, 3)
+    dR = oracle.Oracle(P).param_jacobian(u)
+    assert dR.shape[0] == 2 * P.m + 3
+    for j in range(dR.shape[0]):
+        base = ([P.D[k] for k in range(P.m)] + list(P.c_in[: P.m - 1]) + list(P.bv_phi_app))[j]
+        h = 1e-6 * max(abs(base), 1e-3)
+        fd = (oracle.Oracle(_perturb(P, j, h)).residual(u)
+              - oracle.Oracle(_perturb(P, j, -h)).residual(u)) / (2 * h)
+        scale = max(np.abs(dR[j]).max(), 1e-300)
+        if np.abs(fd).max() < 1e-12 and np.abs(dR[j]).max() < 1e-12:
+            continue  # electrodes 2, 3 absent: both derivatives vanish
+        assert np.abs(dR[j] - fd).max() <= 1e-6 * scale, (j, np.abs(dR[j] - fd).max(), scale)
