@@ -11,7 +11,9 @@ block apply) per second, in GDOF/s, summed over ranks. Each step is timed with
 CUDA events on the launching stream; between steps a 512 MB buffer is written
 to flush the 129 MB L2 (outside the events). The block-Jacobi setup, FGMRES and
 Newton rows run in a full solve of the cube16_p3 workload after the timed
-steps, FP64 and mixed precision, reported under `solve`.
+steps, FP64 and mixed precision, reported under `solve`; the batched
+operating-point sweep of the plate reactor (graph-captured Krylov cycles) is
+reported under `batched_solve`.
 
 Extra keys: per-operator throughput (`ops`), the roofline of the dominant kernel
 (`roofline`), the CPU oracle on a bounded sample (`cpu_baseline`), the same
@@ -49,13 +51,15 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
 # the hash of the operator source it was taken from (stale -> reported null).
 TRAFFIC = {
-    ("21a4a7a60dc3", "jvp_f64", "channel64_p3"): 134.96e6,
+    ("5b4d5098ed56", "jvp_f64", "channel64_p3"): 134.67e6,
+    ("5b4d5098ed56", "jvp_f32", "channel64_p3"): 57.11e6,
+    ("5b4d5098ed56", "bj_apply_f32", "channel64_p3"): 4935.10e6,
 }
 
 
 def _kernel_hash():
     h = hashlib.sha1()
-    for f in ("enp_operator.cuh", "enp_common.cuh"):
+    for f in ("enp_operator.cuh", "enp_operator3d.cuh", "enp_common.cuh", "enp_solver.cu"):
         with open(os.path.join(ROOT, "paper_2112_09271_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -205,6 +209,38 @@ def run_solves(enp, W, name):
     return out
 
 
+def run_batched_solve(enp, W, name, batch=8, volts=(0.01, 0.08)):
+    """The operating-point sweep of the plate reactor (Sec. 5.2): `batch`
+    applied cathode potentials (anode at 0), all solved in one batched Newton
+    run whose FGMRES restart cycles replay a captured CUDA graph. FP64 and
+    mixed (FP32 inner operator, FP32 block inverses), initial guess c = c_in,
+    Phi = phi_app / 2."""
+    import torch
+    prob = W.config(name)
+    phis = 38.92 * np.linspace(volts[0], volts[1], batch)  # F/RT at 298.15 K
+    op = enp.Operator(prob, batch=batch)
+    op.autotune()
+    op.set_phi_app(np.array([[ph, 0.0, 0.0, 0.0] for ph in phis]))
+    u0 = W.reactor_initial_state(prob, phis)
+    out = {"workload": name, "batch": batch, "volts": list(volts), "n_dof_per_point": prob.n_dof,
+           "rtol": 1e-10}
+    for label, kw in (("fp64_graph", dict(bj_storage=enp.BJ_F64, mixed=False)),
+                      ("mixed_graph", dict(bj_storage=enp.BJ_F32, mixed=True))):
+        u = torch.tensor(u0, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.newton_solve(u, max_it=30, rtol=1e-10, krylov_restart=50, krylov_max_it=4000,
+                             krylov_rtol=1e-3, raise_on_fail=False, graph=True, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[label] = {"seconds": dt, "points_per_second": batch / dt,
+                      "newton_iterations": st["iterations"],
+                      "krylov_iterations": st["krylov_iterations"],
+                      "converged": bool(st["converged"]),
+                      "final_relative_residual": st["residual_norm"] / st["initial_norm"]}
+    return out
+
+
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
@@ -243,6 +279,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--solve-workload", default="cube16_p3")
+    ap.add_argument("--only", default=None,
+                    help="time one operator alone (for profiling): residual_f64, jvp_f64, "
+                         "vjp_f64, jvp_f32, bj_apply_f32; no autotune, solves or e2e")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -277,10 +316,18 @@ def main():
     jv32 = torch.empty_like(u32)
     cm = torch.empty(prob.E * prob.Np, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    op.block_jacobi_setup(u, enp.BJ_F32)   # preconditioner set up once, outside the steps
+    if args.only:
+        tuned = [0] * 5
+        if args.only == "bj_apply_f32":
+            op.block_jacobi_setup(u, enp.BJ_F32)
+    else:
+        tuned = op.autotune()                  # launch shape per operator, before any timing
+        op.block_jacobi_setup(u, enp.BJ_F32)   # preconditioner set up once, outside the steps
     ops = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32", "bj_apply_f32", "recover_cm",
            "inner_product"]
     applications = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32", "bj_apply_f32"]
+    if args.only:
+        ops, applications = [args.only], [args.only]
     launches = {"residual_f64": 1, "jvp_f64": 1, "vjp_f64": 1, "jvp_f32": 1, "bj_apply_f32": 1,
                 "recover_cm": 1, "inner_product": 2}
     launches_per_step = sum(launches.values())
@@ -350,6 +397,14 @@ def main():
 
     per_op = {nm: {"ms": t_ops[nm] / args.steps,
                    "GDOF_s": n / (t_ops[nm] / args.steps * 1e-3) / 1e9} for nm in ops}
+    if args.only:
+        if rank == 0:
+            print(json.dumps({"only": args.only, "ops": per_op, "kernel_hash": _kernel_hash()}),
+                  flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     # roofline of the dominant kernel (the FP64 operator: ALU-bound on GB300)
     dom = max(("residual_f64", "jvp_f64", "vjp_f64"), key=lambda k: t_ops[k])
     if t_ops["jvp_f64"] >= 0.95 * t_ops[dom]:
@@ -423,9 +478,10 @@ def main():
            "ms_per_step": e2e_ms}
 
     del flush
-    solve = None
+    solve = batched = None
     if rank == 0 and not args.no_solve:
         solve = run_solves(enp, W, args.solve_workload)
+        batched = run_batched_solve(enp, W, "reactor_n2_p2")
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(prob)
@@ -440,8 +496,11 @@ def main():
                            "step": "R f64, J v f64, J^T w f64, J v f32, block-Jacobi apply "
                                    "(FP32 inverses), c_m recovery, inner product",
                            "applications_per_step": len(applications),
+                           "elements_per_block": dict(zip(["residual_f64", "jvp_f64", "vjp_f64",
+                                                           "jvp_f32", "residual_f32"], tuned)),
                            "l2": "flushed between steps (512 MB write)"},
                 "ops": per_op, "roofline": roof, "roofline_hbm": roof_hbm, "solve": solve,
+                "batched_solve": batched,
                 "cpu_baseline": cb, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "kernel_hash": kh}

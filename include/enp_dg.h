@@ -187,6 +187,9 @@ typedef struct {
   int max_it;    /* total iterations */
   double rtol;   /* stop when ||b - A x|| <= max(rtol ||b||, atol) */
   double atol;
+  int graph;     /* 1: capture one restart cycle in a CUDA graph and replay it (one
+                    launch and one host read per cycle; the graph always runs whole
+                    cycles, a converged point stays frozen) */
 } enp_krylov_opts;
 
 typedef struct {
@@ -237,6 +240,14 @@ typedef struct {
  * opts->krylov.rtol. Synchronises. Errors: NOT_CONVERGED, NONFINITE, OOM, CUDA. */
 enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* opts,
                             enp_newton_stats* stats);
+
+/* Choose the launch shape of the hexahedral operator kernel for this handle's
+ * degree and field count: for each of R (FP64), J v (FP64), J^T w (FP64),
+ * J v (FP32) and R (FP32), every feasible number of elements per thread block
+ * is timed on this mesh (three launches, CUDA events) and the fastest kept
+ * for the process. chosen (host, 5 ints, may be NULL) receives the choices in
+ * that order. Allocates and frees three work vectors; synchronises. No-op in 2D. */
+enp_status enp_autotune(enp_handle h, int* chosen);
 
 /* Number of parameters theta of enp_param_jacobian / enp_param_vjp: 2m + 3,
  * ordered (D_1..D_m, c_in_1..c_in_{m-1}, phi_app of electrodes 0..3). */

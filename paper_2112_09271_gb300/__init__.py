@@ -104,7 +104,7 @@ class DiscDesc(ctypes.Structure):
 
 class KrylovOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_it", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("atol", ctypes.c_double)]
+                ("atol", ctypes.c_double), ("graph", ctypes.c_int)]
 
 
 class KrylovStats(ctypes.Structure):
@@ -153,6 +153,7 @@ _PROTOS = [
     ("enp_fgmres_solve", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_fgmres_solve_f32", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_newton_solve", _I, [_V, _V, _V, _V]),
+    ("enp_autotune", _I, [_V, _V]),
     ("enp_param_count", _I, [_V, ctypes.POINTER(_I)]),
     ("enp_param_jacobian", _I, [_V, _V, _V]),
     ("enp_param_vjp", _I, [_V, _V, _V, _V]),
@@ -355,12 +356,12 @@ class Operator:
         return out
 
     def fgmres_solve(self, u_lin, b, x, restart=30, max_it=300, rtol=1e-8, atol=0.0,
-                     raise_on_fail=True):
+                     raise_on_fail=True, graph=False):
         """Solve J(u_lin) x = b in place on x; returns the stats as a dict."""
         import torch
         f32 = u_lin.dtype == torch.float32
         dt = torch.float32 if f32 else torch.float64
-        o = KrylovOpts(restart, max_it, rtol, atol)
+        o = KrylovOpts(restart, max_it, rtol, atol, int(graph))
         st = KrylovStats()
         fn = self._lib.enp_fgmres_solve_f32 if f32 else self._lib.enp_fgmres_solve
         rc = fn(self.h, _dptr(u_lin, dt), _dptr(b, dt), _dptr(x, dt), ctypes.byref(o),
@@ -371,11 +372,11 @@ class Operator:
 
     def newton_solve(self, u, max_it=20, rtol=1e-10, atol=0.0, armijo_c=1e-4,
                      max_backtracks=12, bj_storage=BJ_F64, mixed=False, krylov_restart=30,
-                     krylov_max_it=500, krylov_rtol=1e-3, raise_on_fail=True):
+                     krylov_max_it=500, krylov_rtol=1e-3, raise_on_fail=True, graph=False):
         """Newton with backtracking line search in place on u; returns the stats."""
         import torch
         o = NewtonOpts(max_it, rtol, atol, armijo_c, max_backtracks, bj_storage, int(mixed),
-                       KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0))
+                       KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0, int(graph)))
         st = NewtonStats()
         rc = self._lib.enp_newton_solve(self.h, _dptr(u, torch.float64), ctypes.byref(o),
                                         ctypes.byref(st))
@@ -385,6 +386,13 @@ class Operator:
         out["history"] = list(st.history[: st.iterations + 1])
         out["status"] = rc
         return out
+
+    def autotune(self):
+        """Pick the elements per block of the hexahedral kernel for this shape;
+        returns the choices for R, J v, J^T w (FP64), J v, R (FP32)."""
+        c = (ctypes.c_int * 5)()
+        self._check(self._lib.enp_autotune(self.h, c))
+        return list(c)
 
     @property
     def n_theta(self):

@@ -501,6 +501,66 @@ enp_status enp_param_jacobian(enp_handle h, const double* u, double* dRdtheta) {
   return ENP_OK;
 }
 
+}  // extern "C"
+
+// Time every feasible elements-per-block value of the hexahedral kernel for
+// each operator mode on this handle's mesh (three launches each, CUDA events)
+// and keep the fastest. The block-column pass follows the J v choice.
+template <class R>
+static cudaError_t tune_mode(enp_handle h, int mode, R* u, R* v, R* out, int* chosen) {
+  const OpParams& P = h->prm;
+  const int mx = enp::eb3d_max<R>(P.p, P.NF, mode);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_eb = 0;
+  cudaError_t err = cudaSuccess;
+  for (int eb = 1; eb <= mx && err == cudaSuccess; ++eb) {
+    enp::eb3d_set<R>(P.p, P.NF, mode, eb);
+    err = enp::launch_op<R>(mode, P, h->d_tab, u, v, out, 1, h->stream);
+    if (err != cudaSuccess) break;
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < 3; ++r) enp::launch_op<R>(mode, P, h->d_tab, u, v, out, 1, h->stream);
+    cudaEventRecord(e1, h->stream);
+    err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && ms < best) { best = ms; best_eb = eb; }
+  }
+  enp::eb3d_set<R>(P.p, P.NF, mode, best_eb);
+  if (mode == enp::kJvp) enp::eb3d_set<R>(P.p, P.NF, enp::kBlockCol, best_eb);
+  if (chosen) *chosen = best_eb;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return err;
+}
+
+extern "C" {
+
+enp_status enp_autotune(enp_handle h, int* chosen) {
+  if (!h) return ENP_ERR_INVALID_ARG;
+  if (h->prm.dim != 3) return ENP_OK;  // the quad kernel has a fixed shape
+  const size_t n = (size_t)h->n_dof;
+  double *u = nullptr, *v = nullptr, *o = nullptr;
+  cudaError_t e = cudaMalloc(&u, 3 * n * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc autotune");
+  v = u + n;
+  o = v + n;
+  cudaMemsetAsync(u, 0, 3 * n * sizeof(double), h->stream);
+  int c[5] = {0, 0, 0, 0, 0};
+  e = tune_mode<double>(h, enp::kResidual, u, v, o, &c[0]);
+  if (e == cudaSuccess) e = tune_mode<double>(h, enp::kJvp, u, v, o, &c[1]);
+  if (e == cudaSuccess) e = tune_mode<double>(h, enp::kVjp, u, v, o, &c[2]);
+  if (e == cudaSuccess) e = tune_mode<float>(h, enp::kJvp, (float*)u, (float*)v, (float*)o, &c[3]);
+  if (e == cudaSuccess) e = tune_mode<float>(h, enp::kResidual, (float*)u, (float*)v, (float*)o, &c[4]);
+  cudaFree(u);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+  if (chosen)
+    for (int i = 0; i < 5; ++i) chosen[i] = c[i];
+  return ENP_OK;
+}
+
 const char* enp_last_error(enp_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 }  // extern "C"

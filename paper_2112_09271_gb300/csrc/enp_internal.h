@@ -15,6 +15,11 @@ cudaError_t launch_op(int mode, const OpParams& prm, const Tables* tabs, const R
 
 bool shape_supported(int dim, int p, int nf);
 
+// Elements per block of the hexahedral kernel (autotuner hooks).
+template <class R> int eb3d_max(int p, int nf, int mode);
+template <class R> void eb3d_set(int p, int nf, int mode, int eb);
+template <class R> int eb3d_get(int p, int nf, int mode);
+
 // Upload the degree-p basis tables to the constant memory the kernels of type R
 // read (current device).
 template <class R>

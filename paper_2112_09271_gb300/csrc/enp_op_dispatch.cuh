@@ -8,27 +8,49 @@
 
 namespace enp {
 
-// Hexahedra: the thread-per-pencil kernel, EB elements per block sized so that
-// a block's shared memory stays near 96 KB.
+// Elements per block of the hexahedral kernel, per (p, fields, mode) of this
+// translation unit's arithmetic type; 0 = the default (shared memory near 96 KB).
+static int g_eb3d[kMaxP + 1][4][5] = {};
+
+template <int P, int NF, int MODE, class R>
+static int default_eb() {
+  constexpr size_t per_el = (size_t)Smem3<P, NF, MODE>::total * sizeof(R);
+  constexpr int NT = (P + 2) * (P + 2);
+  int eb = (int)((96 * 1024) / per_el);
+  eb = eb < 1 ? 1 : eb;
+  while (eb > 1 && eb * NT > kMaxThreads3D) --eb;
+  return eb;
+}
+
+template <int P, int NF, int MODE, class R>
+static int max_eb() {
+  constexpr size_t per_el = (size_t)Smem3<P, NF, MODE>::total * sizeof(R);
+  constexpr int NT = (P + 2) * (P + 2);
+  int eb = kMaxThreads3D / NT;
+  while (eb > 1 && (size_t)eb * per_el > 200 * 1024) --eb;
+  return eb < 1 ? 1 : eb;
+}
+
+// Hexahedra: the thread-per-pencil kernel with EB elements per block.
 template <int P, int NF, int MODE, class R>
 static cudaError_t launch_3d(const OpParams& prm, const R* u, const R* v, R* out, int batch,
                              cudaStream_t stream) {
   using S3 = Smem3<P, NF, MODE>;
   constexpr size_t per_el = (size_t)S3::total * sizeof(R);
-  constexpr int EBr = (int)((96 * 1024) / per_el);
-  constexpr int EB = EBr < 1 ? 1 : (EBr > 8 ? 8 : EBr);
   constexpr int NT = (P + 2) * (P + 2);
-  const size_t smem = (size_t)EB * per_el;
-  auto kern = op3d_kernel<P, NF, MODE, EB, R>;
+  int eb = g_eb3d[P][NF][MODE];
+  if (eb <= 0) eb = default_eb<P, NF, MODE, R>();
+  const size_t smem = (size_t)eb * per_el;
+  auto kern = op3d_kernel<P, NF, MODE, R>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)((size_t)max_eb<P, NF, MODE, R>() * per_el));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((prm.E + EB - 1) / EB, batch);
-  kern<<<grid, EB * NT, smem, stream>>>(prm, u, v, out);
+  dim3 grid((prm.E + eb - 1) / eb, batch);
+  kern<<<grid, eb * NT, smem, stream>>>(prm, u, v, out);
   return cudaGetLastError();
 }
 
@@ -77,6 +99,30 @@ static cudaError_t launch_nf(int mode, const OpParams& prm, const Tables* t, con
   if (prm.NF == 2) return launch_mode<DIM, P, 2, R>(mode, prm, t, u, v, out, batch, s);
   if (prm.NF == 3) return launch_mode<DIM, P, 3, R>(mode, prm, t, u, v, out, batch, s);
   return cudaErrorInvalidConfiguration;
+}
+
+// Elements-per-block of the hexahedral kernel: the largest feasible value for
+// (p, fields, mode), and setting the value launches use (0 = default).
+template <class R>
+int eb3d_max(int p, int nf, int mode) {
+#define ENP_EBM(PP, NFF, MM) if (p == PP && nf == NFF && mode == MM) return max_eb<PP, NFF, MM, R>();
+#define ENP_EBM_P(PP) ENP_EBM(PP, 2, 0) ENP_EBM(PP, 2, 1) ENP_EBM(PP, 2, 2) ENP_EBM(PP, 2, 3) ENP_EBM(PP, 2, 4) \
+  ENP_EBM(PP, 3, 0) ENP_EBM(PP, 3, 1) ENP_EBM(PP, 3, 2) ENP_EBM(PP, 3, 3) ENP_EBM(PP, 3, 4)
+  ENP_EBM_P(1) ENP_EBM_P(2) ENP_EBM_P(3) ENP_EBM_P(4)
+#undef ENP_EBM_P
+#undef ENP_EBM
+  return 1;
+}
+
+template <class R>
+void eb3d_set(int p, int nf, int mode, int eb) {
+  if (p >= 1 && p <= kMaxP && nf >= 2 && nf <= 3 && mode >= 0 && mode <= 4) g_eb3d[p][nf][mode] = eb;
+}
+
+template <class R>
+int eb3d_get(int p, int nf, int mode) {
+  if (p >= 1 && p <= kMaxP && nf >= 2 && nf <= 3 && mode >= 0 && mode <= 4) return g_eb3d[p][nf][mode];
+  return 0;
 }
 
 // Upload the degree-p tables to this translation unit's constant memory on

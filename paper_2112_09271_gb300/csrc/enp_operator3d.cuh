@@ -183,8 +183,12 @@ struct Smem3 {
   static constexpr int kPrefetch = (NA * NN + Q * Q - 1) / (Q * Q);  // neighbour values per thread
 };
 
-template <int P, int NF, int MODE, int EB, class R>
-__global__ void __launch_bounds__(EB * (P + 2) * (P + 2))
+// Largest thread block of the hexahedral kernel; the elements per block (EB,
+// chosen at launch by the autotuner) satisfy EB * (P+2)^2 <= this.
+constexpr int kMaxThreads3D = 256;
+
+template <int P, int NF, int MODE, class R>
+__global__ void __launch_bounds__(kMaxThreads3D)
 op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v,
             R* __restrict__ out) {
   using S = Smem3<P, NF, MODE>;
@@ -201,6 +205,7 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   R* XA = base;                 // [NA][NNP] padded nodal arrays
   R* RO = XA + S::kX;           // [NF][NNP]
   R* WK = RO + S::kOut;
+  const int EB = blockDim.x / NT;   // elements per block, chosen at launch
   const int e = blockIdx.x * EB + es;
   const bool valid = e < prm.E;
   const int ee = valid ? e : prm.E - 1;   // invalid slots shadow a valid element, write nothing

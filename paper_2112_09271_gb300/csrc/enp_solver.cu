@@ -153,6 +153,23 @@ __global__ void scale_copy(const TX* __restrict__ x, const double* __restrict__ 
   }
 }
 
+// z[b] = x[b] + lam[b] y[b] (per operating point step lengths)
+__global__ void axpy_batched(const double* __restrict__ x, const double* __restrict__ lam,
+                             const double* __restrict__ y, double* __restrict__ z, long long n,
+                             int B) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n * B;
+       k += (long long)gridDim.x * blockDim.x)
+    z[k] = x[k] + lam[k / n] * y[k];
+}
+
+// y[b] = s[b] x[b] (per operating point scale, e.g. 0 to freeze a converged point)
+__global__ void scale_batched(const double* __restrict__ x, const double* __restrict__ sc,
+                              double* __restrict__ y, long long n, int B) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n * B;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] = sc[k / n] * x[k];
+}
+
 __global__ void axpby_kernel(double a, const double* __restrict__ x, double bcoef,
                              const double* __restrict__ y, double* __restrict__ z, long long n) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -433,6 +450,13 @@ struct SolverState {
   size_t krylov_bytes = 0;
   double* dRdtheta = nullptr;     // parameter Jacobian workspace [n_theta][batch][n]
   size_t dRdtheta_count = 0;
+  // CUDA graph of one FGMRES restart cycle, on handle-owned copies of the inputs
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  void* gbuf = nullptr;           // [3][B][n] of the Krylov type: u_lin, b, x
+  size_t gbuf_bytes = 0;
+  const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
+  int gkey_i[4] = {0, 0, 0, 0};
 };
 
 }  // namespace
@@ -492,6 +516,9 @@ void enp_solver_free(enp_handle h) {
   cudaFree(S.blocks); cudaFree(S.binv); cudaFree(S.gj_work); cudaFree(S.d_flag);
   cudaFree(S.blocks32); cudaFree(S.u32);
   cudaFree(S.part); cudaFree(S.dsmall); cudaFree(S.V); cudaFree(S.dRdtheta);
+  if (S.gexec) cudaGraphExecDestroy(S.gexec);
+  if (S.gstream) cudaStreamDestroy(S.gstream);
+  cudaFree(S.gbuf);
   delete h->solver;
   h->solver = nullptr;
 }
@@ -749,6 +776,7 @@ static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
     enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, K.inv, 0.0, V, n, n);
     int j = 0;
     bool cycle_done = false;
+    const int cycle_start = total_it;
     for (; j < m && total_it < o->max_it; ++j) {
       TV* vj = V + j * vs;
       TV* zj = Z + j * vs;
@@ -773,7 +801,14 @@ static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
         if (hflag[1]) { nonfinite = true; break; }
         cycle_done = true;
         for (int i = 0; i < B; ++i) cycle_done = cycle_done && hj[i] != -1;
-        if (cycle_done) { ++j; break; }
+        if (cycle_done) {
+          // count iterations up to each point's convergence, not up to this check
+          int used = 0;
+          for (int i = 0; i < B; ++i) if (hj[i] >= 0) used = std::max(used, hj[i] + 1);
+          total_it = cycle_start + used;
+          ++j;
+          break;
+        }
       }
     }
     if (nonfinite) break;
@@ -812,48 +847,240 @@ static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
   return ENP_OK;
 }
 
+// FGMRES with each restart cycle (r0, m Arnoldi iterations, update) captured
+// once in a CUDA graph and replayed: one launch and one host read per cycle.
+// The inputs are copied into handle-owned buffers so that the graph's pointers
+// stay fixed across calls. Iterations are counted up to each point's
+// convergence; the graph itself always runs whole cycles (a converged point is
+// frozen, so the extra iterations do not change x).
+template <class TV>
+static enp_status fgmres_graph(enp_handle h, const TV* ulin, const TV* b, TV* x,
+                               const enp_krylov_opts* o, enp_krylov_stats* st) {
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  const long long n = h->n_dof;
+  const int B = h->batch;
+  const int m = std::max(1, std::min(o->restart, 200));
+  const long long ntot = n * B;
+  const bool precond = S.storage >= 0;
+  cudaError_t e;
+  const size_t vbytes = sizeof(TV) * ntot;
+  const size_t need = vbytes * (size_t)(m + 1) + vbytes * (size_t)m;
+  cudaStream_t user = h->stream;
+  auto fail_cuda = [&](cudaError_t er, const char* what) { h->stream = user; return cuda_err(h, er, what); };
+  if (!S.gstream && (e = cudaStreamCreateWithFlags(&S.gstream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_err(h, e, "create graph stream");
+  if (S.krylov_bytes < need) {
+    if (S.gexec) { cudaGraphExecDestroy(S.gexec); S.gexec = nullptr; }
+    cudaFree(S.V); S.V = nullptr; S.krylov_bytes = 0;
+    if ((e = cudaMalloc(&S.V, need)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc Krylov basis");
+    S.krylov_bytes = need;
+  }
+  if (S.gbuf_bytes < 3 * vbytes) {
+    if (S.gexec) { cudaGraphExecDestroy(S.gexec); S.gexec = nullptr; }
+    cudaFree(S.gbuf); S.gbuf = nullptr; S.gbuf_bytes = 0;
+    if ((e = cudaMalloc(&S.gbuf, 3 * vbytes)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc graph inputs");
+    S.gbuf_bytes = 3 * vbytes;
+  }
+  TV* ug = (TV*)S.gbuf;
+  TV* bg = ug + ntot;
+  TV* xg = bg + ntot;
+  TV* V = (TV*)S.V;
+  TV* Z = (TV*)((char*)S.V + vbytes * (m + 1));
+  const long long vs = ntot;
+  const size_t nH = (size_t)B * (m + 1) * m, nG = (size_t)B * (m + 1), nM = (size_t)B * m;
+  const size_t nsmall = nH + 2 * nG + 2 * nM + nM + (size_t)B * (m + 1) + 7 * (size_t)B + 4;
+  if ((e = small(h, nsmall)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc small");
+  if ((e = ensure(&S.part, S.part_count, (size_t)B * (m + 1) * enp::kRedBlocks)) != cudaSuccess)
+    return cuda_err(h, e, "cudaMalloc partials");
+  double* q = S.dsmall;
+  enp::KrylovDev K;
+  K.H = q; q += nH;
+  K.g = q; q += nG;
+  K.hcol = q; q += nG;
+  K.cs = q; q += nM;
+  K.sn = q; q += nM;
+  K.coef = q; q += nM;
+  K.dh = q; q += (size_t)B * (m + 1);
+  K.hn2 = q; q += B;
+  K.inv = q; q += B;
+  K.beta = q; q += B;
+  K.bn2 = q; q += B;
+  K.tol = q; q += B;
+  K.resn = q; q += B;
+  int* flags = reinterpret_cast<int*>(q); q += B;
+  int* dflag = reinterpret_cast<int*>(q);
+  K.jconv = flags;
+  const int gx = grid_for(n);
+  dim3 gv(gx, B);
+  const int tb = std::min(B, 256), gbk = (B + tb - 1) / tb;
+  // inputs into the graph's buffers, ordered after the caller's stream
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, user);
+  cudaStreamWaitEvent(S.gstream, ev, 0);
+  h->stream = S.gstream;
+  cudaMemcpyAsync(ug, ulin, vbytes, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(bg, b, vbytes, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(xg, x, vbytes, cudaMemcpyDeviceToDevice, h->stream);
+  if ((e = multidot<TV>(h, bg, 0, 1, bg, K.bn2)) != cudaSuccess) { cudaEventDestroy(ev); return fail_cuda(e, "fgmres norm"); }
+  enp::krylov_tolerance<<<gbk, tb, 0, h->stream>>>(K, B, o->rtol, o->atol);
+  auto apply_A = [&](const TV* in, TV* outv) -> cudaError_t {
+    return enp::launch_op<TV>(enp::kJvp, P, h->d_tab, ug, in, outv, B, h->stream);
+  };
+  const bool same = S.gexec && S.gkey[0] == (const void*)S.V && S.gkey[1] == S.binv &&
+                    S.gkey[2] == (const void*)S.gbuf && S.gkey[3] == (const void*)S.dsmall &&
+                    S.gkey_i[0] == m && S.gkey_i[1] == S.storage && S.gkey_i[2] == (int)sizeof(TV) &&
+                    S.gkey_i[3] == B;
+  if (!same) {
+    if (S.gexec) { cudaGraphExecDestroy(S.gexec); S.gexec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+      cudaEventDestroy(ev); return fail_cuda(e, "begin capture");
+    }
+    apply_A(xg, V);
+    enp::b_minus<TV><<<grid_for(ntot), 256, 0, h->stream>>>(bg, V, ntot);
+    multidot<TV>(h, V, 0, 1, V, K.dh);
+    cudaMemsetAsync(dflag, 0, 2 * sizeof(int), h->stream);
+    enp::krylov_cycle_init<<<gbk, tb, 0, h->stream>>>(K, B, m, dflag, dflag + 1);
+    enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(V, K.inv, 0.0, V, n, n);
+    for (int j = 0; j < m; ++j) {
+      TV* vj = V + j * vs;
+      TV* zj = Z + j * vs;
+      TV* w = V + (j + 1) * vs;
+      if (precond) bj_apply_any<TV>(h, vj, zj);
+      else cudaMemcpyAsync(zj, vj, vbytes, cudaMemcpyDeviceToDevice, h->stream);
+      apply_A(zj, w);
+      for (int pass = 0; pass < 2; ++pass) {
+        multidot<TV>(h, V, vs, j + 1, w, K.dh);
+        enp::krylov_hcol_add<<<(B * (j + 1) + 127) / 128, 128, 0, h->stream>>>(K, B, m, j + 1, pass == 0);
+        enp::multi_axpy<TV><<<gv, 256, 0, h->stream>>>(V, vs, j + 1, K.dh, w, n, n);
+      }
+      multidot<TV>(h, w, 0, 1, w, K.hn2);
+      enp::krylov_givens<<<gbk, tb, 0, h->stream>>>(K, B, m, j, dflag + 1);
+      enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(w, K.inv, 0.0, w, n, n);
+    }
+    enp::krylov_solve_upper<<<gbk, tb, 0, h->stream>>>(K, B, m, m);
+    enp::combine<TV, TV><<<gv, 256, 0, h->stream>>>(Z, vs, m, K.coef, m, xg, n, n, 1);
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&S.gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { S.gexec = nullptr; cudaEventDestroy(ev); return fail_cuda(e, "capture FGMRES cycle"); }
+    S.gkey[0] = S.V; S.gkey[1] = S.binv; S.gkey[2] = S.gbuf; S.gkey[3] = S.dsmall;
+    S.gkey_i[0] = m; S.gkey_i[1] = S.storage; S.gkey_i[2] = (int)sizeof(TV); S.gkey_i[3] = B;
+  }
+  std::vector<int> hj(B);
+  int hflag[2] = {0, 0};
+  std::vector<double> hres(B);
+  int total_it = 0;
+  double first_norm = -1.0;
+  bool all_done = false, nonfinite = false;
+  for (int cycle = 0; !all_done && total_it < o->max_it; ++cycle) {
+    if ((e = cudaGraphLaunch(S.gexec, h->stream)) != cudaSuccess) { cudaEventDestroy(ev); return fail_cuda(e, "graph launch"); }
+    cudaMemcpyAsync(hj.data(), K.jconv, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(hflag, dflag, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(hres.data(), K.beta, B * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { cudaEventDestroy(ev); return fail_cuda(e, "graph sync"); }
+    if (first_norm < 0) {
+      first_norm = 0;
+      for (int i = 0; i < B; ++i) first_norm = std::max(first_norm, hres[i]);
+    }
+    if (hflag[1]) { nonfinite = true; break; }
+    all_done = true;
+    int used = 0;
+    for (int i = 0; i < B; ++i) {
+      if (hj[i] == -1) all_done = false;
+      if (hj[i] >= 0) used = std::max(used, hj[i] + 1);
+    }
+    total_it += all_done ? used : m;
+  }
+  enp_status ret = ENP_OK;
+  if (nonfinite) { h->err = "non-finite value in FGMRES"; ret = ENP_ERR_NONFINITE; }
+  // true residual of the final iterate
+  std::vector<double> hr2(B), htol(B), hbn(B);
+  if (ret == ENP_OK) {
+    apply_A(xg, V);
+    enp::b_minus<TV><<<grid_for(ntot), 256, 0, h->stream>>>(bg, V, ntot);
+    multidot<TV>(h, V, 0, 1, V, K.dh);
+    cudaMemcpyAsync(hr2.data(), K.dh, B * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(htol.data(), K.tol, B * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(hbn.data(), K.bn2, B * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  }
+  cudaMemcpyAsync(x, xg, vbytes, cudaMemcpyDeviceToDevice, h->stream);
+  cudaEventRecord(ev, h->stream);
+  cudaStreamWaitEvent(user, ev, 0);
+  e = cudaStreamSynchronize(h->stream);
+  cudaEventDestroy(ev);
+  h->stream = user;
+  if (e != cudaSuccess) return cuda_err(h, e, "graph final sync");
+  if (ret != ENP_OK) return ret;
+  double worst_rel = 0.0, worst = 0.0;
+  bool conv = all_done;
+  for (int i = 0; i < B; ++i) {
+    const double r = std::sqrt(hr2[i]), bn = std::sqrt(hbn[i]);
+    if (!(r <= htol[i] * 1.0001)) conv = false;
+    worst = std::max(worst, r);
+    worst_rel = std::max(worst_rel, bn > 0 ? r / bn : r);
+  }
+  if (st) {
+    st->iterations = total_it;
+    st->residual_norm = worst;
+    st->relative_residual = worst_rel;
+    st->initial_norm = first_norm < 0 ? 0.0 : first_norm;
+    st->converged = conv ? 1 : 0;
+  }
+  if (!conv) { h->err = "FGMRES reached max_it"; return ENP_ERR_NOT_CONVERGED; }
+  return ENP_OK;
+}
+
 extern "C" enp_status enp_fgmres_solve(enp_handle h, const double* u_lin, const double* b, double* x,
                                        const enp_krylov_opts* o, enp_krylov_stats* st) {
   if (!h || !u_lin || !b || !x || !o || o->restart < 1 || o->max_it < 1) return ENP_ERR_INVALID_ARG;
+  if (o->graph) return fgmres_graph<double>(h, u_lin, b, x, o, st);
   return fgmres_any<double>(h, u_lin, b, x, o, st);
 }
 
 extern "C" enp_status enp_fgmres_solve_f32(enp_handle h, const float* u_lin, const float* b, float* x,
                                            const enp_krylov_opts* o, enp_krylov_stats* st) {
   if (!h || !u_lin || !b || !x || !o || o->restart < 1 || o->max_it < 1) return ENP_ERR_INVALID_ARG;
+  if (o->graph) return fgmres_graph<float>(h, u_lin, b, x, o, st);
   return fgmres_any<float>(h, u_lin, b, x, o, st);
 }
 
 // ---------------------------------------------------------------- Newton
-// Newton's method with backtracking line search (Sec. 4): solve J du = -R with
-// FGMRES (FP64, or with the FP32 operator when opts->mixed), then halve the step
-// until ||R(u + lam du)|| <= (1 - c lam) ||R(u)||. The block-Jacobi
-// preconditioner is rebuilt at every Newton iterate. The norm tested is the
-// largest over the operating points.
+// Newton's method with backtracking line search (Sec. 4), independently for
+// every operating point of the batch: solve J du = -R with FGMRES (FP64, or
+// with the FP32 operator when opts->mixed), then halve each point's step until
+// ||R_b(u_b + lam_b du_b)|| <= (1 - c lam_b) ||R_b(u_b)||. A point that has met
+// its tolerance gets a zero right-hand side (FGMRES leaves it at du = 0). The
+// block-Jacobi preconditioner is rebuilt at every Newton iterate. Norms in the
+// statistics are the largest over the operating points.
 extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* o,
                                        enp_newton_stats* st) {
   if (!h || !u || !o || o->max_it < 0) return ENP_ERR_INVALID_ARG;
   SolverState& S = state_of(h);
-  const long long ntot = h->n_dof * h->batch;
+  const long long n = h->n_dof;
+  const long long ntot = n * h->batch;
   const int B = h->batch;
   cudaError_t e;
-  (void)S;
-  double *r = nullptr, *du = nullptr, *ut = nullptr, *rt = nullptr;
+  double *r = nullptr, *du = nullptr, *ut = nullptr, *rt = nullptr, *dvec = nullptr;
   float *u32 = nullptr, *b32 = nullptr, *x32 = nullptr;
   auto cleanup = [&]() {
-    cudaFree(r); cudaFree(du); cudaFree(ut); cudaFree(rt);
+    cudaFree(r); cudaFree(du); cudaFree(ut); cudaFree(rt); cudaFree(dvec);
     cudaFree(u32); cudaFree(b32); cudaFree(x32);
   };
   e = cudaMalloc(&r, sizeof(double) * ntot);
   if (e == cudaSuccess) e = cudaMalloc(&du, sizeof(double) * ntot);
   if (e == cudaSuccess) e = cudaMalloc(&ut, sizeof(double) * ntot);
   if (e == cudaSuccess) e = cudaMalloc(&rt, sizeof(double) * ntot);
+  if (e == cudaSuccess) e = cudaMalloc(&dvec, sizeof(double) * 2 * B);
   if (e == cudaSuccess && o->mixed) {
     e = cudaMalloc(&u32, sizeof(float) * ntot);
     if (e == cudaSuccess) e = cudaMalloc(&b32, sizeof(float) * ntot);
     if (e == cudaSuccess) e = cudaMalloc(&x32, sizeof(float) * ntot);
   }
   if (e != cudaSuccess) { cleanup(); return cuda_err(h, e, "cudaMalloc newton work"); }
+  double* dlam = dvec;       // [B] step lengths
   auto norms = [&](const double* v, std::vector<double>& out) -> cudaError_t {
     cudaError_t er = small(h, (size_t)B * 4);
     if (er != cudaSuccess) return er;
@@ -866,60 +1093,82 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
     for (auto& x : out) x = std::sqrt(x);
     return er;
   };
-  auto maxof = [](const std::vector<double>& v) { double m = 0; for (double x : v) m = std::max(m, std::isnan(x) ? INFINITY : x); return m; };
+  auto maxof = [](const std::vector<double>& v) {
+    double m = 0;
+    for (double x : v) m = std::max(m, std::isnan(x) ? INFINITY : x);
+    return m;
+  };
+  const int gx = grid_for(ntot);
   enp_status status = ENP_OK;
-  std::vector<double> rn;
+  std::vector<double> rn, r0, tol(B), lam(B), mask(B), rnew;
   if ((e = enp::launch_op<double>(enp::kResidual, h->prm, h->d_tab, u, nullptr, r, B, h->stream)) != cudaSuccess ||
       (e = norms(r, rn)) != cudaSuccess) { cleanup(); return cuda_err(h, e, "newton residual"); }
-  double r0 = maxof(rn), rcur = r0;
-  if (!std::isfinite(r0)) { cleanup(); h->err = "non-finite initial residual"; return ENP_ERR_NONFINITE; }
+  r0 = rn;
+  for (int b = 0; b < B; ++b) {
+    if (!std::isfinite(rn[b])) { cleanup(); h->err = "non-finite initial residual"; return ENP_ERR_NONFINITE; }
+    tol[b] = std::max(o->rtol * r0[b], o->atol);
+  }
   int it = 0, kry_total = 0;
-  if (st) { std::memset(st, 0, sizeof(*st)); st->initial_norm = r0; st->history[0] = r0; }
-  const int gx = grid_for(ntot);
+  if (st) { std::memset(st, 0, sizeof(*st)); st->initial_norm = maxof(r0); st->history[0] = maxof(rn); }
   while (true) {
-    if (rcur <= std::max(o->rtol * r0, o->atol)) break;
+    bool all_conv = true;
+    for (int b = 0; b < B; ++b) {
+      mask[b] = rn[b] <= tol[b] ? 0.0 : 1.0;
+      all_conv = all_conv && mask[b] == 0.0;
+    }
+    if (all_conv) break;
     if (it >= o->max_it) { status = ENP_ERR_NOT_CONVERGED; h->err = "Newton reached max_it"; break; }
     enp_status s2 = enp_block_jacobi_setup(h, u, o->bj_storage);
     if (s2 != ENP_OK) { status = s2; break; }
     enp_krylov_stats ks{};
     enp_krylov_opts ko = o->krylov;
-    // b = -r, x = 0
-    enp::axpby_kernel<<<gx, 256, 0, h->stream>>>(-1.0, r, 0.0, r, rt, ntot);
+    // right-hand side -R on the running points, 0 on the converged ones
+    for (int b = 0; b < B; ++b) lam[b] = -mask[b];
+    cudaMemcpyAsync(dlam, lam.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
+    enp::scale_batched<<<gx, 256, 0, h->stream>>>(r, dlam, rt, n, B);
     cudaMemsetAsync(du, 0, sizeof(double) * ntot, h->stream);
     if (o->mixed) {
       enp::convert_kernel<double, float><<<gx, 256, 0, h->stream>>>(u, u32, ntot);
       enp::convert_kernel<double, float><<<gx, 256, 0, h->stream>>>(rt, b32, ntot);
       cudaMemsetAsync(x32, 0, sizeof(float) * ntot, h->stream);
-      s2 = fgmres_any<float>(h, u32, b32, x32, &ko, &ks);
+      s2 = ko.graph ? fgmres_graph<float>(h, u32, b32, x32, &ko, &ks)
+                    : fgmres_any<float>(h, u32, b32, x32, &ko, &ks);
       enp::convert_kernel<float, double><<<gx, 256, 0, h->stream>>>(x32, du, ntot);
     } else {
-      s2 = fgmres_any<double>(h, u, rt, du, &ko, &ks);
+      s2 = ko.graph ? fgmres_graph<double>(h, u, rt, du, &ko, &ks)
+                    : fgmres_any<double>(h, u, rt, du, &ko, &ks);
     }
     kry_total += ks.iterations;
     if (s2 != ENP_OK && s2 != ENP_ERR_NOT_CONVERGED) { status = s2; break; }
-    // backtracking line search
-    double lam = 1.0, rnew = INFINITY;
-    int bt = 0;
-    for (;; ++bt) {
-      enp::axpby_kernel<<<gx, 256, 0, h->stream>>>(1.0, u, lam, du, ut, ntot);
+    // backtracking line search, one step length per operating point
+    std::vector<int> accepted(B, 0);
+    for (int b = 0; b < B; ++b) { lam[b] = mask[b] > 0 ? 1.0 : 0.0; accepted[b] = mask[b] == 0.0; }
+    for (int bt = 0;; ++bt) {
+      cudaMemcpyAsync(dlam, lam.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
+      enp::axpy_batched<<<gx, 256, 0, h->stream>>>(u, dlam, du, ut, n, B);
       if ((e = enp::launch_op<double>(enp::kResidual, h->prm, h->d_tab, ut, nullptr, rt, B, h->stream)) != cudaSuccess ||
-          (e = norms(rt, rn)) != cudaSuccess) { cleanup(); return cuda_err(h, e, "newton line search"); }
-      rnew = maxof(rn);
-      if (rnew <= (1.0 - o->armijo_c * lam) * rcur || bt >= o->max_backtracks) break;
-      lam *= 0.5;
+          (e = norms(rt, rnew)) != cudaSuccess) { cleanup(); return cuda_err(h, e, "newton line search"); }
+      bool all_acc = true;
+      for (int b = 0; b < B; ++b) {
+        if (accepted[b]) continue;
+        if (rnew[b] <= (1.0 - o->armijo_c * lam[b]) * rn[b] || bt >= o->max_backtracks) accepted[b] = 1;
+        else lam[b] *= 0.5;
+        all_acc = all_acc && accepted[b];
+      }
+      if (all_acc) break;
     }
     cudaMemcpyAsync(u, ut, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, h->stream);
     cudaMemcpyAsync(r, rt, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, h->stream);
+    rn = rnew;
     ++it;
-    rcur = rnew;
-    if (st && it < 64) st->history[it] = rcur;
-    if (!std::isfinite(rcur)) { status = ENP_ERR_NONFINITE; h->err = "non-finite residual"; break; }
+    if (st && it < 64) st->history[it] = maxof(rn);
+    if (!std::isfinite(maxof(rn))) { status = ENP_ERR_NONFINITE; h->err = "non-finite residual"; break; }
   }
   cudaStreamSynchronize(h->stream);
   if (st) {
     st->iterations = it;
     st->krylov_iterations = kry_total;
-    st->residual_norm = rcur;
+    st->residual_norm = maxof(rn);
     st->converged = (status == ENP_OK) ? 1 : 0;
   }
   cleanup();

@@ -4,3 +4,6 @@
 template cudaError_t enp::launch_op<float>(int, const OpParams&, const Tables*, const float*,
                                            const float*, float*, int, cudaStream_t);
 template cudaError_t enp::prepare_tables<float>(int, const Tables&);
+template int enp::eb3d_max<float>(int, int, int);
+template void enp::eb3d_set<float>(int, int, int, int);
+template int enp::eb3d_get<float>(int, int, int);

@@ -3,3 +3,6 @@
 template cudaError_t enp::launch_op<double>(int, const OpParams&, const Tables*, const double*,
                                             const double*, double*, int, cudaStream_t);
 template cudaError_t enp::prepare_tables<double>(int, const Tables&);
+template int enp::eb3d_max<double>(int, int, int);
+template void enp::eb3d_set<double>(int, int, int, int);
+template int enp::eb3d_get<double>(int, int, int);

@@ -156,8 +156,10 @@ def config(name: str, p: Optional[int] = None) -> Problem:
                       z=(+1,-1,+2), D=(5e-4,1e-3,2e-3), plate flow u_avg=5.
     cube24_p2         3D unit cube, 24^3 hex, p=2, as cube16.
     reactor192_p{2,4} (0,12)x(0,3)x(0,1), 192x48x16 hex, CuSO4-like binary
-                      z=(+2,-2), D=(1e-4,1.48e-4), one Butler-Volmer cathode on y=0
-                      for x in [5,7] with a J_0 profile across z.
+                      z=(+2,-2), D=(1e-4,1.48e-4), Butler-Volmer cathode on y=0 and
+                      anode (phi_app = 0) on y=3 for x in [5,7] (electrode length
+                      between inlet and outlet regions 5:2:5 as in Sec. 5.2), with
+                      a J_0 profile across z.
     Small variants for tests take a suffix, e.g. 'cube_n4_p3' (n^3 elements).
     """
     if name == "mms2d_8x8_p2" or name.startswith("mms2d_n"):
@@ -211,7 +213,7 @@ def config(name: str, p: Optional[int] = None) -> Problem:
         if p is not None:
             pp = p
         coords = _linspace_coords(n_el, [12.0, 3.0, 1.0])
-        tags = _reactor_tags(3, n_el, coords, 5.0, 7.0, anode=False)
+        tags = _reactor_tags(3, n_el, coords, 5.0, 7.0, anode=True)
         return Problem(dim=3, n_el=n_el, coords=coords, tags=tags, m=2, z=[2.0, -2.0],
                        D=[1e-4, 1.48e-4], c_in=[1.0, 1.0], p=pp, q=pp + 2,
                        vel_kind=VEL_PLATE, vel_params=[0, 1, 0.0, 3.0, 1.0, 0, 0, 0],
@@ -219,6 +221,19 @@ def config(name: str, p: Optional[int] = None) -> Problem:
                        bv_gamma=1.0, bv_c_ref=1.0, bv_phi_app=[0.1 * 38.92, 0.0, 0.0, 0.0],
                        bv_J0_axis=2, bv_J0_lo=0.0, bv_J0_hi=1.0, name=name)
     raise KeyError(name)
+
+
+def reactor_initial_state(P: Problem, phi_app) -> np.ndarray:
+    """Initial guess of the reactor solves: c = c_in and Phi = phi_app / 2 (between
+    the anode at 0 and the cathode), one block per operating point."""
+    out = []
+    for ph in np.atleast_1d(phi_app):
+        u = np.zeros((P.n_fields, P.E, P.Np))
+        u[0] = 0.5 * ph
+        for k in range(1, P.n_fields):
+            u[k] = P.c_in[k - 1]
+        out.append(u.reshape(-1))
+    return np.concatenate(out)
 
 
 def random_state(P: Problem, seed: int, c_mean: float = 1.0, c_amp: float = 0.1,
