@@ -291,71 +291,105 @@ __global__ void b_minus(const T* __restrict__ b, T* __restrict__ r, long long n)
 // ------------------------------------------------------------------ block inverse
 // In-place Gauss-Jordan inversion with partial (row) pivoting of one n x n
 // block per thread block. The matrix lives in shared memory when it fits
-// (SMEM = true) else in global memory. Row swaps are undone at the end as
-// column swaps in reverse order. A zero or non-finite pivot sets *singular.
-// The inverse is written transposed (out[e][c][r] = inv[r][c]) in type TS.
+// (SMEM = true), else in global memory, with the odd leading dimension n + 1
+// (no shared-memory bank conflicts down a column). Lane l of every warp owns
+// the rows i = l (mod 32), warp w the columns j = w (mod nwarps). Step k:
+//   (1) stage the pivot row (old row p) and the pivot column (rows k and p
+//       exchanged), and move row k to row p;
+//   (2) rank-1 update of every entry, A_ij -= A_ik A_kj / A_kk, the column
+//       entries of the thread's rows held in registers;
+//   (3) overwrite row k (scaled pivot row) and column k (-A_ik / A_kk), while
+//       warp 0 finds the next pivot in column k+1 (in the matrix's type).
+// A zero or non-finite pivot sets *singular. Row swaps are undone at the end
+// as column swaps in reverse order. The inverse is written transposed
+// (out[e][c][r] = inv[r][c]) in type TS.
+constexpr int kGjRows = 8;  // rows per lane held in registers: n <= 256
+
+template <class T>
+__device__ __forceinline__ void gj_pivot(const T* A, int ld, int n, int col, int lane, int* s_p,
+                                         int* s_bad) {
+  T best = T(-1);
+  int bi = col;
+  for (int i = col + lane; i < n; i += 32) {
+    const T a = fabs(A[(long long)i * ld + col]);
+    if (a > best) { best = a; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ob = __shfl_down_sync(0xffffffffu, best, o);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) { *s_p = bi; *s_bad = (!(best > T(0)) || !isfinite(best)) ? 1 : 0; }
+}
+
 template <class T, class TS, bool SMEM, class TB>
 __global__ void gj_invert(const TB* __restrict__ blocks, T* __restrict__ work, TS* __restrict__ out,
                           int n, int* __restrict__ singular) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const long long e = blockIdx.x;
-  const long long nn = (long long)n * n;
-  T* A = SMEM ? reinterpret_cast<T*>(gsm) : work + e * nn;
-  T* colk = SMEM ? A + nn : reinterpret_cast<T*>(gsm);
-  int* piv = reinterpret_cast<int*>(colk + n);
-  __shared__ double rv[32];
-  __shared__ int ri[32];
+  const int ld = n + 1;
+  const long long na = (long long)n * ld;
+  T* A = SMEM ? reinterpret_cast<T*>(gsm) : work + e * na;
+  T* prow = SMEM ? A + na : reinterpret_cast<T*>(gsm);   // [n] pivot row (old row p)
+  T* pcol = prow + n;                                     // [n] pivot column after the swap
+  int* piv = reinterpret_cast<int*>(pcol + n);            // [n] row chosen at each step
   __shared__ int s_p;
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const TB* src = blocks + e * nn;
-  for (long long t = tid; t < nn; t += nt) A[t] = (T)src[t];
-  if (tid == 0) s_bad = 0;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const TB* src = blocks + e * (long long)n * n;
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) A[(long long)i * ld + j] = (T)src[(long long)i * n + j];
   __syncthreads();
+  if (warp == 0) gj_pivot<T>(A, ld, n, 0, lane, &s_p, &s_bad);
+  __syncthreads();
+  const bool regs = n <= 32 * kGjRows;
   for (int k = 0; k < n; ++k) {
-    // pivot: argmax_{i >= k} |A[i][k]| (lowest index on ties)
-    double best = -1.0; int bi = k;
-    for (int i = k + tid; i < n; i += nt) {
-      double a = fabs((double)A[(long long)i * n + k]);
-      if (a > best) { best = a; bi = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_down_sync(0xffffffffu, best, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double b = rv[0]; int i0 = ri[0];
-      for (int wv = 1; wv < (nt + 31) / 32; ++wv)
-        if (rv[wv] > b || (rv[wv] == b && ri[wv] < i0)) { b = rv[wv]; i0 = ri[wv]; }
-      s_p = i0;
-      piv[k] = i0;
-      if (!(b > 0.0) || !isfinite(b)) s_bad = 1;
-    }
-    __syncthreads();
     if (s_bad) break;
     const int p = s_p;
-    if (p != k)
-      for (int j = tid; j < n; j += nt) {
-        T tmp = A[(long long)k * n + j];
-        A[(long long)k * n + j] = A[(long long)p * n + j];
-        A[(long long)p * n + j] = tmp;
-      }
-    __syncthreads();
-    const T pinv = T(1) / A[(long long)k * n + k];
-    for (int i = tid; i < n; i += nt) colk[i] = A[(long long)i * n + k];
-    __syncthreads();
-    for (int j = tid; j < n; j += nt) A[(long long)k * n + j] = (j == k) ? pinv : A[(long long)k * n + j] * pinv;
-    __syncthreads();
-    for (long long t = tid; t < nn; t += nt) {
-      const int i = (int)(t / n), j = (int)(t % n);
-      if (i == k) continue;
-      if (j == k) A[t] = -colk[i] * pinv;
-      else A[t] -= colk[i] * A[(long long)k * n + j];
+    // (1)
+    for (int j = tid; j < n; j += nt) {
+      const T vp = A[(long long)p * ld + j], vk = A[(long long)k * ld + j];
+      prow[j] = vp;
+      if (p != k) A[(long long)p * ld + j] = vk;
     }
+    for (int i = tid; i < n; i += nt) {
+      const int si = (i == k) ? p : ((i == p) ? k : i);
+      pcol[i] = A[(long long)si * ld + k];
+    }
+    if (tid == 0) piv[k] = p;
+    __syncthreads();
+    // (2)
+    const T pinv = T(1) / prow[k];
+    if (regs) {
+      T pc[kGjRows];
+#pragma unroll
+      for (int r = 0; r < kGjRows; ++r) {
+        const int i = lane + 32 * r;
+        pc[r] = i < n ? pcol[i] : T(0);
+      }
+      for (int j = warp; j < n; j += nw) {
+        const T rj = prow[j] * pinv;
+        T* colj = A + j;
+#pragma unroll
+        for (int r = 0; r < kGjRows; ++r) {
+          const int i = lane + 32 * r;
+          if (i < n) colj[(long long)i * ld] -= pc[r] * rj;
+        }
+      }
+    } else {
+      for (int j = warp; j < n; j += nw) {
+        const T rj = prow[j] * pinv;
+        for (int i = lane; i < n; i += 32) A[(long long)i * ld + j] -= pcol[i] * rj;
+      }
+    }
+    __syncthreads();
+    // (3)
+    for (int j = tid; j < n; j += nt) A[(long long)k * ld + j] = (j == k) ? pinv : prow[j] * pinv;
+    for (int i = tid; i < n; i += nt)
+      if (i != k) A[(long long)i * ld + k] = -pcol[i] * pinv;
+    if (warp == 0 && k + 1 < n) gj_pivot<T>(A, ld, n, k + 1, lane, &s_p, &s_bad);
     __syncthreads();
   }
   if (s_bad) {
@@ -367,17 +401,15 @@ __global__ void gj_invert(const TB* __restrict__ blocks, T* __restrict__ work, T
     const int p = piv[k];
     if (p != k)
       for (int i = tid; i < n; i += nt) {
-        T tmp = A[(long long)i * n + k];
-        A[(long long)i * n + k] = A[(long long)i * n + p];
-        A[(long long)i * n + p] = tmp;
+        T tmp = A[(long long)i * ld + k];
+        A[(long long)i * ld + k] = A[(long long)i * ld + p];
+        A[(long long)i * ld + p] = tmp;
       }
     __syncthreads();
   }
-  TS* o = out + e * nn;
-  for (long long t = tid; t < nn; t += nt) {
-    const int r = (int)(t / n), c = (int)(t % n);
-    o[(long long)c * n + r] = (TS)A[t];
-  }
+  TS* o = out + e * (long long)n * n;
+  for (int c = warp; c < n; c += nw)
+    for (int r = lane; r < n; r += 32) o[(long long)c * n + r] = (TS)A[(long long)r * ld + c];
 }
 
 // y_e = Binv_e x_e with the inverse stored transposed (BT[c][r]); accumulation in TA.
@@ -612,14 +644,14 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
   S.storage = storage;
   cudaMemsetAsync(S.d_flag, 0, sizeof(int), h->stream);
   const size_t telt = f64 ? 8 : 4;
-  const size_t smem_full = telt * (nn + nb) + sizeof(int) * nb;
+  const size_t smem_full = telt * ((size_t)nb * (nb + 1) + 2 * nb) + sizeof(int) * nb;
   const bool in_smem = smem_full <= 200 * 1024;
   const int threads = 512;
   if (!in_smem) {
-    e = ensure((char**)&S.gj_work, S.gj_work_bytes, telt * nn * nblk);
+    e = ensure((char**)&S.gj_work, S.gj_work_bytes, telt * (size_t)nb * (nb + 1) * nblk);
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc inversion work");
   }
-  const size_t smem = in_smem ? smem_full : telt * nb + sizeof(int) * nb;
+  const size_t smem = in_smem ? smem_full : telt * 2 * nb + sizeof(int) * nb;
 #define ENP_GJ(T, TS, SM, TB, SRC)                                                              \
   {                                                                                             \
     auto k = enp::gj_invert<T, TS, SM, TB>;                                                     \
