@@ -295,6 +295,7 @@ def main():
 
     import torch
     import paper_2112_09271_gb300 as enp
+    from paper_2112_09271_gb300 import dist as pdist
     import workloads as W
 
     torch.cuda.set_device(local)
@@ -369,9 +370,8 @@ def main():
     if dist:
         dist.barrier()
     import tempfile
-    cdir = os.path.join(ROOT, "gpurun_out")
-    sampler = ClockSampler(local, os.path.join(cdir if os.path.isdir(cdir) else tempfile.gettempdir(),
-                                               f"clocks_rank{rank}.csv"))
+    cdir = os.environ.get("ENP_CLOCKS_DIR", tempfile.gettempdir())
+    sampler = ClockSampler(local, os.path.join(cdir, f"clocks_rank{rank}.csv"))
     sampler.start()
     time.sleep(0.3)
     total_ms = 0.0
@@ -387,11 +387,7 @@ def main():
             t_ops[nm] += ev[nm][0].elapsed_time(ev[nm][1])
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms_step = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = pdist.max_over_ranks(total_ms / args.steps, device="cuda")
     units = n * len(applications)
     value = world * units / (ms_step * 1e-3) / 1e9
 
@@ -468,11 +464,7 @@ def main():
         e2e_step()
     s1.record(stream)
     s1.synchronize()
-    e2e_ms = s0.elapsed_time(s1) / e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = pdist.max_over_ranks(s0.elapsed_time(s1) / e_steps, device="cuda")
     e2e = {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
            "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 4 * n * 8 + n * 4,
            "ms_per_step": e2e_ms}
