@@ -179,11 +179,34 @@ enp_status enp_block_diagonal(enp_handle h, const double* u, double* blocks);
  * Errors: NONFINITE if a block is singular or not finite. */
 enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage);
 
-/* y = P^{-1} x with P the block diagonal of the last setup. x, y: [batch][m][E][Np]. */
+/* y = M^{-1} x with M the preconditioner of the last setup: the inverse block
+ * diagonal, plus the coarse correction when the two-level preconditioner is on.
+ * x, y: [batch][m][E][Np]. */
 enp_status enp_block_jacobi_apply(enp_handle h, const double* x, double* y);
 
+/* Choose the preconditioner that the next enp_block_jacobi_setup builds (and
+ * that FGMRES and Newton then use). two_level = 0: block-Jacobi alone (the
+ * element-wise Jacobi of Sec. 4.2, the default). two_level = 1 (hexahedral
+ * meshes): block-Jacobi plus an additive coarse correction on the element-mean
+ * potential, P V(P^T r), with P the constant on the potential nodes of each
+ * element; A0 = P^T J_PhiPhi(u) P, a 7-point stencil on the element grid, is
+ * assembled exactly from 7 coloured J v products at setup, and V is one
+ * multigrid V-cycle on it (2 x 2 x 2 Galerkin aggregation, red-black
+ * Gauss-Seidel, 2 + 2 sweeps per level, 100 sweeps on the coarsest grid of at
+ * most 512 cells). The Schur-complement-like stiffness of the potential
+ * equation (Sec. 3.3) is what block-Jacobi alone cannot reduce.
+ * Takes effect at the next setup. Errors: INVALID_ARG (two_level not 0 or 1),
+ * UNSUPPORTED (two_level = 1 on a 2D mesh). */
+enp_status enp_set_preconditioner(enp_handle h, int two_level);
+
+/* a0: device [batch][E][7] = the level-0 coarse operator of the last setup,
+ * entries (self, -x, +x, -y, +y, -z, +z) of each element's row of
+ * P^T J_PhiPhi P (zero where the neighbour does not exist).
+ * Errors: INVALID_ARG if the two-level preconditioner has not been set up. */
+enp_status enp_coarse_operator(enp_handle h, double* a0);
+
 typedef struct {
-  int restart;   /* Krylov vectors per cycle (FGMRES(restart)) */
+  int restart;   /* Krylov vectors per cycle (FGMRES(restart)), at most 255 */
   int max_it;    /* total iterations */
   double rtol;   /* stop when ||b - A x|| <= max(rtol ||b||, atol) */
   double atol;

@@ -150,6 +150,8 @@ _PROTOS = [
     ("enp_block_diagonal", _I, [_V, _V, _V]),
     ("enp_block_jacobi_setup", _I, [_V, _V, _I]),
     ("enp_block_jacobi_apply", _I, [_V, _V, _V]),
+    ("enp_set_preconditioner", _I, [_V, _I]),
+    ("enp_coarse_operator", _I, [_V, _V]),
     ("enp_fgmres_solve", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_fgmres_solve_f32", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_newton_solve", _I, [_V, _V, _V, _V]),
@@ -353,6 +355,18 @@ class Operator:
         out = self._new(torch.float64) if out is None else out
         self._check(self._lib.enp_block_jacobi_apply(self.h, _dptr(x, torch.float64),
                                                      _dptr(out, torch.float64)))
+        return out
+
+    def set_preconditioner(self, two_level):
+        """0: block-Jacobi; 1: block-Jacobi plus the coarse potential correction
+        (takes effect at the next block_jacobi_setup)."""
+        self._check(self._lib.enp_set_preconditioner(self.h, int(two_level)))
+
+    def coarse_operator(self):
+        """The level-0 coarse operator [batch][E][7] of the last two-level setup."""
+        import torch
+        out = torch.empty(self.batch * self.prob.E * 7, dtype=torch.float64, device="cuda")
+        self._check(self._lib.enp_coarse_operator(self.h, _dptr(out, torch.float64)))
         return out
 
     def fgmres_solve(self, u_lin, b, x, restart=30, max_it=300, rtol=1e-8, atol=0.0,

@@ -288,6 +288,220 @@ __global__ void b_minus(const T* __restrict__ b, T* __restrict__ r, long long n)
     r[k] = b[k] - r[k];
 }
 
+// ------------------------------------------------------------------ two-level
+// Coarse space: one potential value per element (the element mean mode,
+// P = constant on the element's Phi nodes). A0 = P^T J_PhiPhi P is a 7-point
+// stencil on the element grid, stored [batch][cell][7] with entries
+// (self, -x, +x, -y, +y, -z, +z). Coarser levels aggregate 2 x 2 x 2 cells
+// (Galerkin: the stencil stays 7-point), smoothed by red-black Gauss-Seidel.
+
+// Element colour (ix + 2 iy + 3 iz) mod 7: the seven cells of a 7-point
+// stencil have offsets 0, +-1, +-2, +-3 (mod 7), all distinct, so every cell's
+// stencil holds exactly one cell of each colour and seven probes recover A0.
+__device__ __forceinline__ int cell_colour(int ix, int iy, int iz) {
+  return (ix + 2 * iy + 3 * iz) % 7;
+}
+
+// v = indicator of the Phi field on the elements of colour c (other fields 0).
+__global__ void coarse_colour_vector(double* __restrict__ v, int nx, int ny, int nz, int Np,
+                                     long long bstride, int E, int colour) {
+  const int b = blockIdx.y;
+  const long long n = (long long)E * Np;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(t / Np);
+    const int ix = e % nx, iy = (e / nx) % ny, iz = e / (nx * ny);
+    v[b * bstride + t] = (cell_colour(ix, iy, iz) == colour) ? 1.0 : 0.0;
+  }
+}
+
+// Sum of the Phi rows of element K of J v, filed under the direction of the
+// colour-c element in K's stencil (if that element exists).
+__global__ void coarse_gather(const double* __restrict__ jv, double* __restrict__ A, int nx, int ny,
+                              int nz, int Np, long long bstride, int colour) {
+  const int b = blockIdx.y;
+  const int E = nx * ny * nz;
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < E; K += gridDim.x * blockDim.x) {
+    const int ix = K % nx, iy = (K / nx) % ny, iz = K / (nx * ny);
+    // offset of the colour-c cell relative to K, as a colour difference
+    const int d = ((colour - cell_colour(ix, iy, iz)) % 7 + 7) % 7;
+    int dir = -1;
+    switch (d) {
+      case 0: dir = 0; break;
+      case 6: dir = ix > 0 ? 1 : -1; break;
+      case 1: dir = ix < nx - 1 ? 2 : -1; break;
+      case 5: dir = iy > 0 ? 3 : -1; break;
+      case 2: dir = iy < ny - 1 ? 4 : -1; break;
+      case 4: dir = iz > 0 ? 5 : -1; break;
+      case 3: dir = iz < nz - 1 ? 6 : -1; break;
+    }
+    if (dir < 0) continue;
+    const double* row = jv + b * bstride + (long long)K * Np;  // field 0 block starts at 0
+    double s = 0.0;
+    for (int i = 0; i < Np; ++i) s += row[i];
+    A[((long long)b * E + K) * 7 + dir] = s;
+  }
+}
+
+// Galerkin aggregation of a 7-point level onto 2 x 2 x 2 blocks of cells.
+__global__ void coarse_aggregate(const double* __restrict__ Af, int fx, int fy, int fz,
+                                 double* __restrict__ Ac, int cx, int cy, int cz) {
+  const int b = blockIdx.y;
+  const int Nc = cx * cy * cz, Nf = fx * fy * fz;
+  for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < Nc; C += gridDim.x * blockDim.x) {
+    const int jx = C % cx, jy = (C / cx) % cy, jz = C / (cx * cy);
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int ix = 2 * jx + dx, iy = 2 * jy + dy, iz = 2 * jz + dz;
+          if (ix >= fx || iy >= fy || iz >= fz) continue;
+          const double* a = Af + ((long long)b * Nf + ix + fx * (iy + fy * iz)) * 7;
+          acc[0] += a[0];
+          // x neighbours: inside the aggregate -> self, outside -> the coarse neighbour
+          acc[dx == 0 ? 1 : 0] += a[1];
+          acc[dx == 1 ? 2 : 0] += a[2];
+          acc[dy == 0 ? 3 : 0] += a[3];
+          acc[dy == 1 ? 4 : 0] += a[4];
+          acc[dz == 0 ? 5 : 0] += a[5];
+          acc[dz == 1 ? 6 : 0] += a[6];
+        }
+    double* o = Ac + ((long long)b * Nc + C) * 7;
+    for (int d = 0; d < 7; ++d) o[d] = acc[d];
+  }
+}
+
+__device__ __forceinline__ double stencil_off(const double* __restrict__ a, const double* __restrict__ x,
+                                              int i, int nx, int ny, int nz, int ix, int iy, int iz) {
+  double s = 0.0;
+  if (ix > 0) s += a[1] * x[i - 1];
+  if (ix < nx - 1) s += a[2] * x[i + 1];
+  if (iy > 0) s += a[3] * x[i - nx];
+  if (iy < ny - 1) s += a[4] * x[i + nx];
+  if (iz > 0) s += a[5] * x[i - nx * ny];
+  if (iz < nz - 1) s += a[6] * x[i + nx * ny];
+  return s;
+}
+
+// One half-sweep of red-black Gauss-Seidel on cells of parity `colour`.
+__global__ void coarse_gs(const double* __restrict__ A, double* __restrict__ x,
+                          const double* __restrict__ bvec, int nx, int ny, int nz, int colour) {
+  const int b = blockIdx.y;
+  const int N = nx * ny * nz;
+  const double* Ab = A + (long long)b * N * 7;
+  double* xb = x + (long long)b * N;
+  const double* bb = bvec + (long long)b * N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+    if (((ix + iy + iz) & 1) != colour) continue;
+    const double* a = Ab + (long long)i * 7;
+    if (a[0] == 0.0) continue;
+    xb[i] = (bb[i] - stencil_off(a, xb, i, nx, ny, nz, ix, iy, iz)) / a[0];
+  }
+}
+
+// r = b - A x
+__global__ void coarse_residual(const double* __restrict__ A, const double* __restrict__ x,
+                                const double* __restrict__ bvec, double* __restrict__ r, int nx,
+                                int ny, int nz) {
+  const int b = blockIdx.y;
+  const int N = nx * ny * nz;
+  const double* Ab = A + (long long)b * N * 7;
+  const double* xb = x + (long long)b * N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+    const double* a = Ab + (long long)i * 7;
+    r[(long long)b * N + i] = bvec[(long long)b * N + i] - a[0] * xb[i] -
+                              stencil_off(a, xb, i, nx, ny, nz, ix, iy, iz);
+  }
+}
+
+// b_c = sum of the fine residual over each 2 x 2 x 2 aggregate
+__global__ void coarse_restrict(const double* __restrict__ rf, int fx, int fy, int fz,
+                                double* __restrict__ bc, int cx, int cy, int cz) {
+  const int b = blockIdx.y;
+  const int Nc = cx * cy * cz, Nf = fx * fy * fz;
+  for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < Nc; C += gridDim.x * blockDim.x) {
+    const int jx = C % cx, jy = (C / cx) % cy, jz = C / (cx * cy);
+    double s = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int ix = 2 * jx + dx, iy = 2 * jy + dy, iz = 2 * jz + dz;
+          if (ix < fx && iy < fy && iz < fz) s += rf[(long long)b * Nf + ix + fx * (iy + fy * iz)];
+        }
+    bc[(long long)b * Nc + C] = s;
+  }
+}
+
+// x_f += x_c on every fine cell of the aggregate
+__global__ void coarse_prolong(const double* __restrict__ xc, int cx, int cy, int cz,
+                               double* __restrict__ xf, int fx, int fy, int fz) {
+  const int b = blockIdx.y;
+  const int Nc = cx * cy * cz, Nf = fx * fy * fz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Nf; i += gridDim.x * blockDim.x) {
+    const int ix = i % fx, iy = (i / fx) % fy, iz = i / (fx * fy);
+    xf[(long long)b * Nf + i] += xc[(long long)b * Nc + ix / 2 + cx * (iy / 2 + cy * (iz / 2))];
+  }
+}
+
+// Coarsest level (at most kCoarsestCells cells): x = 0, then `sweeps`
+// red-black Gauss-Seidel sweeps inside one thread block per operating point,
+// with the stencil, x and b held in shared memory.
+constexpr int kCoarsestCells = 512;
+
+__global__ void __launch_bounds__(kCoarsestCells)
+coarse_solve_small(const double* __restrict__ A, double* __restrict__ x,
+                   const double* __restrict__ bvec, int nx, int ny, int nz, int sweeps) {
+  __shared__ double sA[kCoarsestCells * 7];
+  __shared__ double sx[kCoarsestCells];
+  __shared__ double sb[kCoarsestCells];
+  const int b = blockIdx.x;
+  const int N = nx * ny * nz;  // <= kCoarsestCells, checked by the host
+  const double* Ab = A + (long long)b * N * 7;
+  for (int i = threadIdx.x; i < 7 * N; i += blockDim.x) sA[i] = Ab[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    sx[i] = 0.0;
+    sb[i] = bvec[(long long)b * N + i];
+  }
+  __syncthreads();
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+        if (((ix + iy + iz) & 1) != colour) continue;
+        const double* a = sA + i * 7;
+        if (a[0] != 0.0) sx[i] = (sb[i] - stencil_off(a, sx, i, nx, ny, nz, ix, iy, iz)) / a[0];
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) x[(long long)b * N + i] = sx[i];
+}
+
+// b0[K] = sum over the Phi nodes of element K of r (P^T r)
+template <class TV>
+__global__ void coarse_from_fine(const TV* __restrict__ r, double* __restrict__ b0, int E, int Np,
+                                 long long bstride) {
+  const int b = blockIdx.y;
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < E; K += gridDim.x * blockDim.x) {
+    const TV* row = r + b * bstride + (long long)K * Np;
+    double s = 0.0;
+    for (int i = 0; i < Np; ++i) s += (double)row[i];
+    b0[(long long)b * E + K] = s;
+  }
+}
+
+// z[Phi nodes of K] += x0[K] (P x0)
+template <class TV>
+__global__ void coarse_to_fine(const double* __restrict__ x0, TV* __restrict__ z, int E, int Np,
+                               long long bstride) {
+  const int b = blockIdx.y;
+  const long long n = (long long)E * Np;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    z[b * bstride + t] += (TV)x0[(long long)b * E + t / Np];
+}
+
 // ------------------------------------------------------------------ block inverse
 // In-place Gauss-Jordan inversion with partial (row) pivoting of one n x n
 // block per thread block. The matrix lives in shared memory when it fits
@@ -489,6 +703,13 @@ struct SolverState {
   size_t gbuf_bytes = 0;
   const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
   int gkey_i[4] = {0, 0, 0, 0};
+  // two-level preconditioner: element-mean potential correction
+  bool coarse = false;            // enabled by enp_set_preconditioner
+  bool coarse_ready = false;
+  struct Level { int nx, ny, nz, n; double *A, *x, *b, *r; };
+  std::vector<Level> levels;      // level 0: the element grid
+  double* cwork = nullptr;        // Jv scratch for the coarse setup [B][n]
+  size_t cwork_count = 0;
 };
 
 }  // namespace
@@ -542,12 +763,116 @@ cudaError_t small(enp_handle h, size_t count) {
 
 }  // namespace
 
+
+namespace {
+
+constexpr int kCoarsestSweeps = 100;
+constexpr int kSmoothSweeps = 2;
+
+cudaError_t coarse_levels(enp_handle h) {
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  if (!S.levels.empty()) return cudaSuccess;
+  int nx = P.ne[0], ny = P.ne[1], nz = P.ne[2];
+  const int B = h->batch;
+  while (true) {
+    SolverState::Level L{nx, ny, nz, nx * ny * nz, nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaMalloc(&L.A, sizeof(double) * 7 * (size_t)L.n * B);
+    if (e == cudaSuccess) e = cudaMalloc(&L.x, sizeof(double) * (size_t)L.n * B);
+    if (e == cudaSuccess) e = cudaMalloc(&L.b, sizeof(double) * (size_t)L.n * B);
+    if (e == cudaSuccess) e = cudaMalloc(&L.r, sizeof(double) * (size_t)L.n * B);
+    S.levels.push_back(L);
+    if (e != cudaSuccess) return e;
+    if (L.n <= enp::kCoarsestCells) break;
+    nx = (nx + 1) / 2; ny = (ny + 1) / 2; nz = (nz + 1) / 2;
+  }
+  return cudaSuccess;
+}
+
+// A0 = P^T J_PhiPhi P from 7 coloured J v passes at u, then the hierarchy.
+cudaError_t coarse_setup(enp_handle h, const double* u) {
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  const int B = h->batch;
+  cudaError_t e = coarse_levels(h);
+  if (e != cudaSuccess) return e;
+  const long long ntot = h->n_dof * B;
+  if ((e = ensure(&S.cwork, S.cwork_count, (size_t)2 * ntot)) != cudaSuccess) return e;
+  double* v = S.cwork;
+  double* jv = S.cwork + ntot;
+  SolverState::Level& L0 = S.levels[0];
+  cudaMemsetAsync(L0.A, 0, sizeof(double) * 7 * (size_t)L0.n * B, h->stream);
+  cudaMemsetAsync(v, 0, sizeof(double) * ntot, h->stream);
+  const int gx = grid_for((long long)P.E * P.Np);
+  for (int c = 0; c < 7; ++c) {
+    enp::coarse_colour_vector<<<dim3(gx, B), 256, 0, h->stream>>>(v, P.ne[0], P.ne[1], P.ne[2], P.Np,
+                                                                   P.batch_stride, P.E, c);
+    e = enp::launch_op<double>(enp::kJvp, P, h->d_tab, u, v, jv, B, h->stream);
+    if (e != cudaSuccess) return e;
+    enp::coarse_gather<<<dim3(grid_for(P.E), B), 256, 0, h->stream>>>(jv, L0.A, P.ne[0], P.ne[1],
+                                                                      P.ne[2], P.Np, P.batch_stride, c);
+  }
+  for (size_t l = 0; l + 1 < S.levels.size(); ++l) {
+    const auto& F = S.levels[l];
+    const auto& C = S.levels[l + 1];
+    enp::coarse_aggregate<<<dim3(grid_for(C.n), B), 256, 0, h->stream>>>(F.A, F.nx, F.ny, F.nz, C.A,
+                                                                         C.nx, C.ny, C.nz);
+  }
+  S.coarse_ready = true;
+  return cudaGetLastError();
+}
+
+void vcycle(enp_handle h, size_t l) {
+  SolverState& S = state_of(h);
+  const int B = h->batch;
+  auto& L = S.levels[l];
+  if (l + 1 == S.levels.size()) {
+    enp::coarse_solve_small<<<B, enp::kCoarsestCells, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, kCoarsestSweeps);
+    return;
+  }
+  const dim3 g(grid_for(L.n), B);
+  cudaMemsetAsync(L.x, 0, sizeof(double) * (size_t)L.n * B, h->stream);
+  for (int sw = 0; sw < kSmoothSweeps; ++sw) {
+    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, 0);
+    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, 1);
+  }
+  auto& C = S.levels[l + 1];
+  enp::coarse_residual<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.r, L.nx, L.ny, L.nz);
+  enp::coarse_restrict<<<dim3(grid_for(C.n), B), 256, 0, h->stream>>>(L.r, L.nx, L.ny, L.nz, C.b,
+                                                                      C.nx, C.ny, C.nz);
+  vcycle(h, l + 1);
+  enp::coarse_prolong<<<g, 256, 0, h->stream>>>(C.x, C.nx, C.ny, C.nz, L.x, L.nx, L.ny, L.nz);
+  for (int sw = 0; sw < kSmoothSweeps; ++sw) {
+    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, 1);
+    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, 0);
+  }
+}
+
+// z += P V(P^T r): the coarse correction of the two-level preconditioner.
+template <class TV>
+cudaError_t coarse_apply(enp_handle h, const TV* r, TV* z) {
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  const int B = h->batch;
+  auto& L0 = S.levels[0];
+  enp::coarse_from_fine<TV><<<dim3(grid_for(P.E), B), 256, 0, h->stream>>>(r, L0.b, P.E, P.Np,
+                                                                          P.batch_stride);
+  vcycle(h, 0);
+  enp::coarse_to_fine<TV><<<dim3(grid_for((long long)P.E * P.Np), B), 256, 0, h->stream>>>(
+      L0.x, z, P.E, P.Np, P.batch_stride);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 void enp_solver_free(enp_handle h) {
   if (!h || !h->solver) return;
   SolverState& S = h->solver->s;
   cudaFree(S.blocks); cudaFree(S.binv); cudaFree(S.gj_work); cudaFree(S.d_flag);
   cudaFree(S.blocks32); cudaFree(S.u32);
   cudaFree(S.part); cudaFree(S.dsmall); cudaFree(S.V); cudaFree(S.dRdtheta);
+  for (auto& L : S.levels) { cudaFree(L.A); cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); }
+  cudaFree(S.cwork);
   if (S.gexec) cudaGraphExecDestroy(S.gexec);
   if (S.gstream) cudaStreamDestroy(S.gstream);
   cudaFree(S.gbuf);
@@ -680,6 +1005,9 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     h->err = "singular or non-finite element block";
     return ENP_ERR_NONFINITE;
   }
+  if (S.coarse) {
+    if ((e = coarse_setup(h, u)) != cudaSuccess) return cuda_err(h, e, "coarse setup");
+  }
   return ENP_OK;
 }
 
@@ -687,7 +1015,20 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
 
 // Apply the stored block inverse to a vector of type TV (double or float).
 template <class TV>
+static cudaError_t bj_apply_plain(enp_handle h, const TV* x, TV* y);
+
+// The preconditioner: block-Jacobi, plus the coarse potential correction when
+// the two-level preconditioner is enabled and set up.
+template <class TV>
 static cudaError_t bj_apply_any(enp_handle h, const TV* x, TV* y) {
+  SolverState& S = state_of(h);
+  cudaError_t e = bj_apply_plain<TV>(h, x, y);
+  if (e == cudaSuccess && S.coarse && S.coarse_ready) e = coarse_apply<TV>(h, x, y);
+  return e;
+}
+
+template <class TV>
+static cudaError_t bj_apply_plain(enp_handle h, const TV* x, TV* y) {
   SolverState& S = state_of(h);
   const OpParams& P = h->prm;
   const int nb = S.nb;
@@ -708,6 +1049,36 @@ static cudaError_t bj_apply_any(enp_handle h, const TV* x, TV* y) {
         (const __nv_bfloat16*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride);
   }
   return cudaGetLastError();
+}
+
+extern "C" enp_status enp_set_preconditioner(enp_handle h, int two_level) {
+  if (!h) return ENP_ERR_INVALID_ARG;
+  if (two_level < 0 || two_level > 1) {
+    h->err = "two_level must be 0 or 1";
+    return ENP_ERR_INVALID_ARG;
+  }
+  if (two_level == 1 && h->prm.dim != 3) {
+    h->err = "the two-level preconditioner needs a hexahedral mesh";
+    return ENP_ERR_UNSUPPORTED;
+  }
+  SolverState& S = state_of(h);
+  S.coarse = two_level == 1;
+  S.coarse_ready = false;
+  return ENP_OK;
+}
+
+extern "C" enp_status enp_coarse_operator(enp_handle h, double* a0) {
+  if (!h || !a0) return ENP_ERR_INVALID_ARG;
+  SolverState& S = state_of(h);
+  if (!S.coarse || !S.coarse_ready || S.levels.empty()) {
+    h->err = "the two-level preconditioner has not been set up";
+    return ENP_ERR_INVALID_ARG;
+  }
+  const auto& L = S.levels[0];
+  cudaError_t e = cudaMemcpyAsync(a0, L.A, sizeof(double) * 7 * (size_t)L.n * h->batch,
+                                  cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "coarse operator copy");
 }
 
 extern "C" enp_status enp_block_jacobi_apply(enp_handle h, const double* x, double* y) {
@@ -736,7 +1107,7 @@ static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
   const OpParams& P = h->prm;
   const long long n = h->n_dof;
   const int B = h->batch;
-  const int m = std::max(1, std::min(o->restart, 200));
+  const int m = std::max(1, std::min(o->restart, 255));  // coefficient staging holds 256
   const long long ntot = n * B;
   const bool precond = S.storage >= 0;
   cudaError_t e;
@@ -892,7 +1263,7 @@ static enp_status fgmres_graph(enp_handle h, const TV* ulin, const TV* b, TV* x,
   const OpParams& P = h->prm;
   const long long n = h->n_dof;
   const int B = h->batch;
-  const int m = std::max(1, std::min(o->restart, 200));
+  const int m = std::max(1, std::min(o->restart, 255));  // coefficient staging holds 256
   const long long ntot = n * B;
   const bool precond = S.storage >= 0;
   cudaError_t e;
