@@ -246,6 +246,10 @@ typedef struct {
   int bj_storage;        /* block-Jacobi storage: 0 FP64, 1 FP32, 2 BF16 */
   int mixed;             /* 1: inner FGMRES with the FP32 operator and vectors */
   enp_krylov_opts krylov;
+  int pc_lag;            /* rebuild the preconditioner every pc_lag Newton iterations
+                            (<= 1: every iteration), and after an inner solve that did
+                            not converge; between rebuilds the preconditioner of an
+                            earlier iterate is kept (FGMRES needs no exact one) */
 } enp_newton_opts;
 
 typedef struct {
@@ -255,12 +259,16 @@ typedef struct {
   double initial_norm;
   double residual_norm;
   double history[64];    /* ||R|| after each iteration (largest over operating points) */
+  int setups;            /* preconditioner setups */
+  double setup_seconds;  /* wall time in preconditioner setups */
+  double krylov_seconds; /* wall time in the inner FGMRES solves */
 } enp_newton_stats;
 
 /* Newton's method with backtracking line search (Sec. 4) on R(u) = 0, in
- * place on u (device, [batch][m][E][Np]). Each iteration rebuilds the
- * block-Jacobi preconditioner at u and solves J du = -R with FGMRES to
- * opts->krylov.rtol. Synchronises. Errors: NOT_CONVERGED, NONFINITE, OOM, CUDA. */
+ * place on u (device, [batch][m][E][Np]). An iteration rebuilds the
+ * preconditioner at u (every iteration, or every opts->pc_lag iterations) and
+ * solves J du = -R with FGMRES to opts->krylov.rtol. Synchronises.
+ * Errors: NOT_CONVERGED, NONFINITE, OOM, CUDA. */
 enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* opts,
                             enp_newton_stats* stats);
 

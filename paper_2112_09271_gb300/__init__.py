@@ -116,13 +116,16 @@ class KrylovStats(ctypes.Structure):
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("max_it", ctypes.c_int), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("max_backtracks", ctypes.c_int),
-                ("bj_storage", ctypes.c_int), ("mixed", ctypes.c_int), ("krylov", KrylovOpts)]
+                ("bj_storage", ctypes.c_int), ("mixed", ctypes.c_int), ("krylov", KrylovOpts),
+                ("pc_lag", ctypes.c_int)]
 
 
 class NewtonStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
                 ("converged", ctypes.c_int), ("initial_norm", ctypes.c_double),
-                ("residual_norm", ctypes.c_double), ("history", ctypes.c_double * 64)]
+                ("residual_norm", ctypes.c_double), ("history", ctypes.c_double * 64),
+                ("setups", ctypes.c_int), ("setup_seconds", ctypes.c_double),
+                ("krylov_seconds", ctypes.c_double)]
 
 
 BJ_F64, BJ_F32, BJ_BF16 = 0, 1, 2
@@ -386,11 +389,13 @@ class Operator:
 
     def newton_solve(self, u, max_it=20, rtol=1e-10, atol=0.0, armijo_c=1e-4,
                      max_backtracks=12, bj_storage=BJ_F64, mixed=False, krylov_restart=30,
-                     krylov_max_it=500, krylov_rtol=1e-3, raise_on_fail=True, graph=False):
+                     krylov_max_it=500, krylov_rtol=1e-3, raise_on_fail=True, graph=False,
+                     pc_lag=1):
         """Newton with backtracking line search in place on u; returns the stats."""
         import torch
         o = NewtonOpts(max_it, rtol, atol, armijo_c, max_backtracks, bj_storage, int(mixed),
-                       KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0, int(graph)))
+                       KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0, int(graph)),
+                       int(pc_lag))
         st = NewtonStats()
         rc = self._lib.enp_newton_solve(self.h, _dptr(u, torch.float64), ctypes.byref(o),
                                         ctypes.byref(st))

@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -1511,7 +1512,13 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
     if (!std::isfinite(rn[b])) { cleanup(); h->err = "non-finite initial residual"; return ENP_ERR_NONFINITE; }
     tol[b] = std::max(o->rtol * r0[b], o->atol);
   }
-  int it = 0, kry_total = 0;
+  int it = 0, kry_total = 0, setups = 0, since_setup = 0;
+  bool rebuild = true;
+  double t_setup = 0.0, t_krylov = 0.0;
+  using clk = std::chrono::steady_clock;
+  auto seconds_since = [](clk::time_point t0) {
+    return std::chrono::duration<double>(clk::now() - t0).count();
+  };
   if (st) { std::memset(st, 0, sizeof(*st)); st->initial_norm = maxof(r0); st->history[0] = maxof(rn); }
   while (true) {
     bool all_conv = true;
@@ -1521,9 +1528,19 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
     }
     if (all_conv) break;
     if (it >= o->max_it) { status = ENP_ERR_NOT_CONVERGED; h->err = "Newton reached max_it"; break; }
-    enp_status s2 = enp_block_jacobi_setup(h, u, o->bj_storage);
+    enp_status s2 = ENP_OK;
+    if (rebuild || since_setup >= std::max(o->pc_lag, 1)) {
+      const auto t0 = clk::now();
+      s2 = enp_block_jacobi_setup(h, u, o->bj_storage);  // synchronises
+      t_setup += seconds_since(t0);
+      ++setups;
+      since_setup = 0;
+      rebuild = false;
+    }
     if (s2 != ENP_OK) { status = s2; break; }
+    ++since_setup;
     enp_krylov_stats ks{};
+    const auto tk = clk::now();
     enp_krylov_opts ko = o->krylov;
     // right-hand side -R on the running points, 0 on the converged ones
     for (int b = 0; b < B; ++b) lam[b] = -mask[b];
@@ -1541,8 +1558,11 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
       s2 = ko.graph ? fgmres_graph<double>(h, u, rt, du, &ko, &ks)
                     : fgmres_any<double>(h, u, rt, du, &ko, &ks);
     }
+    cudaStreamSynchronize(h->stream);
+    t_krylov += seconds_since(tk);
     kry_total += ks.iterations;
     if (s2 != ENP_OK && s2 != ENP_ERR_NOT_CONVERGED) { status = s2; break; }
+    if (s2 == ENP_ERR_NOT_CONVERGED) rebuild = true;  // a stale preconditioner may be the cause
     // backtracking line search, one step length per operating point
     std::vector<int> accepted(B, 0);
     for (int b = 0; b < B; ++b) { lam[b] = mask[b] > 0 ? 1.0 : 0.0; accepted[b] = mask[b] == 0.0; }
@@ -1571,6 +1591,9 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
   if (st) {
     st->iterations = it;
     st->krylov_iterations = kry_total;
+    st->setups = setups;
+    st->setup_seconds = t_setup;
+    st->krylov_seconds = t_krylov;
     st->residual_norm = maxof(rn);
     st->converged = (status == ENP_OK) ? 1 : 0;
   }

@@ -47,3 +47,42 @@ def test_create_rejects_bad_descriptors_without_gpu_work():
                              ctypes.byref(dd), None) == enp.ENP_ERR_INVALID_ARG
     assert not h.value
     assert lib.enp_residual(None, None, None) == enp.ENP_ERR_INVALID_ARG
+
+
+STRUCTS = [("enp_mesh_desc", "MeshDesc"), ("enp_physics_desc", "PhysicsDesc"),
+           ("enp_disc_desc", "DiscDesc"), ("enp_krylov_opts", "KrylovOpts"),
+           ("enp_krylov_stats", "KrylovStats"), ("enp_newton_opts", "NewtonOpts"),
+           ("enp_newton_stats", "NewtonStats")]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Size and every field offset of each ctypes structure equal those the C
+    compiler gives the header's struct (a field added on one side only fails)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "enp_dg.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS:
+        cls = getattr(enp, pyname)
+        lines.append(f'printf("{pyname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{pyname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    # the header declares the enp_status enum and plain C types only
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        a, b, c = line.split()
+        got[(a, b)] = int(c)
+    for _, pyname in STRUCTS:
+        cls = getattr(enp, pyname)
+        assert got[(pyname, "size")] == ctypes.sizeof(cls), pyname
+        for f, _ in cls._fields_:
+            assert got[(pyname, f)] == getattr(cls, f).offset, (pyname, f)
