@@ -265,6 +265,36 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.01, 0.08)):
     return out
 
 
+def run_fgmres_profile(enp, W, args):
+    """Whole FGMRES(50) restart cycles (50 iterations each: rtol 0) on the solve
+    workload with the two-level preconditioner, FP64 or FP32 (`--only
+    fgmres_f64|fgmres_f32`): `warmup` untimed cycles, then `steps` timed ones;
+    the per-iteration time of the Krylov loop (J v, preconditioner, CGS2)."""
+    import torch
+    prob = W.config(args.solve_workload)
+    op = enp.Operator(prob)
+    op.set_preconditioner(1)
+    f32 = args.only == "fgmres_f32"
+    u = torch.tensor(W.random_state(prob, 2), device="cuda")
+    op.block_jacobi_setup(u, enp.BJ_F32 if f32 else enp.BJ_F64)
+    dt = torch.float32 if f32 else torch.float64
+    ul = u.to(dt)
+    b = torch.tensor(W.random_vector(prob, 6), device="cuda").to(dt)
+    x = torch.zeros_like(b)
+    its, t = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.fgmres_solve(ul, b, x, restart=50, max_it=50, rtol=0.0, raise_on_fail=False)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            t += time.perf_counter() - t0
+            its += st["iterations"]
+    return {"only": args.only, "workload": prob.name, "n_dof": prob.n_dof,
+            "iterations": its, "ms_per_iteration": 1e3 * t / its, "kernel_hash": _kernel_hash()}
+
+
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
@@ -305,7 +335,9 @@ def main():
     ap.add_argument("--solve-workload", default="cube16_p3")
     ap.add_argument("--only", default=None,
                     help="time one operator alone (for profiling): residual_f64, jvp_f64, "
-                         "vjp_f64, jvp_f32, bj_apply_f32; no autotune, solves or e2e")
+                         "vjp_f64, jvp_f32, bj_apply_f32; no autotune, solves or e2e; or "
+                         "fgmres_f64 / fgmres_f32: FGMRES(50) cycles with the two-level "
+                         "preconditioner on the solve workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -328,6 +360,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     enp.build()
+    if args.only in ("fgmres_f64", "fgmres_f32"):
+        if rank == 0:
+            print(json.dumps(run_fgmres_profile(enp, W, args)), flush=True)
+        return
     prob = W.config(args.workload)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)

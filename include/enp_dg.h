@@ -192,8 +192,10 @@ enp_status enp_block_jacobi_apply(enp_handle h, const double* x, double* y);
  * element; A0 = P^T J_PhiPhi(u) P, a 7-point stencil on the element grid, is
  * assembled exactly from 7 coloured J v products at setup, and V is one
  * multigrid V-cycle on it (2 x 2 x 2 Galerkin aggregation, red-black
- * Gauss-Seidel, 2 + 2 sweeps per level, 100 sweeps on the coarsest grid of at
- * most 512 cells). The Schur-complement-like stiffness of the potential
+ * Gauss-Seidel, 2 + 2 sweeps per level; the coarsest grid, of at most 128
+ * cells, solved with its dense inverse, or by 100 sweeps if it is singular to
+ * working accuracy; the levels of at most 8192 cells run in one launch). A0 is
+ * assembled in FP64; the V-cycle runs in FP32 (it only preconditions). The Schur-complement-like stiffness of the potential
  * equation (Sec. 3.3) is what block-Jacobi alone cannot reduce.
  * Takes effect at the next setup. Errors: INVALID_ARG (two_level not 0 or 1),
  * UNSUPPORTED (two_level = 1 on a 2D mesh). */

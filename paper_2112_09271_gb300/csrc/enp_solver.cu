@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -53,41 +54,108 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Partial sums of nd dot products <V_i, w> (i < nd) over each batch item:
-// part[b][i][block]. V_i = V + i * vstride. Each thread accumulates in the
-// vector's own precision (FP32 vectors: FP32, no conversions on the FP64 pipe),
-// then the warp and block trees run in FP64. Fixed reduction order.
+// W consecutive values of a vector as one 16-byte load (W = 16 / sizeof(T)),
+// or one value (W = 1).
+template <class T, int W>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, T (&a)[W]) {
+  if constexpr (W == 1) {
+    a[0] = p[0];
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+  } else {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    a[0] = t.x; a[1] = t.y;
+  }
+}
+
+template <class T, int W>
+__device__ __forceinline__ void store_vec(T* __restrict__ p, const T (&a)[W]) {
+  if constexpr (W == 1) {
+    p[0] = a[0];
+  } else if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(a[0], a[1]);
+  }
+}
+
+// Transposed butterfly: from v[0..7] on every lane, lane l ends with the sum
+// over the warp's 32 lanes of v[l & 7] (9 shuffles instead of 8 x 5), in a
+// fixed order.
 template <class T>
+__device__ __forceinline__ T warp_reduce8(T (&v)[8], int lane) {
+  constexpr unsigned kAll = 0xffffffffu;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool up = lane & 4;
+    const T send = up ? v[i] : v[i + 4];
+    const T keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(kAll, send, 4);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool up = lane & 2;
+    const T send = up ? v[i] : v[i + 2];
+    const T keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(kAll, send, 2);
+  }
+  {
+    const bool up = lane & 1;
+    const T send = up ? v[0] : v[1];
+    const T keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(kAll, send, 1);
+  }
+  T r = v[0];
+  r += __shfl_xor_sync(kAll, r, 8);
+  r += __shfl_xor_sync(kAll, r, 16);
+  return r;
+}
+
+// Partial sums of nd dot products <V_i, w> (i < nd) over each batch item:
+// part[b][i][block]. V_i = V + i * vstride. The vectors are taken in groups of
+// kDotGroup with one accumulator each per thread (few registers), W
+// consecutive entries per 16-byte load; each thread runs over its units by
+// grid stride, accumulating in the vector's own precision (FP32 vectors: FP32,
+// no conversions on the FP64 pipe); the warp tree runs in that precision, the
+// block and grid sums in FP64. Fixed reduction order for a given grid.
+constexpr int kDotGroup = 8;
+
+template <class T, int W>
 __global__ void __launch_bounds__(kRedThreads)
 multidot_partial(const T* __restrict__ V, long long vstride, int nd, const T* __restrict__ w,
                  long long n, long long bstride, double* __restrict__ part) {
-  __shared__ double red[kRedThreads / 32][32];
+  __shared__ double red[kRedThreads / 32][kDotGroup];
   const int b = blockIdx.y;
   const T* wb = w + b * bstride;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 0; i0 < nd; i0 += 32) {
-    const int ni = min(32, nd - i0);
-    T acc[32];
+  const long long nu = n / W;
+  for (int i0 = 0; i0 < nd; i0 += kDotGroup) {
+    const int ni = min(kDotGroup, nd - i0);
+    const T* V0 = V + i0 * vstride + b * bstride;
+    T acc[kDotGroup];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = T(0);
-    for (long long k = blockIdx.x * (long long)kRedThreads + threadIdx.x; k < n;
-         k += (long long)gridDim.x * kRedThreads) {
-      const T wk = wb[k];
+    for (int i = 0; i < kDotGroup; ++i) acc[i] = T(0);
+    for (long long u = blockIdx.x * (long long)kRedThreads + threadIdx.x; u < nu;
+         u += (long long)gridDim.x * kRedThreads) {
+      T wv[W];
+      load_vec<T, W>(wb + u * W, wv);
 #pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (i < ni) acc[i] += V[(i0 + i) * vstride + b * bstride + k] * wk;
+      for (int i = 0; i < kDotGroup; ++i)
+        if (i < ni) {
+          T vv[W];
+          load_vec<T, W>(V0 + i * vstride + u * W, vv);
+#pragma unroll
+          for (int c = 0; c < W; ++c) acc[i] += vv[c] * wv[c];
+        }
     }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      if (i >= ni) break;
-      double s = warp_sum((double)acc[i]);
-      if (lane == 0) red[warp][i] = s;
-    }
+    const T r = warp_reduce8<T>(acc, lane);
+    if (lane < kDotGroup) red[warp][lane] = (double)r;
     __syncthreads();
-    if (warp == 0 && lane < ni) {
+    if (threadIdx.x < ni) {
       double s = 0.0;
-      for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[wv][lane];
-      part[((long long)b * nd + i0 + lane) * gridDim.x + blockIdx.x] = s;
+      for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[wv][threadIdx.x];
+      part[((long long)b * nd + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
     }
     __syncthreads();
   }
@@ -105,20 +173,49 @@ __global__ void finish_partials(const double* __restrict__ part, int nparts, int
 }
 
 // w[b] -= sum_i V_i[b] h[b][i]  (h on the device, [batch][nd], nd <= 256),
-// in the vector's precision with the coefficients staged once per block.
-template <class T>
-__global__ void multi_axpy(const T* __restrict__ V, long long vstride, int nd,
-                           const double* __restrict__ h, T* __restrict__ w, long long n,
-                           long long bstride) {
+// in the vector's precision with the coefficients staged once per block, W
+// entries per 16-byte load. With NORM, also the partial sums of ||w_new||^2
+// per block, part[b][block] (thread sums in the vector's precision, then FP64).
+template <class T, int W, bool NORM>
+__global__ void __launch_bounds__(kRedThreads)
+multi_axpy(const T* __restrict__ V, long long vstride, int nd, const double* __restrict__ h,
+           T* __restrict__ w, long long n, long long bstride, double* __restrict__ part) {
   __shared__ T hs[256];
+  __shared__ double red[kRedThreads / 32];
   const int b = blockIdx.y;
   for (int i = threadIdx.x; i < nd; i += blockDim.x) hs[i] = (T)h[b * nd + i];
   __syncthreads();
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
-    T acc = w[b * bstride + k];
-    for (int i = 0; i < nd; ++i) acc -= hs[i] * V[i * vstride + b * bstride + k];
-    w[b * bstride + k] = acc;
+  const long long nu = n / W;
+  T nrm = T(0);
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nu;
+       u += (long long)gridDim.x * blockDim.x) {
+    T acc[W];
+    load_vec<T, W>(w + b * bstride + u * W, acc);
+    const T* Vu = V + b * bstride + u * W;
+#pragma unroll 4
+    for (int i = 0; i < nd; ++i) {
+      T vv[W];
+      load_vec<T, W>(Vu + i * vstride, vv);
+      const T hi = hs[i];
+#pragma unroll
+      for (int c = 0; c < W; ++c) acc[c] -= hi * vv[c];
+    }
+    store_vec<T, W>(w + b * bstride + u * W, acc);
+    if (NORM) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) nrm += acc[c] * acc[c];
+    }
+  }
+  if (NORM) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double s = warp_sum((double)nrm);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int wv = 0; wv < kRedThreads / 32; ++wv) t += red[wv];
+      part[(long long)b * gridDim.x + blockIdx.x] = t;
+    }
   }
 }
 
@@ -221,18 +318,41 @@ __global__ void krylov_cycle_init(KrylovDev K, int B, int m, int* any_running, i
   if (!done) atomicOr(any_running, 1);
 }
 
-__global__ void krylov_hcol_add(KrylovDev K, int B, int m, int nd, int first) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per (b, i): dh[b][i] = the partials of <V_i, w>_b summed in block
+// order (as finish_partials), added into the Hessenberg column (first pass:
+// stored).
+__global__ void krylov_hcol_finish(KrylovDev K, const double* __restrict__ part, int nparts,
+                                   int B, int m, int nd, int first) {
+  const int t = blockIdx.x;
   if (t >= B * nd) return;
-  const int b = t / nd, i = t % nd;
-  const double v = K.dh[t];
-  K.hcol[(long long)b * (m + 1) + i] = first ? v : K.hcol[(long long)b * (m + 1) + i] + v;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += 32) s += part[(long long)t * nparts + k];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) {
+    const int b = t / nd, i = t % nd;
+    K.dh[t] = s;
+    K.hcol[(long long)b * (m + 1) + i] = first ? s : K.hcol[(long long)b * (m + 1) + i] + s;
+  }
 }
 
-// Iteration j of Arnoldi with Givens rotations, for every running point.
-__global__ void krylov_givens(KrylovDev K, int B, int m, int j, int* nonfinite) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ void givens_step(KrylovDev K, int b, int m, int j, int* nonfinite);
+
+// Iteration j of Arnoldi with Givens rotations, one warp per running point,
+// with ||w||^2 first summed from its partials in block order.
+__global__ void krylov_norm_givens(KrylovDev K, const double* __restrict__ part, int nparts, int B,
+                                   int m, int j, int* nonfinite) {
+  const int b = blockIdx.x;
   if (b >= B) return;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += 32) s += part[(long long)b * nparts + k];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) {
+    K.hn2[b] = s;
+    givens_step(K, b, m, j, nonfinite);
+  }
+}
+
+__device__ void givens_step(KrylovDev K, int b, int m, int j, int* nonfinite) {
   const double hn = sqrt(K.hn2[b]);
   if (K.jconv[b] != -1) { K.inv[b] = 0.0; return; }
   double* H = K.H + (long long)b * (m + 1) * m;
@@ -372,9 +492,27 @@ __global__ void coarse_aggregate(const double* __restrict__ Af, int fx, int fy, 
   }
 }
 
-__device__ __forceinline__ double stencil_off(const double* __restrict__ a, const double* __restrict__ x,
-                                              int i, int nx, int ny, int nz, int ix, int iy, int iz) {
-  double s = 0.0;
+// The V-cycle runs in FP32 (it only preconditions: FGMRES is flexible, and the
+// outer residual stays in the caller's precision). Each level's stencil is kept
+// packed per cell as 8 floats: the 7 entries and the inverse diagonal (0 where
+// the diagonal is 0: such a cell is left unchanged by smoothing).
+constexpr int kPack = 8;
+
+// (a0..a6 as float, 1 / a0) per cell, from the FP64 stencil
+__global__ void coarse_pack32(const double* __restrict__ A, float* __restrict__ A32,
+                              long long ncells) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncells;
+       c += (long long)gridDim.x * blockDim.x) {
+    const double* a = A + c * 7;
+    float* o = A32 + c * kPack;
+    for (int d = 0; d < 7; ++d) o[d] = (float)a[d];
+    o[7] = a[0] != 0.0 ? (float)(1.0 / a[0]) : 0.0f;
+  }
+}
+
+__device__ __forceinline__ float stencil_off(const float* __restrict__ a, const float* __restrict__ x,
+                                             int i, int nx, int ny, int nz, int ix, int iy, int iz) {
+  float s = 0.0f;
   if (ix > 0) s += a[1] * x[i - 1];
   if (ix < nx - 1) s += a[2] * x[i + 1];
   if (iy > 0) s += a[3] * x[i - nx];
@@ -384,117 +522,262 @@ __device__ __forceinline__ double stencil_off(const double* __restrict__ a, cons
   return s;
 }
 
+// The per-cell steps of the V-cycle, shared by the grid-wide kernels (large
+// levels) and the one-block kernel (small levels), so both give the same bits.
+// Ab, xb, bb: one operating point's packed stencil, iterate and right-hand side.
+
+// Gauss-Seidel update of cell i if it has parity `colour` (red-black).
+__device__ __forceinline__ void gs_cell(const float* __restrict__ Ab, float* __restrict__ xb,
+                                        const float* __restrict__ bb, int nx, int ny, int nz,
+                                        int colour, int i) {
+  const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+  if (((ix + iy + iz) & 1) != colour) return;
+  const float* a = Ab + (long long)i * kPack;
+  if (a[7] == 0.0f) return;
+  xb[i] = (bb[i] - stencil_off(a, xb, i, nx, ny, nz, ix, iy, iz)) * a[7];
+}
+
+__device__ __forceinline__ float residual_cell(const float* __restrict__ Ab,
+                                               const float* __restrict__ xb,
+                                               const float* __restrict__ bb, int nx, int ny,
+                                               int nz, int i) {
+  const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+  const float* a = Ab + (long long)i * kPack;
+  return bb[i] - a[0] * xb[i] - stencil_off(a, xb, i, nx, ny, nz, ix, iy, iz);
+}
+
+// sum of the fine values over the 2 x 2 x 2 aggregate of coarse cell C
+__device__ __forceinline__ float restrict_cell(const float* __restrict__ rf, int fx, int fy,
+                                               int fz, int cx, int cy, int C) {
+  const int jx = C % cx, jy = (C / cx) % cy, jz = C / (cx * cy);
+  float s = 0.0f;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const int ix = 2 * jx + dx, iy = 2 * jy + dy, iz = 2 * jz + dz;
+        if (ix < fx && iy < fy && iz < fz) s += rf[ix + fx * (iy + fy * iz)];
+      }
+  return s;
+}
+
+// the coarse value of the aggregate that holds fine cell i
+__device__ __forceinline__ float prolong_cell(const float* __restrict__ xc, int cx, int cy,
+                                              int fx, int fy, int i) {
+  const int ix = i % fx, iy = (i / fx) % fy, iz = i / (fx * fy);
+  return xc[ix / 2 + cx * (iy / 2 + cy * (iz / 2))];
+}
+
 // One half-sweep of red-black Gauss-Seidel on cells of parity `colour`.
-__global__ void coarse_gs(const double* __restrict__ A, double* __restrict__ x,
-                          const double* __restrict__ bvec, int nx, int ny, int nz, int colour) {
+__global__ void coarse_gs(const float* __restrict__ A, float* __restrict__ x,
+                          const float* __restrict__ bvec, int nx, int ny, int nz, int colour) {
   const int b = blockIdx.y;
   const int N = nx * ny * nz;
-  const double* Ab = A + (long long)b * N * 7;
-  double* xb = x + (long long)b * N;
-  const double* bb = bvec + (long long)b * N;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
-    if (((ix + iy + iz) & 1) != colour) continue;
-    const double* a = Ab + (long long)i * 7;
-    if (a[0] == 0.0) continue;
-    xb[i] = (bb[i] - stencil_off(a, xb, i, nx, ny, nz, ix, iy, iz)) / a[0];
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    gs_cell(A + (long long)b * N * kPack, x + (long long)b * N, bvec + (long long)b * N, nx, ny,
+            nz, colour, i);
 }
 
 // r = b - A x
-__global__ void coarse_residual(const double* __restrict__ A, const double* __restrict__ x,
-                                const double* __restrict__ bvec, double* __restrict__ r, int nx,
+__global__ void coarse_residual(const float* __restrict__ A, const float* __restrict__ x,
+                                const float* __restrict__ bvec, float* __restrict__ r, int nx,
                                 int ny, int nz) {
   const int b = blockIdx.y;
   const int N = nx * ny * nz;
-  const double* Ab = A + (long long)b * N * 7;
-  const double* xb = x + (long long)b * N;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
-    const double* a = Ab + (long long)i * 7;
-    r[(long long)b * N + i] = bvec[(long long)b * N + i] - a[0] * xb[i] -
-                              stencil_off(a, xb, i, nx, ny, nz, ix, iy, iz);
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    r[(long long)b * N + i] = residual_cell(A + (long long)b * N * kPack, x + (long long)b * N,
+                                            bvec + (long long)b * N, nx, ny, nz, i);
 }
 
 // b_c = sum of the fine residual over each 2 x 2 x 2 aggregate
-__global__ void coarse_restrict(const double* __restrict__ rf, int fx, int fy, int fz,
-                                double* __restrict__ bc, int cx, int cy, int cz) {
+__global__ void coarse_restrict(const float* __restrict__ rf, int fx, int fy, int fz,
+                                float* __restrict__ bc, int cx, int cy, int cz) {
   const int b = blockIdx.y;
   const int Nc = cx * cy * cz, Nf = fx * fy * fz;
-  for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < Nc; C += gridDim.x * blockDim.x) {
-    const int jx = C % cx, jy = (C / cx) % cy, jz = C / (cx * cy);
-    double s = 0.0;
-    for (int dz = 0; dz < 2; ++dz)
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx) {
-          const int ix = 2 * jx + dx, iy = 2 * jy + dy, iz = 2 * jz + dz;
-          if (ix < fx && iy < fy && iz < fz) s += rf[(long long)b * Nf + ix + fx * (iy + fy * iz)];
-        }
-    bc[(long long)b * Nc + C] = s;
-  }
+  for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < Nc; C += gridDim.x * blockDim.x)
+    bc[(long long)b * Nc + C] = restrict_cell(rf + (long long)b * Nf, fx, fy, fz, cx, cy, C);
 }
 
 // x_f += x_c on every fine cell of the aggregate
-__global__ void coarse_prolong(const double* __restrict__ xc, int cx, int cy, int cz,
-                               double* __restrict__ xf, int fx, int fy, int fz) {
+__global__ void coarse_prolong(const float* __restrict__ xc, int cx, int cy, int cz,
+                               float* __restrict__ xf, int fx, int fy, int fz) {
   const int b = blockIdx.y;
   const int Nc = cx * cy * cz, Nf = fx * fy * fz;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Nf; i += gridDim.x * blockDim.x) {
-    const int ix = i % fx, iy = (i / fx) % fy, iz = i / (fx * fy);
-    xf[(long long)b * Nf + i] += xc[(long long)b * Nc + ix / 2 + cx * (iy / 2 + cy * (iz / 2))];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Nf; i += gridDim.x * blockDim.x)
+    xf[(long long)b * Nf + i] += prolong_cell(xc + (long long)b * Nc, cx, cy, fx, fy, i);
+}
+
+// The coarsest level (at most kCoarsestCells cells) is solved with its dense
+// inverse, computed in FP64 at setup by the block Gauss-Jordan kernel below and
+// stored in FP32. If that matrix is singular to working accuracy (a potential
+// fixed by no boundary condition), it is smoothed instead: x = 0, then
+// `sweeps` red-black Gauss-Seidel sweeps inside one thread block per operating
+// point, with the stencil, x and b held in shared memory.
+constexpr int kCoarsestCells = 128;
+
+// dense[b][i][j] = the FP64 stencil rows of a level as a dense n x n matrix
+// (one block per operating point)
+__global__ void coarse_dense(const double* __restrict__ A, int nx, int ny, int nz,
+                             double* __restrict__ dense) {
+  const int b = blockIdx.x;
+  const int N = nx * ny * nz;
+  double* D = dense + (long long)b * N * N;
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) D[t] = 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+    const double* a = A + ((long long)b * N + i) * 7;
+    double* row = D + (long long)i * N;
+    row[i] = a[0];
+    if (ix > 0) row[i - 1] = a[1];
+    if (ix < nx - 1) row[i + 1] = a[2];
+    if (iy > 0) row[i - nx] = a[3];
+    if (iy < ny - 1) row[i + nx] = a[4];
+    if (iz > 0) row[i - nx * ny] = a[5];
+    if (iz < nz - 1) row[i + nx * ny] = a[6];
   }
 }
 
-// Coarsest level (at most kCoarsestCells cells): x = 0, then `sweeps`
-// red-black Gauss-Seidel sweeps inside one thread block per operating point,
-// with the stencil, x and b held in shared memory.
-constexpr int kCoarsestCells = 512;
+// Row r of inv * b with the inverse stored transposed (M[c][r]).
+__device__ __forceinline__ float dense_row(const float* __restrict__ M,
+                                           const float* __restrict__ bb, int N, int r) {
+  float s = 0.0f;
+  for (int c = 0; c < N; ++c) s += M[(long long)c * N + r] * bb[c];
+  return s;
+}
+
+// x_b = inv_b r_b, one block per operating point.
+__global__ void __launch_bounds__(kCoarsestCells)
+coarse_dense_apply(const float* __restrict__ invT, const float* __restrict__ rhs, int N,
+                   float* __restrict__ x) {
+  const int b = blockIdx.x;
+  for (int r = threadIdx.x; r < N; r += blockDim.x)
+    x[(long long)b * N + r] = dense_row(invT + (long long)b * N * N, rhs + (long long)b * N, N, r);
+}
 
 __global__ void __launch_bounds__(kCoarsestCells)
-coarse_solve_small(const double* __restrict__ A, double* __restrict__ x,
-                   const double* __restrict__ bvec, int nx, int ny, int nz, int sweeps) {
-  __shared__ double sA[kCoarsestCells * 7];
-  __shared__ double sx[kCoarsestCells];
-  __shared__ double sb[kCoarsestCells];
+coarse_solve_small(const float* __restrict__ A, float* __restrict__ x,
+                   const float* __restrict__ bvec, int nx, int ny, int nz, int sweeps) {
+  __shared__ float sA[kCoarsestCells * kPack];
+  __shared__ float sx[kCoarsestCells];
+  __shared__ float sb[kCoarsestCells];
   const int b = blockIdx.x;
   const int N = nx * ny * nz;  // <= kCoarsestCells, checked by the host
-  const double* Ab = A + (long long)b * N * 7;
-  for (int i = threadIdx.x; i < 7 * N; i += blockDim.x) sA[i] = Ab[i];
+  const float* Ab = A + (long long)b * N * kPack;
+  for (int i = threadIdx.x; i < kPack * N; i += blockDim.x) sA[i] = Ab[i];
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    sx[i] = 0.0;
+    sx[i] = 0.0f;
     sb[i] = bvec[(long long)b * N + i];
   }
   __syncthreads();
   for (int sw = 0; sw < sweeps; ++sw)
     for (int colour = 0; colour < 2; ++colour) {
-      for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
-        if (((ix + iy + iz) & 1) != colour) continue;
-        const double* a = sA + i * 7;
-        if (a[0] != 0.0) sx[i] = (sb[i] - stencil_off(a, sx, i, nx, ny, nz, ix, iy, iz)) / a[0];
-      }
+      for (int i = threadIdx.x; i < N; i += blockDim.x) gs_cell(sA, sx, sb, nx, ny, nz, colour, i);
       __syncthreads();
     }
   for (int i = threadIdx.x; i < N; i += blockDim.x) x[(long long)b * N + i] = sx[i];
 }
 
-// b0[K] = sum over the Phi nodes of element K of r (P^T r)
+// The small levels of the V-cycle (at most kTailCells cells) run in one
+// thread block per operating point, with a barrier between steps, instead of
+// one launch per half-sweep: levels l0 .. nl-2 are smoothed, their residuals
+// restricted, the coarsest solved (its inverse, or smoothing), and the
+// corrections prolonged and post-smoothed, as in the grid-wide kernels.
+constexpr int kTailCells = 8192;
+constexpr int kTailThreads = 1024;
+constexpr int kMaxLevels = 16;
+
+struct LevelDev {
+  int nx, ny, nz, n;
+  const float* A;
+  float *x, *b, *r;
+};
+
+struct VcycleTail {
+  int l0, nl;
+  LevelDev L[kMaxLevels];
+  const float* inv;  // coarsest inverse, transposed, [B][n][n]; null: smoothing
+  int smooth, coarsest_sweeps;
+};
+
+__global__ void __launch_bounds__(kTailThreads) coarse_vcycle_tail(const VcycleTail T) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int l = T.l0; l < T.nl - 1; ++l) {
+    const LevelDev L = T.L[l], C = T.L[l + 1];
+    const int N = L.n;
+    const float* Ab = L.A + (long long)b * N * kPack;
+    float* xb = L.x + (long long)b * N;
+    const float* bb = L.b + (long long)b * N;
+    float* rb = L.r + (long long)b * N;
+    for (int i = tid; i < N; i += nt) xb[i] = 0.0f;
+    __syncthreads();
+    for (int sw = 0; sw < T.smooth; ++sw)
+      for (int colour = 0; colour < 2; ++colour) {
+        for (int i = tid; i < N; i += nt) gs_cell(Ab, xb, bb, L.nx, L.ny, L.nz, colour, i);
+        __syncthreads();
+      }
+    for (int i = tid; i < N; i += nt) rb[i] = residual_cell(Ab, xb, bb, L.nx, L.ny, L.nz, i);
+    __syncthreads();
+    for (int c = tid; c < C.n; c += nt)
+      C.b[(long long)b * C.n + c] = restrict_cell(rb, L.nx, L.ny, L.nz, C.nx, C.ny, c);
+    __syncthreads();
+  }
+  {
+    const LevelDev L = T.L[T.nl - 1];
+    const int N = L.n;
+    float* xb = L.x + (long long)b * N;
+    const float* bb = L.b + (long long)b * N;
+    if (T.inv) {
+      for (int r = tid; r < N; r += nt) xb[r] = dense_row(T.inv + (long long)b * N * N, bb, N, r);
+    } else {
+      const float* Ab = L.A + (long long)b * N * kPack;
+      for (int i = tid; i < N; i += nt) xb[i] = 0.0f;
+      __syncthreads();
+      for (int sw = 0; sw < T.coarsest_sweeps; ++sw)
+        for (int colour = 0; colour < 2; ++colour) {
+          for (int i = tid; i < N; i += nt) gs_cell(Ab, xb, bb, L.nx, L.ny, L.nz, colour, i);
+          __syncthreads();
+        }
+    }
+    __syncthreads();
+  }
+  for (int l = T.nl - 2; l >= T.l0; --l) {
+    const LevelDev L = T.L[l], C = T.L[l + 1];
+    const int N = L.n;
+    const float* Ab = L.A + (long long)b * N * kPack;
+    float* xb = L.x + (long long)b * N;
+    const float* bb = L.b + (long long)b * N;
+    for (int i = tid; i < N; i += nt)
+      xb[i] += prolong_cell(C.x + (long long)b * C.n, C.nx, C.ny, L.nx, L.ny, i);
+    __syncthreads();
+    for (int sw = 0; sw < T.smooth; ++sw)
+      for (int colour = 1; colour >= 0; --colour) {
+        for (int i = tid; i < N; i += nt) gs_cell(Ab, xb, bb, L.nx, L.ny, L.nz, colour, i);
+        __syncthreads();
+      }
+  }
+}
+
+// b0[K] = sum over the Phi nodes of element K of r (P^T r), summed in FP64;
+// one warp per element
 template <class TV>
-__global__ void coarse_from_fine(const TV* __restrict__ r, double* __restrict__ b0, int E, int Np,
+__global__ void coarse_from_fine(const TV* __restrict__ r, float* __restrict__ b0, int E, int Np,
                                  long long bstride) {
   const int b = blockIdx.y;
-  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < E; K += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < E; K += nw) {
     const TV* row = r + b * bstride + (long long)K * Np;
     double s = 0.0;
-    for (int i = 0; i < Np; ++i) s += (double)row[i];
-    b0[(long long)b * E + K] = s;
+    for (int i = lane; i < Np; i += 32) s += (double)row[i];
+    s = warp_sum(s);
+    if (lane == 0) b0[(long long)b * E + K] = (float)s;
   }
 }
 
 // z[Phi nodes of K] += x0[K] (P x0)
 template <class TV>
-__global__ void coarse_to_fine(const double* __restrict__ x0, TV* __restrict__ z, int E, int Np,
+__global__ void coarse_to_fine(const float* __restrict__ x0, TV* __restrict__ z, int E, int Np,
                                long long bstride) {
   const int b = blockIdx.y;
   const long long n = (long long)E * Np;
@@ -515,14 +798,15 @@ __global__ void coarse_to_fine(const double* __restrict__ x0, TV* __restrict__ z
 //       entries of the thread's rows held in registers;
 //   (3) overwrite row k (scaled pivot row) and column k (-A_ik / A_kk), while
 //       warp 0 finds the next pivot in column k+1 (in the matrix's type).
-// A zero or non-finite pivot sets *singular. Row swaps are undone at the end
+// A non-finite pivot, or one not above piv_rtol times the largest |A_ij| (an
+// exact zero when piv_rtol = 0), sets *singular. Row swaps are undone at the end
 // as column swaps in reverse order. The inverse is written transposed
 // (out[e][c][r] = inv[r][c]) in type TS.
 constexpr int kGjRows = 8;  // rows per lane held in registers: n <= 256
 
 template <class T>
 __device__ __forceinline__ void gj_pivot(const T* A, int ld, int n, int col, int lane, int* s_p,
-                                         int* s_bad) {
+                                         int* s_bad, T thr) {
   T best = T(-1);
   int bi = col;
   for (int i = col + lane; i < n; i += 32) {
@@ -535,12 +819,12 @@ __device__ __forceinline__ void gj_pivot(const T* A, int ld, int n, int col, int
     const int oi = __shfl_down_sync(0xffffffffu, bi, o);
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
-  if (lane == 0) { *s_p = bi; *s_bad = (!(best > T(0)) || !isfinite(best)) ? 1 : 0; }
+  if (lane == 0) { *s_p = bi; *s_bad = (!(best > thr) || !isfinite(best)) ? 1 : 0; }
 }
 
 template <class T, class TS, bool SMEM, class TB>
 __global__ void gj_invert(const TB* __restrict__ blocks, T* __restrict__ work, TS* __restrict__ out,
-                          int n, int* __restrict__ singular) {
+                          int n, int* __restrict__ singular, T piv_rtol) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const long long e = blockIdx.x;
   const int ld = n + 1;
@@ -554,10 +838,27 @@ __global__ void gj_invert(const TB* __restrict__ blocks, T* __restrict__ work, T
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const TB* src = blocks + e * (long long)n * n;
+  __shared__ T s_thr;
+  __shared__ T s_wmax[32];
+  T amax = T(0);
   for (int i = warp; i < n; i += nw)
-    for (int j = lane; j < n; j += 32) A[(long long)i * ld + j] = (T)src[(long long)i * n + j];
+    for (int j = lane; j < n; j += 32) {
+      const T a = (T)src[(long long)i * n + j];
+      A[(long long)i * ld + j] = a;
+      amax = fmax(amax, fabs(a));
+    }
+  // pivots at or below piv_rtol * max |A_ij| count as singular (0: exact zero only)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_down_sync(0xffffffffu, amax, o));
+  if (lane == 0) s_wmax[warp] = amax;
   __syncthreads();
-  if (warp == 0) gj_pivot<T>(A, ld, n, 0, lane, &s_p, &s_bad);
+  if (tid == 0) {
+    T mx = T(0);
+    for (int w = 0; w < nw; ++w) mx = fmax(mx, s_wmax[w]);
+    s_thr = piv_rtol > T(0) ? piv_rtol * mx : T(0);
+  }
+  __syncthreads();
+  if (warp == 0) gj_pivot<T>(A, ld, n, 0, lane, &s_p, &s_bad, s_thr);
   __syncthreads();
   const bool regs = n <= 32 * kGjRows;
   for (int k = 0; k < n; ++k) {
@@ -604,7 +905,7 @@ __global__ void gj_invert(const TB* __restrict__ blocks, T* __restrict__ work, T
     for (int j = tid; j < n; j += nt) A[(long long)k * ld + j] = (j == k) ? pinv : prow[j] * pinv;
     for (int i = tid; i < n; i += nt)
       if (i != k) A[(long long)i * ld + k] = -pcol[i] * pinv;
-    if (warp == 0 && k + 1 < n) gj_pivot<T>(A, ld, n, k + 1, lane, &s_p, &s_bad);
+    if (warp == 0 && k + 1 < n) gj_pivot<T>(A, ld, n, k + 1, lane, &s_p, &s_bad, s_thr);
     __syncthreads();
   }
   if (s_bad) {
@@ -707,8 +1008,12 @@ struct SolverState {
   // two-level preconditioner: element-mean potential correction
   bool coarse = false;            // enabled by enp_set_preconditioner
   bool coarse_ready = false;
-  struct Level { int nx, ny, nz, n; double *A, *x, *b, *r; };
+  struct Level { int nx, ny, nz, n; double* A; float *A32, *x, *b, *r; };  // A: FP64 stencil
   std::vector<Level> levels;      // level 0: the element grid
+  bool coarse_direct = false;     // coarsest level solved by its dense inverse
+  double* cdense = nullptr;       // [B][n][n] coarsest matrix
+  float* cinv = nullptr;          // [B][n][n] its inverse, transposed, in FP32
+  size_t cdense_count = 0, cinv_count = 0;
   double* cwork = nullptr;        // Jv scratch for the coarse setup [B][n]
   size_t cwork_count = 0;
 };
@@ -743,17 +1048,101 @@ cudaError_t ensure(P** p, size_t& have, size_t want_count) {
 }
 
 // Batched dot products <V_i, w>_b for i < nd, into dsmall[0 .. batch*nd).
+// Entries per 16-byte load usable on these vectors: every vector start (base
+// pointers and the strides between vectors and operating points) 16-byte aligned.
 template <class T>
-cudaError_t multidot(enp_handle h, const T* V, long long vstride, int nd, const T* w,
-                     double* out) {
+int vec_width(long long n, long long vstride, const void* a, const void* b) {
+  constexpr int W = 16 / sizeof(T);
+  const bool ok = n % W == 0 && vstride % W == 0 &&
+                  reinterpret_cast<uintptr_t>(a) % 16 == 0 && reinterpret_cast<uintptr_t>(b) % 16 == 0;
+  return ok ? W : 1;
+}
+
+// Blocks of a reduction over n entries in units of W: about two units per
+// thread, at most kRedBlocks. Depends on n only (not on the batch), so a point
+// of a batch is reduced exactly as it is alone.
+int red_blocks(long long n, int W) {
+  const long long nu = n / W;
+  const long long g = (nu + 2LL * enp::kRedThreads - 1) / (2LL * enp::kRedThreads);
+  return (int)std::max(1LL, std::min<long long>(g, enp::kRedBlocks));
+}
+
+// Partials of <V_i, w>_b (i < nd) into S.part; *nparts = the partials per dot.
+template <class T>
+cudaError_t dot_partials(enp_handle h, const T* V, long long vstride, int nd, const T* w,
+                         int* nparts) {
   SolverState& S = state_of(h);
   const long long n = h->n_dof;
   const int B = h->batch;
   cudaError_t e = ensure(&S.part, S.part_count, (size_t)B * std::max(nd, 1) * enp::kRedBlocks);
   if (e != cudaSuccess) return e;
-  dim3 g(enp::kRedBlocks, B);
-  enp::multidot_partial<T><<<g, enp::kRedThreads, 0, h->stream>>>(V, vstride, nd, w, n, n, S.part);
-  enp::finish_partials<<<B * nd, 32, 0, h->stream>>>(S.part, enp::kRedBlocks, B * nd, out);
+  const int W = vec_width<T>(n, vstride, V, w);
+  const int nb = red_blocks(n, W);
+  const dim3 g(nb, B);
+  if (W == 1)
+    enp::multidot_partial<T, 1><<<g, enp::kRedThreads, 0, h->stream>>>(V, vstride, nd, w, n, n, S.part);
+  else
+    enp::multidot_partial<T, 16 / sizeof(T)><<<g, enp::kRedThreads, 0, h->stream>>>(V, vstride, nd,
+                                                                                   w, n, n, S.part);
+  *nparts = nb;
+  return cudaGetLastError();
+}
+
+// w -= sum_i V_i h_i (h: device [B][nd]); with part, also the partials of
+// ||w_new||^2 into part (their count per point in *nparts).
+template <class T>
+cudaError_t axpy_many(enp_handle h, const T* V, long long vstride, int nd, const double* hc, T* w,
+                      double* part, int* nparts) {
+  const long long n = h->n_dof;
+  const int B = h->batch;
+  const int W = vec_width<T>(n, vstride, V, w);
+  const int nb = red_blocks(n, W);
+  const dim3 g(nb, B);
+  constexpr int WV = 16 / sizeof(T);
+  if (part) {
+    if (W == 1)
+      enp::multi_axpy<T, 1, true><<<g, enp::kRedThreads, 0, h->stream>>>(V, vstride, nd, hc, w, n, n, part);
+    else
+      enp::multi_axpy<T, WV, true><<<g, enp::kRedThreads, 0, h->stream>>>(V, vstride, nd, hc, w, n, n, part);
+    *nparts = nb;
+  } else {
+    if (W == 1)
+      enp::multi_axpy<T, 1, false><<<g, enp::kRedThreads, 0, h->stream>>>(V, vstride, nd, hc, w, n, n, nullptr);
+    else
+      enp::multi_axpy<T, WV, false><<<g, enp::kRedThreads, 0, h->stream>>>(V, vstride, nd, hc, w, n, n, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t multidot(enp_handle h, const T* V, long long vstride, int nd, const T* w,
+                     double* out) {
+  int np = 0;
+  cudaError_t e = dot_partials<T>(h, V, vstride, nd, w, &np);
+  if (e != cudaSuccess) return e;
+  enp::finish_partials<<<h->batch * nd, 32, 0, h->stream>>>(state_of(h).part, np, h->batch * nd, out);
+  return cudaGetLastError();
+}
+
+// Gram-Schmidt of w against V_0..V_j, twice (classical, CGS2), then ||w||^2
+// and the Givens update of Arnoldi iteration j: seven launches, the partial
+// sums finished inside the kernels that consume them.
+template <class TV>
+cudaError_t arnoldi_orthogonalise(enp_handle h, const enp::KrylovDev& K, TV* V, long long vs,
+                                  int j, TV* w, int m, int* nonfinite) {
+  SolverState& S = state_of(h);
+  const int B = h->batch;
+  const int nd = j + 1;
+  cudaError_t e = cudaSuccess;
+  int np = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    if ((e = dot_partials<TV>(h, V, vs, nd, w, &np)) != cudaSuccess) return e;
+    enp::krylov_hcol_finish<<<B * nd, 32, 0, h->stream>>>(K, S.part, np, B, m, nd, pass == 0);
+    if ((e = axpy_many<TV>(h, V, vs, nd, K.dh, w, pass == 1 ? S.part : nullptr, &np)) !=
+        cudaSuccess)
+      return e;
+  }
+  enp::krylov_norm_givens<<<B, 32, 0, h->stream>>>(K, S.part, np, B, m, j, nonfinite);
   return cudaGetLastError();
 }
 
@@ -777,11 +1166,12 @@ cudaError_t coarse_levels(enp_handle h) {
   int nx = P.ne[0], ny = P.ne[1], nz = P.ne[2];
   const int B = h->batch;
   while (true) {
-    SolverState::Level L{nx, ny, nz, nx * ny * nz, nullptr, nullptr, nullptr, nullptr};
+    SolverState::Level L{nx, ny, nz, nx * ny * nz, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaError_t e = cudaMalloc(&L.A, sizeof(double) * 7 * (size_t)L.n * B);
-    if (e == cudaSuccess) e = cudaMalloc(&L.x, sizeof(double) * (size_t)L.n * B);
-    if (e == cudaSuccess) e = cudaMalloc(&L.b, sizeof(double) * (size_t)L.n * B);
-    if (e == cudaSuccess) e = cudaMalloc(&L.r, sizeof(double) * (size_t)L.n * B);
+    if (e == cudaSuccess) e = cudaMalloc(&L.A32, sizeof(float) * enp::kPack * (size_t)L.n * B);
+    if (e == cudaSuccess) e = cudaMalloc(&L.x, sizeof(float) * (size_t)L.n * B);
+    if (e == cudaSuccess) e = cudaMalloc(&L.b, sizeof(float) * (size_t)L.n * B);
+    if (e == cudaSuccess) e = cudaMalloc(&L.r, sizeof(float) * (size_t)L.n * B);
     S.levels.push_back(L);
     if (e != cudaSuccess) return e;
     if (L.n <= enp::kCoarsestCells) break;
@@ -819,33 +1209,80 @@ cudaError_t coarse_setup(enp_handle h, const double* u) {
     enp::coarse_aggregate<<<dim3(grid_for(C.n), B), 256, 0, h->stream>>>(F.A, F.nx, F.ny, F.nz, C.A,
                                                                          C.nx, C.ny, C.nz);
   }
+  for (const auto& L : S.levels)
+    enp::coarse_pack32<<<grid_for((long long)L.n * B), 256, 0, h->stream>>>(L.A, L.A32,
+                                                                         (long long)L.n * B);
+  // the coarsest level: dense inverse by Gauss-Jordan in FP64 (n <=
+  // kCoarsestCells, in shared memory), stored in FP32, or Gauss-Seidel
+  // smoothing if it is singular
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const auto& Lc = S.levels.back();
+  const size_t nn = (size_t)Lc.n * Lc.n * B;
+  if ((e = ensure(&S.cdense, S.cdense_count, nn)) != cudaSuccess) return e;
+  if ((e = ensure(&S.cinv, S.cinv_count, nn)) != cudaSuccess) return e;
+  enp::coarse_dense<<<B, 256, 0, h->stream>>>(Lc.A, Lc.nx, Lc.ny, Lc.nz, S.cdense);
+  const int nc = Lc.n;
+  const size_t smem = sizeof(double) * ((size_t)nc * (nc + 1) + 2 * nc) + sizeof(int) * nc;
+  auto k = enp::gj_invert<double, float, true, double>;
+  if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  cudaMemsetAsync(S.d_flag, 0, sizeof(int), h->stream);
+  // a pivot below 1e-10 of the largest entry: singular to working accuracy
+  k<<<B, 512, smem, h->stream>>>(S.cdense, nullptr, S.cinv, nc, S.d_flag, 1e-10);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int flag = 0;
+  if ((e = cudaMemcpyAsync(&flag, S.d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    return e;
+  S.coarse_direct = flag == 0;
   S.coarse_ready = true;
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 void vcycle(enp_handle h, size_t l) {
   SolverState& S = state_of(h);
   const int B = h->batch;
   auto& L = S.levels[l];
+  if (L.n <= enp::kTailCells && S.levels.size() <= (size_t)enp::kMaxLevels) {
+    // this level and all below it in one launch
+    enp::VcycleTail T{};
+    T.l0 = (int)l;
+    T.nl = (int)S.levels.size();
+    for (size_t k = 0; k < S.levels.size(); ++k) {
+      const auto& Q = S.levels[k];
+      T.L[k] = enp::LevelDev{Q.nx, Q.ny, Q.nz, Q.n, Q.A32, Q.x, Q.b, Q.r};
+    }
+    T.inv = S.coarse_direct ? S.cinv : nullptr;
+    T.smooth = kSmoothSweeps;
+    T.coarsest_sweeps = kCoarsestSweeps;
+    enp::coarse_vcycle_tail<<<B, enp::kTailThreads, 0, h->stream>>>(T);
+    return;
+  }
   if (l + 1 == S.levels.size()) {
-    enp::coarse_solve_small<<<B, enp::kCoarsestCells, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, kCoarsestSweeps);
+    if (S.coarse_direct)
+      enp::coarse_dense_apply<<<B, enp::kCoarsestCells, 0, h->stream>>>(S.cinv, L.b, L.n, L.x);
+    else
+      enp::coarse_solve_small<<<B, enp::kCoarsestCells, 0, h->stream>>>(L.A32, L.x, L.b, L.nx,
+                                                                      L.ny, L.nz, kCoarsestSweeps);
     return;
   }
   const dim3 g(grid_for(L.n), B);
-  cudaMemsetAsync(L.x, 0, sizeof(double) * (size_t)L.n * B, h->stream);
+  cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)L.n * B, h->stream);
   for (int sw = 0; sw < kSmoothSweeps; ++sw) {
-    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, 0);
-    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, 1);
+    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.nx, L.ny, L.nz, 0);
+    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.nx, L.ny, L.nz, 1);
   }
   auto& C = S.levels[l + 1];
-  enp::coarse_residual<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.r, L.nx, L.ny, L.nz);
+  enp::coarse_residual<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.r, L.nx, L.ny, L.nz);
   enp::coarse_restrict<<<dim3(grid_for(C.n), B), 256, 0, h->stream>>>(L.r, L.nx, L.ny, L.nz, C.b,
                                                                       C.nx, C.ny, C.nz);
   vcycle(h, l + 1);
   enp::coarse_prolong<<<g, 256, 0, h->stream>>>(C.x, C.nx, C.ny, C.nz, L.x, L.nx, L.ny, L.nz);
   for (int sw = 0; sw < kSmoothSweeps; ++sw) {
-    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, 1);
-    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A, L.x, L.b, L.nx, L.ny, L.nz, 0);
+    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.nx, L.ny, L.nz, 1);
+    enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.nx, L.ny, L.nz, 0);
   }
 }
 
@@ -856,8 +1293,8 @@ cudaError_t coarse_apply(enp_handle h, const TV* r, TV* z) {
   const OpParams& P = h->prm;
   const int B = h->batch;
   auto& L0 = S.levels[0];
-  enp::coarse_from_fine<TV><<<dim3(grid_for(P.E), B), 256, 0, h->stream>>>(r, L0.b, P.E, P.Np,
-                                                                          P.batch_stride);
+  enp::coarse_from_fine<TV><<<dim3(grid_for(32LL * P.E), B), 256, 0, h->stream>>>(r, L0.b, P.E, P.Np,
+                                                                               P.batch_stride);
   vcycle(h, 0);
   enp::coarse_to_fine<TV><<<dim3(grid_for((long long)P.E * P.Np), B), 256, 0, h->stream>>>(
       L0.x, z, P.E, P.Np, P.batch_stride);
@@ -872,8 +1309,10 @@ void enp_solver_free(enp_handle h) {
   cudaFree(S.blocks); cudaFree(S.binv); cudaFree(S.gj_work); cudaFree(S.d_flag);
   cudaFree(S.blocks32); cudaFree(S.u32);
   cudaFree(S.part); cudaFree(S.dsmall); cudaFree(S.V); cudaFree(S.dRdtheta);
-  for (auto& L : S.levels) { cudaFree(L.A); cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); }
-  cudaFree(S.cwork);
+  for (auto& L : S.levels) {
+    cudaFree(L.A); cudaFree(L.A32); cudaFree(L.x); cudaFree(L.b); cudaFree(L.r);
+  }
+  cudaFree(S.cwork); cudaFree(S.cdense); cudaFree(S.cinv);
   if (S.gexec) cudaGraphExecDestroy(S.gexec);
   if (S.gstream) cudaStreamDestroy(S.gstream);
   cudaFree(S.gbuf);
@@ -984,7 +1423,7 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
     if (e == cudaSuccess) {                                                                     \
       k<<<(unsigned)nblk, threads, smem, h->stream>>>(SRC, (T*)S.gj_work, (TS*)S.binv, nb,      \
-                                                      S.d_flag);                                \
+                                                      S.d_flag, T(0));                          \
       e = cudaGetLastError();                                                                   \
     }                                                                                           \
   }
@@ -1189,13 +1628,8 @@ static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
       else e = cudaMemcpyAsync(zj, vj, vbytes, cudaMemcpyDeviceToDevice, h->stream);
       if (e != cudaSuccess) return cuda_err(h, e, "fgmres precondition");
       if ((e = apply_A(zj, w)) != cudaSuccess) return cuda_err(h, e, "fgmres A z");
-      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-        if ((e = multidot<TV>(h, V, vs, j + 1, w, K.dh)) != cudaSuccess) return cuda_err(h, e, "fgmres dots");
-        enp::krylov_hcol_add<<<(B * (j + 1) + 127) / 128, 128, 0, h->stream>>>(K, B, m, j + 1, pass == 0);
-        enp::multi_axpy<TV><<<gv, 256, 0, h->stream>>>(V, vs, j + 1, K.dh, w, n, n);
-      }
-      if ((e = multidot<TV>(h, w, 0, 1, w, K.hn2)) != cudaSuccess) return cuda_err(h, e, "fgmres norm w");
-      enp::krylov_givens<<<gbk, tb, 0, h->stream>>>(K, B, m, j, dflag + 1);
+      if ((e = arnoldi_orthogonalise<TV>(h, K, V, vs, j, w, m, dflag + 1)) != cudaSuccess)
+        return cuda_err(h, e, "fgmres orthogonalisation");
       enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(w, K.inv, 0.0, w, n, n);
       ++total_it;
       if ((j + 1) % kCheckEvery == 0 || j + 1 == m || total_it >= o->max_it) {
@@ -1355,13 +1789,7 @@ static enp_status fgmres_graph(enp_handle h, const TV* ulin, const TV* b, TV* x,
       if (precond) bj_apply_any<TV>(h, vj, zj);
       else cudaMemcpyAsync(zj, vj, vbytes, cudaMemcpyDeviceToDevice, h->stream);
       apply_A(zj, w);
-      for (int pass = 0; pass < 2; ++pass) {
-        multidot<TV>(h, V, vs, j + 1, w, K.dh);
-        enp::krylov_hcol_add<<<(B * (j + 1) + 127) / 128, 128, 0, h->stream>>>(K, B, m, j + 1, pass == 0);
-        enp::multi_axpy<TV><<<gv, 256, 0, h->stream>>>(V, vs, j + 1, K.dh, w, n, n);
-      }
-      multidot<TV>(h, w, 0, 1, w, K.hn2);
-      enp::krylov_givens<<<gbk, tb, 0, h->stream>>>(K, B, m, j, dflag + 1);
+      arnoldi_orthogonalise<TV>(h, K, V, vs, j, w, m, dflag + 1);
       enp::scale_copy<TV, TV><<<gv, 256, 0, h->stream>>>(w, K.inv, 0.0, w, n, n);
     }
     enp::krylov_solve_upper<<<gbk, tb, 0, h->stream>>>(K, B, m, m);
