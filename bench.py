@@ -48,21 +48,35 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
-# the hash of the operator source it was taken from (stale -> reported null).
+# DRAM traffic per launch of a kernel from one ncu capture, keyed by the hash
+# of the sources that kernel is built from (stale -> reported null): the
+# operator kernels from the operator headers, the block apply from the solver.
 TRAFFIC = {
-    ("5b4d5098ed56", "jvp_f64", "channel64_p3"): 134.67e6,
-    ("5b4d5098ed56", "jvp_f32", "channel64_p3"): 57.11e6,
+    ("907f08e606c1", "jvp_f64", "channel64_p3"): 134.67e6,
+    ("907f08e606c1", "jvp_f32", "channel64_p3"): 57.11e6,
     ("5b4d5098ed56", "bj_apply_f32", "channel64_p3"): 4935.10e6,
 }
 
+KERNEL_SOURCES = {
+    "operator": ("enp_operator.cuh", "enp_operator3d.cuh", "enp_common.cuh"),
+    "solver": ("enp_solver.cu",),
+}
 
-def _kernel_hash():
+
+def _kernel_hash(kind=None):
+    """Hash of the sources of one kernel family ('operator' or 'solver'), or of
+    both (None)."""
+    files = (KERNEL_SOURCES[kind] if kind else
+             KERNEL_SOURCES["operator"] + KERNEL_SOURCES["solver"])
     h = hashlib.sha1()
-    for f in ("enp_operator.cuh", "enp_operator3d.cuh", "enp_common.cuh", "enp_solver.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2112_09271_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def _family(op_name):
+    return "solver" if op_name.startswith("bj_") else "operator"
 
 
 def contraction_flops(dim, p, nf, mode):
@@ -196,6 +210,7 @@ def run_solves(enp, W, name):
     import torch
     prob = W.config(name)
     op = enp.Operator(prob)
+    op.autotune()
     u0 = np.zeros((prob.n_fields, prob.E, prob.Np))
     for k in range(1, prob.n_fields):
         u0[k] = prob.c_in[k - 1]
@@ -273,6 +288,7 @@ def run_fgmres_profile(enp, W, args):
     import torch
     prob = W.config(args.solve_workload)
     op = enp.Operator(prob)
+    op.autotune()
     op.set_preconditioner(1)
     f32 = args.only == "fgmres_f32"
     u = torch.tensor(W.random_state(prob, 2), device="cuda")
@@ -455,7 +471,8 @@ def main():
                    "GDOF_s": n / (t_ops[nm] / args.steps * 1e-3) / 1e9} for nm in ops}
     if args.only:
         if rank == 0:
-            print(json.dumps({"only": args.only, "ops": per_op, "kernel_hash": _kernel_hash()}),
+            print(json.dumps({"only": args.only, "ops": per_op,
+                              "kernel_hash": _kernel_hash(_family(args.only))}),
                   flush=True)
         if dist:
             dist.barrier()
@@ -471,7 +488,7 @@ def main():
     achieved = fl / dom_s / 1e12
     hbm, hbm_kind = read_peaks()
     hbm_bytes = algorithmic_bytes_per_dof(mode, 8) * n
-    kh = _kernel_hash()
+    kh = _kernel_hash("operator")
     traffic = TRAFFIC.get((kh, dom, prob.name))
     roof = {"bound": "alu", "kernel": f"op_kernel<{prob.dim}D,p={prob.p},NF={prob.n_fields},"
                                       f"{mode},double>",
@@ -489,7 +506,7 @@ def main():
                 "achieved": bj_bytes / bj_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": bj_bytes / bj_s / 1e9 / hbm, "peak_kind": hbm_kind,
                 "bytes_per_launch": bj_bytes,
-                "traffic": TRAFFIC.get((kh, "bj_apply_f32", prob.name))}
+                "traffic": TRAFFIC.get((_kernel_hash("solver"), "bj_apply_f32", prob.name))}
     f32_fl = contraction_flops(prob.dim, prob.p, prob.n_fields, "jvp") * prob.E
     f32_s = t_ops["jvp_f32"] / args.steps * 1e-3
     per_op["jvp_f32"]["fp32_TFLOPs"] = f32_fl / f32_s / 1e12

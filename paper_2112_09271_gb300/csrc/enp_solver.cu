@@ -335,46 +335,47 @@ __global__ void krylov_hcol_finish(KrylovDev K, const double* __restrict__ part,
   }
 }
 
-__device__ void givens_step(KrylovDev K, int b, int m, int j, int* nonfinite);
-
-// Iteration j of Arnoldi with Givens rotations, one warp per running point,
-// with ||w||^2 first summed from its partials in block order.
+// Iteration j of Arnoldi with Givens rotations, one warp per running point:
+// ||w||^2 summed from its partials in block order; the new Hessenberg column
+// and the earlier rotations staged in shared memory by the warp, then rotated
+// by lane 0 with the running entry in a register.
 __global__ void krylov_norm_givens(KrylovDev K, const double* __restrict__ part, int nparts, int B,
                                    int m, int j, int* nonfinite) {
+  __shared__ double s_h[256], s_cs[256], s_sn[256];  // m <= 255
   const int b = blockIdx.x;
   if (b >= B) return;
+  const int lane = threadIdx.x;
   double s = 0.0;
-  for (int k = threadIdx.x; k < nparts; k += 32) s += part[(long long)b * nparts + k];
+  for (int k = lane; k < nparts; k += 32) s += part[(long long)b * nparts + k];
   s = warp_sum(s);
-  if (threadIdx.x == 0) {
-    K.hn2[b] = s;
-    givens_step(K, b, m, j, nonfinite);
-  }
-}
-
-__device__ void givens_step(KrylovDev K, int b, int m, int j, int* nonfinite) {
-  const double hn = sqrt(K.hn2[b]);
+  const double* hc = K.hcol + (long long)b * (m + 1);
+  double* cs = K.cs + (long long)b * m;
+  double* sn = K.sn + (long long)b * m;
+  for (int r = lane; r <= j; r += 32) s_h[r] = hc[r];
+  for (int r = lane; r < j; r += 32) { s_cs[r] = cs[r]; s_sn[r] = sn[r]; }
+  __syncwarp();
+  if (lane != 0) return;
+  K.hn2[b] = s;
+  const double hn = sqrt(s);
   if (K.jconv[b] != -1) { K.inv[b] = 0.0; return; }
   double* H = K.H + (long long)b * (m + 1) * m;
   double* g = K.g + (long long)b * (m + 1);
-  double* cs = K.cs + (long long)b * m;
-  double* sn = K.sn + (long long)b * m;
-  const double* hc = K.hcol + (long long)b * (m + 1);
-  for (int r = 0; r <= j; ++r) H[(long long)r * m + j] = hc[r];
-  H[(long long)(j + 1) * m + j] = hn;
+  double a = s_h[0];  // entry r of the column, already rotated by rotations < r
   for (int r = 0; r < j; ++r) {
-    const double a = H[(long long)r * m + j], c = H[(long long)(r + 1) * m + j];
-    H[(long long)r * m + j] = cs[r] * a + sn[r] * c;
-    H[(long long)(r + 1) * m + j] = -sn[r] * a + cs[r] * c;
+    const double c = s_h[r + 1], cr = s_cs[r], sr = s_sn[r];
+    H[(long long)r * m + j] = cr * a + sr * c;
+    a = -sr * a + cr * c;
   }
-  const double a = H[(long long)j * m + j], c = H[(long long)(j + 1) * m + j];
+  const double c = hn;
   const double rr = hypot(a, c);
-  cs[j] = rr > 0 ? a / rr : 1.0;
-  sn[j] = rr > 0 ? c / rr : 0.0;
+  const double cj = rr > 0 ? a / rr : 1.0, sj = rr > 0 ? c / rr : 0.0;
+  cs[j] = cj;
+  sn[j] = sj;
   H[(long long)j * m + j] = rr;
   H[(long long)(j + 1) * m + j] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
+  const double gj = g[j];
+  g[j + 1] = -sj * gj;
+  g[j] = cj * gj;
   const double res = fabs(g[j + 1]);
   K.resn[b] = res;
   if (!isfinite(res)) atomicOr(nonfinite, 1);
