@@ -11,9 +11,10 @@ block apply) per second, in GDOF/s, summed over ranks. Each step is timed with
 CUDA events on the launching stream; between steps a 512 MB buffer is written
 to flush the 129 MB L2 (outside the events). The block-Jacobi setup, FGMRES and
 Newton rows run in a full solve of the cube16_p3 workload after the timed
-steps, FP64 and mixed precision, reported under `solve`; the batched
-operating-point sweep of the plate reactor (graph-captured Krylov cycles) is
-reported under `batched_solve`.
+steps, FP64 and mixed precision, with block-Jacobi and with the two-level
+preconditioner, reported under `solve`; the batched operating-point sweep of
+the plate reactor at 0.1-0.8 V (continuation in the applied potential,
+graph-captured Krylov cycles) is reported under `batched_solve`.
 
 Extra keys: per-operator throughput (`ops`), the roofline of the dominant kernel
 (`roofline`), the CPU oracle on a bounded sample (`cpu_baseline`), the same
@@ -243,40 +244,53 @@ def run_solves(enp, W, name):
     return out
 
 
-def run_batched_solve(enp, W, name, batch=8, volts=(0.01, 0.08)):
+def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8), labels=("fp64", "mixed")):
     """The operating-point sweep of the plate reactor (Sec. 5.2): `batch`
-    applied cathode potentials (anode at 0), all solved in one batched Newton
-    run whose FGMRES restart cycles replay a captured CUDA graph. FP64 and
-    mixed (FP32 inner operator, FP32 block inverses), initial guess c = c_in,
-    Phi = phi_app / 2."""
+    applied cathode potentials from volts[0] to volts[1] (anode at 0), all
+    solved in one batched Newton run per stage, with continuation in the
+    applied potential (Butler-Volmer exponents reach e^31 at 0.8 V, beyond the
+    reach of Newton from a plain guess), the two-level preconditioner and FGMRES
+    restart cycles replayed from a captured CUDA graph. FP64 and mixed (FP32
+    inner operator, FP32 block inverses); initial guess c = c_in,
+    Phi = phi_app / 2 at the first stage; the last stage to 1e-10 relative."""
     import torch
     prob = W.config(name)
     phis = 38.92 * np.linspace(volts[0], volts[1], batch)  # F/RT at 298.15 K
+    target = np.array([[ph, 0.0, 0.0, 0.0] for ph in phis])
     op = enp.Operator(prob, batch=batch)
     op.autotune()
-    op.set_phi_app(np.array([[ph, 0.0, 0.0, 0.0] for ph in phis]))
-    u0 = W.reactor_initial_state(prob, phis)
+    op.set_preconditioner(1)
+    step0 = 0.125
+    u0 = W.reactor_initial_state(prob, phis * step0)
     out = {"workload": name, "batch": batch, "volts": list(volts), "n_dof_per_point": prob.n_dof,
-           "rtol": 1e-10}
-    f64 = dict(bj_storage=enp.BJ_F64, mixed=False)
-    mix = dict(bj_storage=enp.BJ_F32, mixed=True)
-    for label, two, kw in (("fp64_graph", 0, f64), ("mixed_graph", 0, mix),
-                           ("fp64_graph_two_level", 1, f64), ("mixed_graph_two_level", 1, mix)):
-        op.set_preconditioner(two)
+           "rtol_last_stage": 1e-10, "continuation": "lambda from 0.125, x1.5 after a converged "
+           "stage (max 0.25), /2 after a failed one; intermediate stages to 1e-6 in 10 iterations"}
+    sols = {}
+    kws = {"fp64": dict(bj_storage=enp.BJ_F64, mixed=False),
+           "mixed": dict(bj_storage=enp.BJ_F32, mixed=True)}
+    for label in labels:
         u = torch.tensor(u0, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = op.newton_solve(u, max_it=30, rtol=1e-10, krylov_restart=50, krylov_max_it=4000,
-                             krylov_rtol=1e-3, raise_on_fail=False, graph=True, **kw)
+        st = op.newton_continuation(u, target, step0=step0, graph=True, raise_on_fail=False,
+                                    **kws[label])
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        sols[label] = u.cpu().numpy()
+        last = st["last"]
         out[label] = {"seconds": dt, "points_per_second": batch / dt,
-                      "newton_iterations": st["iterations"],
+                      "reached_lambda": st["lambda"], "stages": st["stages"],
+                      "failed_stages": st["failed_stages"],
+                      "newton_iterations": st["newton_iterations"],
                       "krylov_iterations": st["krylov_iterations"],
-                      "setup_seconds": st["setup_seconds"],
-                      "krylov_seconds": st["krylov_seconds"],
-                      "converged": bool(st["converged"]),
-                      "final_relative_residual": st["residual_norm"] / st["initial_norm"]}
+                      "converged": st["status"] == 0,
+                      "last_stage_relative_residual": last["residual_norm"] / last["initial_norm"],
+                      "last_stage_residual_norm": last["residual_norm"]}
+    if "fp64" in sols and "mixed" in sols:
+        ref = sols["fp64"]
+        out["mixed_vs_fp64_relative_error"] = float(
+            np.linalg.norm(sols["mixed"] - ref) / np.linalg.norm(ref))
+        out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     return out
 
 
@@ -349,6 +363,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--solve-workload", default="cube16_p3")
+    ap.add_argument("--reactor-workload", default="reactor_n2_p2",
+                    help="workload of the batched 0.1-0.8 V sweep (reactor192_p2: the full "
+                         "plate reactor, mixed precision only, about 13 minutes)")
     ap.add_argument("--only", default=None,
                     help="time one operator alone (for profiling): residual_f64, jvp_f64, "
                          "vjp_f64, jvp_f32, bj_apply_f32; no autotune, solves or e2e; or "
@@ -550,7 +567,9 @@ def main():
     solve = batched = None
     if rank == 0 and not args.no_solve:
         solve = run_solves(enp, W, args.solve_workload)
-        batched = run_batched_solve(enp, W, "reactor_n2_p2")
+        full = args.reactor_workload.startswith("reactor192")
+        batched = run_batched_solve(enp, W, args.reactor_workload,
+                                    labels=("mixed",) if full else ("fp64", "mixed"))
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(prob)

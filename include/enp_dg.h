@@ -192,14 +192,26 @@ enp_status enp_block_jacobi_apply(enp_handle h, const double* x, double* y);
  * element; A0 = P^T J_PhiPhi(u) P, a 7-point stencil on the element grid, is
  * assembled exactly from 7 coloured J v products at setup, and V is one
  * multigrid V-cycle on it (2 x 2 x 2 Galerkin aggregation, red-black
- * Gauss-Seidel, 2 + 2 sweeps per level; the coarsest grid, of at most 128
+ * Gauss-Seidel, 2 + 2 sweeps per level, prolongation over-corrected by 1.8; the coarsest grid, of at most 128
  * cells, solved with its dense inverse, or by 100 sweeps if it is singular to
  * working accuracy; the levels of at most 8192 cells run in one launch). A0 is
- * assembled in FP64; the V-cycle runs in FP32 (it only preconditions). The Schur-complement-like stiffness of the potential
+ * assembled with the FP64 operator when the block inverses are stored in FP64,
+ * else with the FP32 one; the V-cycle runs in FP32 (it only preconditions). The Schur-complement-like stiffness of the potential
  * equation (Sec. 3.3) is what block-Jacobi alone cannot reduce.
  * Takes effect at the next setup. Errors: INVALID_ARG (two_level not 0 or 1),
  * UNSUPPORTED (two_level = 1 on a 2D mesh). */
 enp_status enp_set_preconditioner(enp_handle h, int two_level);
+
+/* Options of the coarse solve of the two-level preconditioner (defaults 1, 2,
+ * 1.8): `cycles` V-cycles per application (1..8; each further cycle solves
+ * for the correction of the level-0 residual), `smooth` red-black Gauss-Seidel
+ * sweeps before and after each coarse step (1..8), and `omega` (0 < omega <= 3)
+ * multiplying every prolongated coarse correction. Piecewise-constant
+ * aggregation makes each Galerkin level about twice as stiff as the
+ * operator it approximates, so the plain correction comes out too small:
+ * omega near 2 compensates (on the plate reactor, 1.8 cut the FGMRES
+ * iterations by a quarter at 147k elements). Errors: INVALID_ARG. */
+enp_status enp_set_coarse_options(enp_handle h, int cycles, int smooth, double omega);
 
 /* a0: device [batch][E][7] = the level-0 coarse operator of the last setup,
  * entries (self, -x, +x, -y, +y, -z, +z) of each element's row of
@@ -273,6 +285,40 @@ typedef struct {
  * Errors: NOT_CONVERGED, NONFINITE, OOM, CUDA. */
 enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* opts,
                             enp_newton_stats* stats);
+
+/* Continuation in the applied potential for operating points that Newton
+ * cannot reach from a plain initial guess (strongly driven Butler-Volmer
+ * electrodes, Eq. bv, Sec. 5.2): solves R(u; lambda Phi_app) = 0 for a rising
+ * sequence of lambda ending at 1, each stage by enp_newton_solve from the
+ * previous stage's solution. The increment starts at step0, is multiplied by
+ * grow after a converged stage (up to step_max), and is halved after a failed
+ * one, whose iterate is discarded. Stages with lambda < 1 stop at stage_rtol
+ * within stage_max_it iterations; the last stage uses opts as given. */
+typedef struct {
+  double step0, step_max, step_min;  /* increments of lambda, 0 < step_min <= step0 <= step_max <= 1 */
+  double grow;                       /* >= 1 */
+  double stage_rtol;                 /* Newton tolerance of the stages with lambda < 1 */
+  int stage_max_it;                  /* Newton iterations of those stages */
+} enp_continuation_opts;
+
+typedef struct {
+  int stages;             /* Newton solves run, converged or not */
+  int failed_stages;
+  int newton_iterations;  /* over all stages */
+  int krylov_iterations;
+  double lambda;          /* the last converged lambda (1 on success) */
+  enp_newton_stats last;  /* the last stage run */
+} enp_continuation_stats;
+
+/* u: device [batch][m][E][Np], on entry the initial guess for the first stage
+ * (lambda = step0), on return the solution at the last converged lambda.
+ * phi_app: host [batch][4], the target potentials; on return the handle's
+ * applied potentials are the target ones. stats: host pointer (may be NULL).
+ * Synchronises. Errors: NOT_CONVERGED (the increment fell below step_min),
+ * INVALID_ARG, NONFINITE, OOM, CUDA. */
+enp_status enp_newton_continuation(enp_handle h, double* u, const double* phi_app,
+                                   const enp_continuation_opts* copts,
+                                   const enp_newton_opts* opts, enp_continuation_stats* stats);
 
 /* Choose the launch shape of the hexahedral operator kernel for this handle's
  * degree and field count: for each of R (FP64), J v (FP64), J^T w (FP64),

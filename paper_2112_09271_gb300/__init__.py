@@ -128,6 +128,18 @@ class NewtonStats(ctypes.Structure):
                 ("krylov_seconds", ctypes.c_double)]
 
 
+class ContinuationOpts(ctypes.Structure):
+    _fields_ = [("step0", ctypes.c_double), ("step_max", ctypes.c_double),
+                ("step_min", ctypes.c_double), ("grow", ctypes.c_double),
+                ("stage_rtol", ctypes.c_double), ("stage_max_it", ctypes.c_int)]
+
+
+class ContinuationStats(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_int), ("failed_stages", ctypes.c_int),
+                ("newton_iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
+                ("lambda_", ctypes.c_double), ("last", NewtonStats)]
+
+
 BJ_F64, BJ_F32, BJ_BF16 = 0, 1, 2
 
 _lib = None
@@ -154,10 +166,12 @@ _PROTOS = [
     ("enp_block_jacobi_setup", _I, [_V, _V, _I]),
     ("enp_block_jacobi_apply", _I, [_V, _V, _V]),
     ("enp_set_preconditioner", _I, [_V, _I]),
+    ("enp_set_coarse_options", _I, [_V, _I, _I, ctypes.c_double]),
     ("enp_coarse_operator", _I, [_V, _V]),
     ("enp_fgmres_solve", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_fgmres_solve_f32", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_newton_solve", _I, [_V, _V, _V, _V]),
+    ("enp_newton_continuation", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_autotune", _I, [_V, _V]),
     ("enp_param_count", _I, [_V, ctypes.POINTER(_I)]),
     ("enp_param_jacobian", _I, [_V, _V, _V]),
@@ -365,6 +379,11 @@ class Operator:
         (takes effect at the next block_jacobi_setup)."""
         self._check(self._lib.enp_set_preconditioner(self.h, int(two_level)))
 
+    def set_coarse_options(self, cycles=1, smooth=2, omega=1.0):
+        """V-cycles per application, smoothing sweeps, prolongation over-correction."""
+        self._check(self._lib.enp_set_coarse_options(self.h, int(cycles), int(smooth),
+                                                     float(omega)))
+
     def coarse_operator(self):
         """The level-0 coarse operator [batch][E][7] of the last two-level setup."""
         import torch
@@ -403,6 +422,34 @@ class Operator:
             self._check(rc)
         out = {k: getattr(st, k) for k, _ in NewtonStats._fields_ if k != "history"}
         out["history"] = list(st.history[: st.iterations + 1])
+        out["status"] = rc
+        return out
+
+    def newton_continuation(self, u, phi_app, step0=0.125, step_max=0.25, step_min=1.0 / 512,
+                            grow=1.5, stage_rtol=1e-6, stage_max_it=10, max_it=30, rtol=1e-10,
+                            atol=0.0, armijo_c=1e-4, max_backtracks=12, bj_storage=BJ_F64,
+                            mixed=False, krylov_restart=50, krylov_max_it=4000,
+                            krylov_rtol=1e-3, graph=False, pc_lag=1, raise_on_fail=True):
+        """Continuation in the applied potential up to phi_app ([batch][4]), in
+        place on u; returns the stats (the last stage's Newton stats under 'last')."""
+        import numpy as np
+        import torch
+        ph = np.ascontiguousarray(np.asarray(phi_app, dtype=np.float64).reshape(self.batch, 4))
+        c = ContinuationOpts(step0, step_max, step_min, grow, stage_rtol, stage_max_it)
+        o = NewtonOpts(max_it, rtol, atol, armijo_c, max_backtracks, bj_storage, int(mixed),
+                       KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0, int(graph)),
+                       int(pc_lag))
+        st = ContinuationStats()
+        rc = self._lib.enp_newton_continuation(
+            self.h, _dptr(u, torch.float64), ph.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(c), ctypes.byref(o), ctypes.byref(st))
+        if rc != ENP_OK and raise_on_fail:
+            self._check(rc)
+        out = {k: getattr(st, k) for k, _ in ContinuationStats._fields_ if k not in ("last", "lambda_")}
+        out["lambda"] = st.lambda_
+        last = {k: getattr(st.last, k) for k, _ in NewtonStats._fields_ if k != "history"}
+        last["history"] = list(st.last.history[: st.last.iterations + 1])
+        out["last"] = last
         out["status"] = rc
         return out
 

@@ -425,7 +425,8 @@ __device__ __forceinline__ int cell_colour(int ix, int iy, int iz) {
 }
 
 // v = indicator of the Phi field on the elements of colour c (other fields 0).
-__global__ void coarse_colour_vector(double* __restrict__ v, int nx, int ny, int nz, int Np,
+template <class T>
+__global__ void coarse_colour_vector(T* __restrict__ v, int nx, int ny, int nz, int Np,
                                      long long bstride, int E, int colour) {
   const int b = blockIdx.y;
   const long long n = (long long)E * Np;
@@ -433,13 +434,14 @@ __global__ void coarse_colour_vector(double* __restrict__ v, int nx, int ny, int
        t += (long long)gridDim.x * blockDim.x) {
     const int e = (int)(t / Np);
     const int ix = e % nx, iy = (e / nx) % ny, iz = e / (nx * ny);
-    v[b * bstride + t] = (cell_colour(ix, iy, iz) == colour) ? 1.0 : 0.0;
+    v[b * bstride + t] = (cell_colour(ix, iy, iz) == colour) ? T(1) : T(0);
   }
 }
 
 // Sum of the Phi rows of element K of J v, filed under the direction of the
 // colour-c element in K's stencil (if that element exists).
-__global__ void coarse_gather(const double* __restrict__ jv, double* __restrict__ A, int nx, int ny,
+template <class T>
+__global__ void coarse_gather(const T* __restrict__ jv, double* __restrict__ A, int nx, int ny,
                               int nz, int Np, long long bstride, int colour) {
   const int b = blockIdx.y;
   const int E = nx * ny * nz;
@@ -458,9 +460,9 @@ __global__ void coarse_gather(const double* __restrict__ jv, double* __restrict_
       case 3: dir = iz < nz - 1 ? 6 : -1; break;
     }
     if (dir < 0) continue;
-    const double* row = jv + b * bstride + (long long)K * Np;  // field 0 block starts at 0
+    const T* row = jv + b * bstride + (long long)K * Np;  // field 0 block starts at 0
     double s = 0.0;
-    for (int i = 0; i < Np; ++i) s += row[i];
+    for (int i = 0; i < Np; ++i) s += (double)row[i];
     A[((long long)b * E + K) * 7 + dir] = s;
   }
 }
@@ -598,13 +600,13 @@ __global__ void coarse_restrict(const float* __restrict__ rf, int fx, int fy, in
     bc[(long long)b * Nc + C] = restrict_cell(rf + (long long)b * Nf, fx, fy, fz, cx, cy, C);
 }
 
-// x_f += x_c on every fine cell of the aggregate
+// x_f += omega x_c on every fine cell of the aggregate
 __global__ void coarse_prolong(const float* __restrict__ xc, int cx, int cy, int cz,
-                               float* __restrict__ xf, int fx, int fy, int fz) {
+                               float* __restrict__ xf, int fx, int fy, int fz, float omega) {
   const int b = blockIdx.y;
   const int Nc = cx * cy * cz, Nf = fx * fy * fz;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Nf; i += gridDim.x * blockDim.x)
-    xf[(long long)b * Nf + i] += prolong_cell(xc + (long long)b * Nc, cx, cy, fx, fy, i);
+    xf[(long long)b * Nf + i] += omega * prolong_cell(xc + (long long)b * Nc, cx, cy, fx, fy, i);
 }
 
 // The coarsest level (at most kCoarsestCells cells) is solved with its dense
@@ -698,6 +700,7 @@ struct VcycleTail {
   LevelDev L[kMaxLevels];
   const float* inv;  // coarsest inverse, transposed, [B][n][n]; null: smoothing
   int smooth, coarsest_sweeps;
+  float omega;       // over-correction of the prolongated coarse values
 };
 
 __global__ void __launch_bounds__(kTailThreads) coarse_vcycle_tail(const VcycleTail T) {
@@ -749,7 +752,7 @@ __global__ void __launch_bounds__(kTailThreads) coarse_vcycle_tail(const VcycleT
     float* xb = L.x + (long long)b * N;
     const float* bb = L.b + (long long)b * N;
     for (int i = tid; i < N; i += nt)
-      xb[i] += prolong_cell(C.x + (long long)b * C.n, C.nx, C.ny, L.nx, L.ny, i);
+      xb[i] += T.omega * prolong_cell(C.x + (long long)b * C.n, C.nx, C.ny, L.nx, L.ny, i);
     __syncthreads();
     for (int sw = 0; sw < T.smooth; ++sw)
       for (int colour = 1; colour >= 0; --colour) {
@@ -774,6 +777,13 @@ __global__ void coarse_from_fine(const TV* __restrict__ r, float* __restrict__ b
     s = warp_sum(s);
     if (lane == 0) b0[(long long)b * E + K] = (float)s;
   }
+}
+
+// acc += x
+__global__ void axpy_f32(const float* __restrict__ x, float* __restrict__ acc, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    acc[t] += x[t];
 }
 
 // z[Phi nodes of K] += x0[K] (P x0)
@@ -1008,6 +1018,12 @@ struct SolverState {
   int gkey_i[4] = {0, 0, 0, 0};
   // two-level preconditioner: element-mean potential correction
   bool coarse = false;            // enabled by enp_set_preconditioner
+  int coarse_cycles = 1;          // V-cycles per application (enp_set_coarse_options)
+  int coarse_smooth = 2;          // Gauss-Seidel sweeps before and after the coarse step
+  float coarse_omega = 1.8f;      // prolongation over-correction
+  float* cx_acc = nullptr;        // [B][n0] accumulated level-0 solution (cycles > 1)
+  float* cb_keep = nullptr;       // [B][n0] level-0 right-hand side (cycles > 1)
+  size_t cx_acc_count = 0, cb_keep_count = 0;
   bool coarse_ready = false;
   struct Level { int nx, ny, nz, n; double* A; float *A32, *x, *b, *r; };  // A: FP64 stencil
   std::vector<Level> levels;      // level 0: the element grid
@@ -1158,7 +1174,6 @@ cudaError_t small(enp_handle h, size_t count) {
 namespace {
 
 constexpr int kCoarsestSweeps = 100;
-constexpr int kSmoothSweeps = 2;
 
 cudaError_t coarse_levels(enp_handle h) {
   SolverState& S = state_of(h);
@@ -1190,20 +1205,31 @@ cudaError_t coarse_setup(enp_handle h, const double* u) {
   if (e != cudaSuccess) return e;
   const long long ntot = h->n_dof * B;
   if ((e = ensure(&S.cwork, S.cwork_count, (size_t)2 * ntot)) != cudaSuccess) return e;
-  double* v = S.cwork;
-  double* jv = S.cwork + ntot;
   SolverState::Level& L0 = S.levels[0];
   cudaMemsetAsync(L0.A, 0, sizeof(double) * 7 * (size_t)L0.n * B, h->stream);
-  cudaMemsetAsync(v, 0, sizeof(double) * ntot, h->stream);
-  const int gx = grid_for((long long)P.E * P.Np);
-  for (int c = 0; c < 7; ++c) {
-    enp::coarse_colour_vector<<<dim3(gx, B), 256, 0, h->stream>>>(v, P.ne[0], P.ne[1], P.ne[2], P.Np,
-                                                                   P.batch_stride, P.E, c);
-    e = enp::launch_op<double>(enp::kJvp, P, h->d_tab, u, v, jv, B, h->stream);
-    if (e != cudaSuccess) return e;
-    enp::coarse_gather<<<dim3(grid_for(P.E), B), 256, 0, h->stream>>>(jv, L0.A, P.ne[0], P.ne[1],
-                                                                      P.ne[2], P.Np, P.batch_stride, c);
+  // seven J v products with the FP64 operator, or with the FP32 one when the
+  // block inverses are stored in single or half precision (mixed solves)
+  auto probe = [&](auto* uu, auto* v, auto* jv) -> cudaError_t {
+    using T = std::remove_pointer_t<decltype(v)>;
+    cudaMemsetAsync(v, 0, sizeof(T) * ntot, h->stream);
+    const int gx = grid_for((long long)P.E * P.Np);
+    for (int c = 0; c < 7; ++c) {
+      enp::coarse_colour_vector<T><<<dim3(gx, B), 256, 0, h->stream>>>(v, P.ne[0], P.ne[1], P.ne[2],
+                                                                        P.Np, P.batch_stride, P.E, c);
+      cudaError_t er = enp::launch_op<T>(enp::kJvp, P, h->d_tab, uu, v, jv, B, h->stream);
+      if (er != cudaSuccess) return er;
+      enp::coarse_gather<T><<<dim3(grid_for(P.E), B), 256, 0, h->stream>>>(
+          jv, L0.A, P.ne[0], P.ne[1], P.ne[2], P.Np, P.batch_stride, c);
+    }
+    return cudaGetLastError();
+  };
+  if (S.storage == 0) {
+    e = probe(u, S.cwork, S.cwork + ntot);
+  } else {
+    float* w32 = reinterpret_cast<float*>(S.cwork);  // 2 ntot doubles hold 2 ntot floats
+    e = probe(static_cast<const float*>(S.u32), w32, w32 + ntot);
   }
+  if (e != cudaSuccess) return e;
   for (size_t l = 0; l + 1 < S.levels.size(); ++l) {
     const auto& F = S.levels[l];
     const auto& C = S.levels[l + 1];
@@ -1256,7 +1282,8 @@ void vcycle(enp_handle h, size_t l) {
       T.L[k] = enp::LevelDev{Q.nx, Q.ny, Q.nz, Q.n, Q.A32, Q.x, Q.b, Q.r};
     }
     T.inv = S.coarse_direct ? S.cinv : nullptr;
-    T.smooth = kSmoothSweeps;
+    T.smooth = S.coarse_smooth;
+    T.omega = S.coarse_omega;
     T.coarsest_sweeps = kCoarsestSweeps;
     enp::coarse_vcycle_tail<<<B, enp::kTailThreads, 0, h->stream>>>(T);
     return;
@@ -1271,7 +1298,7 @@ void vcycle(enp_handle h, size_t l) {
   }
   const dim3 g(grid_for(L.n), B);
   cudaMemsetAsync(L.x, 0, sizeof(float) * (size_t)L.n * B, h->stream);
-  for (int sw = 0; sw < kSmoothSweeps; ++sw) {
+  for (int sw = 0; sw < S.coarse_smooth; ++sw) {
     enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.nx, L.ny, L.nz, 0);
     enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.nx, L.ny, L.nz, 1);
   }
@@ -1280,8 +1307,9 @@ void vcycle(enp_handle h, size_t l) {
   enp::coarse_restrict<<<dim3(grid_for(C.n), B), 256, 0, h->stream>>>(L.r, L.nx, L.ny, L.nz, C.b,
                                                                       C.nx, C.ny, C.nz);
   vcycle(h, l + 1);
-  enp::coarse_prolong<<<g, 256, 0, h->stream>>>(C.x, C.nx, C.ny, C.nz, L.x, L.nx, L.ny, L.nz);
-  for (int sw = 0; sw < kSmoothSweeps; ++sw) {
+  enp::coarse_prolong<<<g, 256, 0, h->stream>>>(C.x, C.nx, C.ny, C.nz, L.x, L.nx, L.ny, L.nz,
+                                                S.coarse_omega);
+  for (int sw = 0; sw < S.coarse_smooth; ++sw) {
     enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.nx, L.ny, L.nz, 1);
     enp::coarse_gs<<<g, 256, 0, h->stream>>>(L.A32, L.x, L.b, L.nx, L.ny, L.nz, 0);
   }
@@ -1297,6 +1325,23 @@ cudaError_t coarse_apply(enp_handle h, const TV* r, TV* z) {
   enp::coarse_from_fine<TV><<<dim3(grid_for(32LL * P.E), B), 256, 0, h->stream>>>(r, L0.b, P.E, P.Np,
                                                                                P.batch_stride);
   vcycle(h, 0);
+  if (S.coarse_cycles > 1) {
+    // further cycles on the level-0 residual: x += V(b - A0 x)
+    const size_t n0 = (size_t)L0.n * B;
+    cudaError_t e = ensure(&S.cx_acc, S.cx_acc_count, n0);
+    if (e == cudaSuccess) e = ensure(&S.cb_keep, S.cb_keep_count, n0);
+    if (e != cudaSuccess) return e;
+    cudaMemcpyAsync(S.cb_keep, L0.b, sizeof(float) * n0, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(S.cx_acc, L0.x, sizeof(float) * n0, cudaMemcpyDeviceToDevice, h->stream);
+    const dim3 g0(grid_for(L0.n), B);
+    for (int c = 1; c < S.coarse_cycles; ++c) {
+      enp::coarse_residual<<<g0, 256, 0, h->stream>>>(L0.A32, S.cx_acc, S.cb_keep, L0.b, L0.nx,
+                                                      L0.ny, L0.nz);
+      vcycle(h, 0);
+      enp::axpy_f32<<<grid_for((long long)n0), 256, 0, h->stream>>>(L0.x, S.cx_acc, (long long)n0);
+    }
+    cudaMemcpyAsync(L0.x, S.cx_acc, sizeof(float) * n0, cudaMemcpyDeviceToDevice, h->stream);
+  }
   enp::coarse_to_fine<TV><<<dim3(grid_for((long long)P.E * P.Np), B), 256, 0, h->stream>>>(
       L0.x, z, P.E, P.Np, P.batch_stride);
   return cudaGetLastError();
@@ -1314,6 +1359,7 @@ void enp_solver_free(enp_handle h) {
     cudaFree(L.A); cudaFree(L.A32); cudaFree(L.x); cudaFree(L.b); cudaFree(L.r);
   }
   cudaFree(S.cwork); cudaFree(S.cdense); cudaFree(S.cinv);
+  cudaFree(S.cx_acc); cudaFree(S.cb_keep);
   if (S.gexec) cudaGraphExecDestroy(S.gexec);
   if (S.gstream) cudaStreamDestroy(S.gstream);
   cudaFree(S.gbuf);
@@ -1505,6 +1551,19 @@ extern "C" enp_status enp_set_preconditioner(enp_handle h, int two_level) {
   SolverState& S = state_of(h);
   S.coarse = two_level == 1;
   S.coarse_ready = false;
+  return ENP_OK;
+}
+
+extern "C" enp_status enp_set_coarse_options(enp_handle h, int cycles, int smooth, double omega) {
+  if (!h) return ENP_ERR_INVALID_ARG;
+  if (cycles < 1 || cycles > 8 || smooth < 1 || smooth > 8 || !(omega > 0.0) || !(omega <= 3.0)) {
+    h->err = "coarse options out of range";
+    return ENP_ERR_INVALID_ARG;
+  }
+  SolverState& S = state_of(h);
+  S.coarse_cycles = cycles;
+  S.coarse_smooth = smooth;
+  S.coarse_omega = (float)omega;
   return ENP_OK;
 }
 
@@ -2027,6 +2086,68 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
     st->converged = (status == ENP_OK) ? 1 : 0;
   }
   cleanup();
+  return status;
+}
+
+extern "C" enp_status enp_newton_continuation(enp_handle h, double* u, const double* phi_app,
+                                              const enp_continuation_opts* c,
+                                              const enp_newton_opts* o,
+                                              enp_continuation_stats* st) {
+  if (!h || !u || !phi_app || !c || !o) return ENP_ERR_INVALID_ARG;
+  if (!(c->step_min > 0.0) || !(c->step0 >= c->step_min) || !(c->step_max >= c->step0) ||
+      !(c->step_max <= 1.0) || !(c->grow >= 1.0) || c->stage_max_it < 1) {
+    h->err = "continuation options out of range";
+    return ENP_ERR_INVALID_ARG;
+  }
+  const int B = h->batch;
+  const long long ntot = h->n_dof * B;
+  double* ut = nullptr;
+  cudaError_t e = cudaMalloc(&ut, sizeof(double) * ntot);
+  if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc continuation iterate");
+  std::vector<double> phi(4 * (size_t)B);
+  enp_continuation_stats cs{};
+  double lam = 0.0, dl = c->step0;
+  enp_status status = ENP_OK;
+  while (true) {
+    const double nl = std::min(1.0, lam + dl);
+    const bool last = nl >= 1.0;
+    for (size_t i = 0; i < phi.size(); ++i) phi[i] = (last ? 1.0 : nl) * phi_app[i];
+    enp_status s2 = enp_set_phi_app(h, phi.data());
+    if (s2 != ENP_OK) { status = s2; break; }
+    e = cudaMemcpyAsync(ut, u, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) { status = cuda_err(h, e, "continuation copy"); break; }
+    enp_newton_opts so = *o;
+    if (!last) { so.rtol = c->stage_rtol; so.max_it = c->stage_max_it; }
+    enp_newton_stats ns{};
+    s2 = enp_newton_solve(h, ut, &so, &ns);
+    ++cs.stages;
+    cs.newton_iterations += ns.iterations;
+    cs.krylov_iterations += ns.krylov_iterations;
+    cs.last = ns;
+    if (s2 == ENP_OK) {
+      e = cudaMemcpyAsync(u, ut, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) { status = cuda_err(h, e, "continuation copy"); break; }
+      lam = last ? 1.0 : nl;
+      if (last) break;
+      dl = std::min(dl * c->grow, c->step_max);
+    } else if (s2 == ENP_ERR_NOT_CONVERGED || s2 == ENP_ERR_NONFINITE) {
+      ++cs.failed_stages;  // discard the stage's iterate, retry with half the increment
+      dl *= 0.5;
+      if (dl < c->step_min) {
+        status = ENP_ERR_NOT_CONVERGED;
+        h->err = "continuation increment fell below step_min";
+        break;
+      }
+    } else {
+      status = s2;
+      break;
+    }
+  }
+  enp_set_phi_app(h, phi_app);
+  cs.lambda = lam;
+  if (st) *st = cs;
+  cudaFree(ut);
   return status;
 }
 

@@ -52,7 +52,8 @@ def test_create_rejects_bad_descriptors_without_gpu_work():
 STRUCTS = [("enp_mesh_desc", "MeshDesc"), ("enp_physics_desc", "PhysicsDesc"),
            ("enp_disc_desc", "DiscDesc"), ("enp_krylov_opts", "KrylovOpts"),
            ("enp_krylov_stats", "KrylovStats"), ("enp_newton_opts", "NewtonOpts"),
-           ("enp_newton_stats", "NewtonStats")]
+           ("enp_newton_stats", "NewtonStats"), ("enp_continuation_opts", "ContinuationOpts"),
+           ("enp_continuation_stats", "ContinuationStats")]
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):
@@ -68,7 +69,8 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         cls = getattr(enp, pyname)
         lines.append(f'printf("{pyname} size %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
-            lines.append(f'printf("{pyname} {f} %zu\\n", offsetof({cname}, {f}));')
+            cf = f.rstrip("_")  # ctypes names a C field that is a Python keyword with a trailing _
+            lines.append(f'printf("{pyname} {f} %zu\\n", offsetof({cname}, {cf}));')
     lines += ["return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))

@@ -103,3 +103,46 @@ def test_autotune_keeps_results():
     after = (op.residual(u).cpu().numpy(), op.jvp(u, v).cpu().numpy())
     np.testing.assert_array_equal(before[0], after[0])
     np.testing.assert_array_equal(before[1], after[1])
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_continuation_reaches_strongly_driven_electrodes(mixed):
+    """Applied potentials 0.1 to 0.8 V on the plate reactor (Butler-Volmer
+    exponents up to e^31, Sec. 5.2): Newton from c = c_in, Phi = Phi_app / 2
+    fails at the top of the range, continuation in Phi_app reaches it. At the
+    end every operating point satisfies the oracle's residual equations at its
+    target potential to the tolerance, and the applied potentials of the
+    handle are the target ones."""
+    enp = _enp()
+    P = W.config("reactor_n1_p2")
+    volts = np.array([0.1, 0.35, 0.6, 0.8])
+    phis = 38.92 * volts
+    B = len(phis)
+    target = np.array([[ph, 0.0, 0.0, 0.0] for ph in phis])
+    op = enp.Operator(P, batch=B)
+    op.set_preconditioner(1)
+    kw = dict(bj_storage=enp.BJ_F32 if mixed else enp.BJ_F64, mixed=mixed, graph=mixed)
+    u = _cuda(W.reactor_initial_state(P, phis * 0.125))
+    st = op.newton_continuation(u, target, **kw)
+    assert st["status"] == enp.ENP_OK and st["lambda"] == 1.0, st
+    assert st["last"]["residual_norm"] <= 1e-10 * st["last"]["initial_norm"]
+    got = u.cpu().numpy().reshape(B, -1)
+    for i in range(B):
+        orc = oracle.Oracle(dataclasses.replace(P, bv_phi_app=list(target[i])))
+        r = np.linalg.norm(orc.residual(got[i]))
+        assert r <= 2e-10 * st["last"]["initial_norm"], (i, r)
+    # the handle is left at the target potentials: its residual there is small
+    import torch
+    r = torch.empty_like(u)
+    op.residual(u, out=r)
+    assert float(r.norm()) <= 2e-10 * st["last"]["initial_norm"] * np.sqrt(B)
+
+
+def test_continuation_rejects_bad_options():
+    enp = _enp()
+    P = W.config("reactor_n1_p2")
+    op = enp.Operator(P)
+    u = _cuda(W.reactor_initial_state(P, [1.0]))
+    with pytest.raises(enp.EnpError) as ei:
+        op.newton_continuation(u, [[1.0, 0, 0, 0]], step0=0.5, step_max=0.25)
+    assert ei.value.status == enp.ENP_ERR_INVALID_ARG
