@@ -53,9 +53,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # of the sources that kernel is built from (stale -> reported null): the
 # operator kernels from the operator headers, the block apply from the solver.
 TRAFFIC = {
-    ("907f08e606c1", "jvp_f64", "channel64_p3"): 134.67e6,
-    ("907f08e606c1", "jvp_f32", "channel64_p3"): 57.11e6,
-    ("5b4d5098ed56", "bj_apply_f32", "channel64_p3"): 4935.10e6,
+    ("26a945e0eac3", "jvp_f32", "channel64_p3"): 63.78e6,
 }
 
 KERNEL_SOURCES = {

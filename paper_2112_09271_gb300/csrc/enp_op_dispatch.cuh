@@ -14,8 +14,8 @@ static int g_eb3d[kMaxP + 1][4][5] = {};
 
 template <int P, int NF, int MODE, class R>
 static int default_eb() {
-  constexpr size_t per_el = (size_t)Smem3<P, NF, MODE>::total * sizeof(R);
-  constexpr int NT = (P + 2) * (P + 2);
+  constexpr int NT = tpe3d<P, R>();
+  constexpr size_t per_el = (size_t)Smem3<P, NF, MODE, NT>::total * sizeof(R);
   int eb = (int)((96 * 1024) / per_el);
   eb = eb < 1 ? 1 : eb;
   while (eb > 1 && eb * NT > kMaxThreads3D) --eb;
@@ -24,8 +24,8 @@ static int default_eb() {
 
 template <int P, int NF, int MODE, class R>
 static int max_eb() {
-  constexpr size_t per_el = (size_t)Smem3<P, NF, MODE>::total * sizeof(R);
-  constexpr int NT = (P + 2) * (P + 2);
+  constexpr int NT = tpe3d<P, R>();
+  constexpr size_t per_el = (size_t)Smem3<P, NF, MODE, NT>::total * sizeof(R);
   int eb = kMaxThreads3D / NT;
   while (eb > 1 && (size_t)eb * per_el > 200 * 1024) --eb;
   return eb < 1 ? 1 : eb;
@@ -35,9 +35,9 @@ static int max_eb() {
 template <int P, int NF, int MODE, class R>
 static cudaError_t launch_3d(const OpParams& prm, const R* u, const R* v, R* out, int batch,
                              cudaStream_t stream) {
-  using S3 = Smem3<P, NF, MODE>;
+  constexpr int NT = tpe3d<P, R>();
+  using S3 = Smem3<P, NF, MODE, NT>;
   constexpr size_t per_el = (size_t)S3::total * sizeof(R);
-  constexpr int NT = (P + 2) * (P + 2);
   int eb = g_eb3d[P][NF][MODE];
   if (eb <= 0) eb = default_eb<P, NF, MODE, R>();
   const size_t smem = (size_t)eb * per_el;

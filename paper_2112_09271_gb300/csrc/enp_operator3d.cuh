@@ -150,7 +150,16 @@ __device__ PhysT<Tan<R>> seed_phys(const PhysT<R>& p, int m, int j) {
   return q;
 }
 
-template <int P, int NF, int MODE>
+// Threads per element of the hexahedral kernel: Q x Q (one per pencil) for
+// FP64, whose issue rate the FP64 pipe bounds; more for FP32, which is
+// latency-bound and needs more warps in flight for the same shared memory.
+template <int P, class R>
+__host__ __device__ constexpr int tpe3d() {
+  if constexpr (std::is_same<R, double>::value) return (P + 2) * (P + 2);
+  else return P <= 1 ? 32 : (P == 2 ? 64 : 128);
+}
+
+template <int P, int NF, int MODE, int NT>
 struct Smem3 {
   static constexpr int N = P + 1, Q = P + 2;
   static constexpr int NX = Pad<N>::X;                   // padded x row of nodal arrays
@@ -179,23 +188,23 @@ struct Smem3 {
   // modulo the bank count (32 words), so that a warp spanning two elements
   // keeps consecutive threads on consecutive banks
   static constexpr int kBankWords = 32;
-  static constexpr int total = raw + ((Q * Q - raw % kBankWords) % kBankWords + kBankWords) % kBankWords;
-  static constexpr int kPrefetch = (NA * NN + Q * Q - 1) / (Q * Q);  // neighbour values per thread
+  static constexpr int total = raw + ((NT - raw % kBankWords) % kBankWords + kBankWords) % kBankWords;
+  static constexpr int kPrefetch = (NA * NN + NT - 1) / NT;  // neighbour values per thread
 };
 
 // Largest thread block of the hexahedral kernel; the elements per block (EB,
-// chosen at launch by the autotuner) satisfy EB * (P+2)^2 <= this.
+// chosen at launch by the autotuner) satisfy EB * tpe3d <= this.
 constexpr int kMaxThreads3D = 256;
 
 template <int P, int NF, int MODE, class R>
 __global__ void __launch_bounds__(kMaxThreads3D)
 op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v,
             R* __restrict__ out) {
-  using S = Smem3<P, NF, MODE>;
+  using S = Smem3<P, NF, MODE, tpe3d<P, R>()>;
   using TO = TabOff<P>;
   constexpr int N = S::N, Q = S::Q, NN = S::NN, NQ = S::NQ, FN = S::FN, FQ = S::FQ;
   constexpr int NX = S::NX, NNP = S::NNP, FNP = S::FNP;
-  constexpr int NV = S::NV, NA = S::NA, NT = Q * Q, PF = S::kPrefetch;
+  constexpr int NV = S::NV, NA = S::NA, NT = tpe3d<P, R>(), PF = S::kPrefetch;
   constexpr bool kBlk = MODE == kBlockCol;
   constexpr int MODEc = kBlk ? kJvp : MODE;
   const PhysT<R>& ph = phys<R>(prm);
@@ -278,14 +287,20 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   __syncthreads();
 
   {
-    const int kx = tid % Q, ky = tid / Q;
-    const R wxy = ctab<P, R>(TO::W + kx) * ctab<P, R>(TO::W + ky) * detJ;
-    R xp[3];
-    xp[0] = lo[0] + R(0.5) * (ctab<P, R>(TO::X + kx) + R(1)) * h[0];
-    xp[1] = lo[1] + R(0.5) * (ctab<P, R>(TO::X + ky) + R(1)) * h[1];
+    // points pt = tid, tid + NT, ...: with NT = Q^2 one thread runs down the z
+    // line of its (kx, ky), and the x-y weight and coordinates are hoisted
+    constexpr bool kLine = NT == Q * Q;
+    const int kx0 = tid % Q, ky0 = (tid / Q) % Q;
+    const R wxy0 = ctab<P, R>(TO::W + kx0) * ctab<P, R>(TO::W + ky0) * detJ;
+    const R xp00 = lo[0] + R(0.5) * (ctab<P, R>(TO::X + kx0) + R(1)) * h[0];
+    const R xp01 = lo[1] + R(0.5) * (ctab<P, R>(TO::X + ky0) + R(1)) * h[1];
 #pragma unroll 1
-    for (int kz = 0; kz < Q; ++kz) {
-      const int pt = kx + Q * (ky + Q * kz);
+    for (int pt = tid; pt < NQ; pt += NT) {
+      const int kx = kLine ? kx0 : pt % Q, ky = kLine ? ky0 : (pt / Q) % Q, kz = pt / (Q * Q);
+      const R wxy = kLine ? wxy0 : ctab<P, R>(TO::W + kx) * ctab<P, R>(TO::W + ky) * detJ;
+      R xp[3];
+      xp[0] = kLine ? xp00 : lo[0] + R(0.5) * (ctab<P, R>(TO::X + kx) + R(1)) * h[0];
+      xp[1] = kLine ? xp01 : lo[1] + R(0.5) * (ctab<P, R>(TO::X + ky) + R(1)) * h[1];
       xp[2] = lo[2] + R(0.5) * (ctab<P, R>(TO::X + kz) + R(1)) * h[2];
       R uv[3];
       velocity(ph, xp, uv);
@@ -452,7 +467,8 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
           ? (prm.phiapp_batch ? R(prm.phiapp_batch[bidx * 4 + (tag - kElectrode0)])
                               : ph.phiapp[tag - kElectrode0])
           : R(0);
-      const int pt = tid;  // NT == FQ
+#pragma unroll 1
+      for (int pt = tid; pt < FQ; pt += NT) {
       const int k1 = pt % Q, k2 = pt / Q;
       R xp[3];
       xp[a] = hi ? lo[a] + h[a] : lo[a];
@@ -546,6 +562,7 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
       for (int f = 0; f < NF; ++f) {
         FC[f * FQ + pt] = w * oS[f];
         FC[(NF + f) * FQ + pt] = w * sca * oT[f];
+      }
       }
     }
     __syncthreads();
