@@ -81,7 +81,9 @@ def _family(op_name):
 def contraction_flops(dim, p, nf, mode):
     """Floating-point operations (2 per multiply-add) of the sum-factorised
     contractions of one element for one operator application (mode 'res', 'jvp'
-    or 'vjp'), all faces counted as interior. Pointwise physics is excluded."""
+    or 'vjp'): the volume, and the dim faces the element owns (every face once),
+    each with the traces of both sides and the test contractions of both sides,
+    all counted as interior. Pointwise physics is excluded."""
     n, q = p + 1, p + 2
     if dim == 3:
         interp = q * n ** 3 + q * q * n * n + q ** 3 * n + 3 * q ** 4
@@ -93,7 +95,7 @@ def contraction_flops(dim, p, nf, mode):
         ftest = 2 * q * n + n * n
     nv = 1 if mode == "res" else 2
     vol = nf * (nv * interp + interp)
-    faces = 2 * dim * nf * (2 * nv * trace + ftest)
+    faces = dim * nf * (2 * nv * trace + 2 * ftest)
     return 2 * (vol + faces)
 
 

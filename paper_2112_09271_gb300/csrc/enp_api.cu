@@ -334,6 +334,22 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
   if (e == cudaSuccess) e = cudaMemcpy(h->d_tab, &h->htab, sizeof(Tables), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload tables"); enp_dg_destroy(h); return s; }
   P.btag = h->d_btag;
+  P.fbuf = nullptr;
+  P.fbuf_stride = 0;
+  for (int a = 0; a < 4; ++a) P.foff[a] = 0;
+  if (dim == 3) {
+    long long off = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+      P.foff[a] = off;
+      off += (long long)(P.ne[a] + 1) * P.ne[b0] * P.ne[b1];
+    }
+    P.foff[3] = off;
+    P.fbuf_stride = off * 2 * 2 * P.NF * (long long)P.n * P.n;
+    e = cudaMalloc(&h->d_fbuf, sizeof(double) * P.fbuf_stride * P.batch);
+    if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "cudaMalloc face buffer"); enp_dg_destroy(h); return s; }
+    P.fbuf = h->d_fbuf;
+  }
   e = enp::prepare_tables<double>(P.p, h->htab);
   if (e == cudaSuccess) e = enp::prepare_tables<float>(P.p, h->htab);
   if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload constant tables"); enp_dg_destroy(h); return s; }
@@ -350,6 +366,7 @@ enp_status enp_dg_destroy(enp_handle h) {
   cudaFree(h->d_src);
   cudaFree(h->d_dir);
   cudaFree(h->d_phiapp);
+  cudaFree(h->d_fbuf);
   delete h;
   return ENP_OK;
 }

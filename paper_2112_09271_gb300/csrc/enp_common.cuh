@@ -73,6 +73,13 @@ struct OpParams {
   double RT;
   int batch;                  // operating points
   int n_theta;                // parameters of dR/dtheta: D_1..D_m, c_in_1..c_in_{m-1}, phi_app_0..3
+  // hexahedra: faces of direction a are planes ia = 0..ne[a] times the cells of
+  // the other two axes, numbered from foff[a] (foff[3] = all faces); the face
+  // kernel leaves per face and side the lifted face coefficients in fbuf,
+  // [batch][face][side][value, normal derivative][NF][n^2], in the kernel's type
+  long long foff[4];
+  void* fbuf;
+  long long fbuf_stride;      // entries per operating point
 };
 
 template <class R> __host__ __device__ __forceinline__ const PhysT<R>& phys(const OpParams& p);

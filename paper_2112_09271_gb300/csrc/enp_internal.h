@@ -40,6 +40,7 @@ struct enp_dg {
   double* d_src = nullptr;
   double* d_dir = nullptr;
   double* d_phiapp = nullptr;
+  void* d_fbuf = nullptr;        // face coefficients of the hexahedral operator
   int batch = 1;
   long long n_dof = 0;           // per operating point
   cudaStream_t stream = nullptr;

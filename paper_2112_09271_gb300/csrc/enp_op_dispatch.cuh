@@ -49,6 +49,24 @@ static cudaError_t launch_3d(const OpParams& prm, const R* u, const R* v, R* out
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  if constexpr (S3::kFB) {
+    // the faces first: each face once, both sides' terms into the face buffer
+    constexpr int TF = tpf3d<P, R>();
+    constexpr size_t per_face = (size_t)SmemF<P, NF, MODE, TF>::total * sizeof(R);
+    constexpr int fpb_s = (int)((96 * 1024) / per_face);
+    constexpr int fpb = fpb_s < 1 ? 1 : (fpb_s * TF > kMaxThreads3D ? kMaxThreads3D / TF : fpb_s);
+    auto fk = face3d_kernel<P, NF, MODE, R>;
+    static bool fconfigured = false;
+    if (!fconfigured) {
+      cudaError_t e = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(fpb * per_face));
+      if (e != cudaSuccess) return e;
+      fconfigured = true;
+    }
+    const long long nf = prm.foff[3];
+    dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
+    fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v);
+  }
   dim3 grid((prm.E + eb - 1) / eb, batch);
   kern<<<grid, eb * NT, smem, stream>>>(prm, u, v, out);
   return cudaGetLastError();

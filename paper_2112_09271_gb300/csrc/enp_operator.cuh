@@ -165,6 +165,39 @@ __device__ __forceinline__ void face_interior_flux(const PhysT<C>& p, const S* c
   Sf[0] = S0 + R(-0.5) * (kapm * dm[0] + kapp * dp[0]) + (R(0.5) * delta) * (kapm + kapp) * jphi;
 }
 
+// The same interior flux for both sides of the face at once: (Sf, Tf) for the
+// minus side as above, and for the plus side (its own outward normal -n) the
+// value coefficient -Sf and the normal-derivative coefficient TfP. Only the
+// potential's T term differs from -Tf: it carries the plus side's kappa.
+template <int NF, class S, class R, class C = R>
+__device__ __forceinline__ void face_interior_flux2(const PhysT<C>& p, const S* cm, const S* dm,
+                                                    const S* cp, const S* dp, R un, R delta,
+                                                    S* Sf, S* Tf, S* TfP) {
+  S kapm = S(R(0)), kapp = S(R(0));
+  S T0 = S(R(0)), S0 = S(R(0));
+#pragma unroll
+  for (int k = 0; k < NF - 1; ++k) {
+    const int f = k + 1;
+    const C Dk = p.D[k], mg = p.mig[k], ak = p.acoef[k];
+    const S jc = cm[f] - cp[f];
+    const S qnm = un - mg * dm[0];
+    const S qnp = un - mg * dp[0];
+    const S qa = R(0.5) * (qnm + qnp);
+    Tf[f] = R(-0.5) * Dk * jc;
+    TfP[f] = -Tf[f];
+    Sf[f] = R(-0.5) * Dk * (dm[f] + dp[f]) + (Dk * delta) * jc +
+            R(0.5) * (cm[f] * qnm + cp[f] * qnp) + R(0.5) * absv(qa) * jc;
+    kapm += p.kcoef[k] * cm[f];
+    kapp += p.kcoef[k] * cp[f];
+    T0 += R(-0.5) * ak * jc;
+    S0 += R(-0.5) * ak * (dm[f] + dp[f]);
+  }
+  const S jphi = cm[0] - cp[0];
+  Tf[0] = T0 + R(-0.5) * kapm * jphi;
+  TfP[0] = -(T0 + R(-0.5) * kapp * jphi);
+  Sf[0] = S0 + R(-0.5) * (kapm * dm[0] + kapp * dp[0]) + (R(0.5) * delta) * (kapm + kapp) * jphi;
+}
+
 // Adjoint of the linearised interior own-row flux with respect to both sides,
 // given the weighted test traces Sh (value) and Th (normal derivative).
 // Accumulates into (acm, adm) for this side and (acp, adp) for the other side.

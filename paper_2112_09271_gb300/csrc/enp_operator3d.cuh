@@ -173,13 +173,17 @@ struct Smem3 {
   static constexpr int kT1 = NA * Q * N * N;             // after the x contraction
   static constexpr int kT2 = NA * Q * Q * N;             // after the y contraction
   static constexpr int kPts = NA * 4 * NQ;               // values + 3 gradients
-  static constexpr int kFace = NA * NNP                   // neighbour data
+  // R, J v and J^T w take their face terms from the face kernel's buffer:
+  // the six sides' lifted coefficients [6][2][NF][FN]
+  static constexpr bool kFB = MODE == kResidual || MODE == kJvp || MODE == kVjp;
+  static constexpr int kFaceLoop = NA * NNP              // neighbour data
                                + 2 * NA * 2 * FNP         // layer values + normal derivatives
                                + 2 * NA * 2 * Q * N       // after the first face contraction
                                + 2 * NA * 2 * FQ          // traces at face points
                                + 2 * NF * FQ              // face coefficients
                                + 2 * NF * Q * N           // transposed, first stage
                                + 2 * NF * FNP;            // transposed, at face nodes
+  static constexpr int kFace = kFB ? 6 * 2 * NF * FN : kFaceLoop;
   // T1 is dead once T2 is formed, so it shares space with the point arrays
   static constexpr int kVol = kT2 + (kPts > kT1 ? kPts : kT1);
   static constexpr int kWork = kVol > kFace ? kVol : kFace;
@@ -268,7 +272,7 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
       }
     }
   };
-  prefetch(0);
+  if constexpr (!S::kFB) prefetch(0);
   __syncthreads();
 
   // ---------------------------------------------------------------- volume
@@ -389,6 +393,43 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
   __syncthreads();
 
   // ---------------------------------------------------------------- faces
+  if constexpr (S::kFB) {
+    // the lifted coefficients of the six sides, left by the face kernel: side
+    // (a, hi) of this element is the lower element (0) of face plane
+    // idx[a] + 1 when hi, the upper one (1) of plane idx[a] otherwise
+    R* FS = WK;  // [6][2][NF][FN]
+    const R* fb = reinterpret_cast<const R*>(prm.fbuf) + (long long)bidx * prm.fbuf_stride;
+    constexpr int PER = 2 * NF * FN;
+    for (int w = tid; w < 6 * PER; w += NT) {
+      const int s = w / PER, r = w % PER;
+      const int a = s >> 1, hi = s & 1;
+      const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+      const long long gid = prm.foff[a] + (idx[a] + hi) +
+                            (long long)(prm.ne[a] + 1) * (idx[b0] + (long long)prm.ne[b0] * idx[b1]);
+      FS[w] = fb[(gid * 2 + (hi ? 0 : 1)) * PER + r];
+    }
+    __syncthreads();
+    // each row gathers its six face terms in side order (no two threads write
+    // one row)
+    for (int t = tid; t < NF * NN; t += NT) {
+      const int f = t / NN, i = t % NN;
+      const int c3[3] = {i % N, (i / N) % N, i / (N * N)};
+      R acc = RO[f * NNP + padded_node<N>(i)];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        const int a = s >> 1, hi = s & 1;
+        const int k = c3[a];
+        const int j = a == 0 ? c3[1] + N * c3[2] : (a == 1 ? c3[0] + N * c3[2] : c3[0] + N * c3[1]);
+        const R sv = FS[((s * 2 + 0) * NF + f) * FN + j];
+        const R tv = FS[((s * 2 + 1) * NF + f) * FN + j];
+        R add = ctab<P, R>(TO::dL + hi * N + k) * tv;
+        if (k == (hi ? N - 1 : 0)) add += sv;
+        acc += add;
+      }
+      RO[f * NNP + padded_node<N>(i)] = acc;
+    }
+    __syncthreads();
+  } else {
   R* XN = WK;                                  // [NA][NNP] neighbour data
   R* FL = XN + NA * NNP;                       // [2 sides][NA][2][FNP] layer values, derivatives
   R* F1 = FL + 2 * NA * 2 * FNP;               // [2][NA][2][Q][N]
@@ -587,6 +628,7 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
     }
     __syncthreads();
   }
+  }  // face loop of the block-column and parameter modes
 
   if (valid) {
     if (kBlk) {
@@ -598,6 +640,278 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
         const int f = t / NN, i = t % NN;
         out[ooff + f * EN + (long long)e * NN + i] = RO[f * NNP + padded_node<N>(i)];
       }
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Face kernel of R, J v and J^T w: each face of the mesh once, for both of its
+// sides. Threads per face: Q x Q for FP64, 64 for FP32 (p >= 2).
+template <int P, class R>
+__host__ __device__ constexpr int tpf3d() {
+  if constexpr (std::is_same<R, double>::value) return (P + 2) * (P + 2);
+  else return P <= 1 ? 32 : 64;
+}
+
+template <int P, int NF, int MODE, int NT>
+struct SmemF {
+  static constexpr int N = P + 1, Q = P + 2;
+  static constexpr int NX = Pad<N>::X;
+  static constexpr int NN = N * N * N, FN = N * N, FQ = Q * Q;
+  static constexpr int NNP = NX * N * N, FNP = NX * N;
+  static constexpr int NV = MODE == kResidual ? 1 : 2;
+  static constexpr int NA = NV * NF;
+  static constexpr int kX = 2 * NA * NNP;              // both elements' data
+  static constexpr int kF1 = 2 * NA * 2 * Q * N;       // after the first face contraction
+  static constexpr int kTR = 2 * NA * 2 * FQ;          // traces at the face points
+  static constexpr int kA = kX > kF1 + kTR ? kX : kF1 + kTR;  // X is dead once FL is formed
+  static constexpr int kFL = 2 * NA * 2 * FNP;         // layer values + normal derivatives
+  static constexpr int kFC = 2 * 2 * NF * FQ;          // [side][S, T][NF] at face points
+  static constexpr int kG1 = 2 * 2 * NF * Q * N;
+  static constexpr int kG2 = 2 * 2 * NF * FNP;
+  static constexpr int raw = kA + kFL + kFC + kG1 + kG2;
+  static constexpr int total = raw + ((NT - raw % 32) % 32 + 32) % 32;
+};
+
+template <int P, int NF, int MODE, class R>
+__global__ void __launch_bounds__(kMaxThreads3D)
+face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v) {
+  constexpr int NT = tpf3d<P, R>();
+  using S = SmemF<P, NF, MODE, NT>;
+  using TO = TabOff<P>;
+  constexpr int N = S::N, Q = S::Q, NN = S::NN, FN = S::FN, FQ = S::FQ;
+  constexpr int NX = S::NX, NNP = S::NNP, FNP = S::FNP, NA = S::NA;
+  const PhysT<R>& ph = phys<R>(prm);
+  extern __shared__ __align__(16) unsigned char smemf_raw[];
+  const int fs = threadIdx.x / NT, tid = threadIdx.x % NT;
+  R* base = reinterpret_cast<R*>(smemf_raw) + fs * S::total;
+  R* XS = base;                  // [2][NA][NNP]
+  R* F1 = base;                  // [2][NA][2][Q][N] (over XS, once FL is formed)
+  R* TR = F1 + S::kF1;           // [2][NA][2][FQ]
+  R* FL = base + S::kA;          // [2][NA][2][FNP]
+  R* FC = FL + S::kFL;           // [2][2][NF][FQ]
+  R* G1 = FC + S::kFC;           // [2][2][NF][N][Q]
+  R* G2 = G1 + S::kG1;           // [2][2][NF][FNP]
+  const int FPB = blockDim.x / NT;
+  const long long nf = prm.foff[3];
+  const long long graw = (long long)blockIdx.x * FPB + fs;
+  const bool valid = graw < nf;
+  const long long gid = valid ? graw : nf - 1;   // idle slots shadow a face, write nothing
+  const int bidx = blockIdx.y;
+  const long long boff = (long long)bidx * prm.batch_stride;
+  const long long EN = (long long)prm.E * NN;
+
+  const int a = (gid >= prm.foff[1]) + (gid >= prm.foff[2]);
+  const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+  const long long fi = gid - prm.foff[a];
+  const int na = prm.ne[a] + 1;
+  const int ia = (int)(fi % na);
+  const long long rr = fi / na;
+  const int j0 = (int)(rr % prm.ne[b0]), j1 = (int)(rr / prm.ne[b0]);
+  const bool hasL = ia > 0, hasU = ia < prm.ne[a];
+  const int stride[3] = {1, prm.ne[0], prm.ne[0] * prm.ne[1]};
+  const int eU = ia * stride[a] + j0 * stride[b0] + j1 * stride[b1];  // valid when hasU
+  const int eL = eU - stride[a];                                      // valid when hasL
+  const R lo0 = vertex<R>(prm, b0, j0), lo1 = vertex<R>(prm, b1, j1);
+  const R h0 = vertex<R>(prm, b0, j0 + 1) - lo0, h1 = vertex<R>(prm, b1, j1 + 1) - lo1;
+  const R xa = vertex<R>(prm, a, ia);
+  const R hL = hasL ? xa - vertex<R>(prm, a, ia - 1) : R(1);
+  const R hU = hasU ? vertex<R>(prm, a, ia + 1) - xa : R(1);
+  const R diagL = sqrt(hL * hL + h0 * h0 + h1 * h1), diagU = sqrt(hU * hU + h0 * h0 + h1 * h1);
+
+  // both elements' data (a missing side is zero and never read)
+  for (int t = tid; t < 2 * NA * NN; t += NT) {
+    const int side = t / (NA * NN), r = t % (NA * NN);
+    const int vv = r / (NF * NN), q = r % (NF * NN), f = q / NN, i = q % NN;
+    const bool has = side == 0 ? hasL : hasU;
+    R val = R(0);
+    if (has) {
+      const long long gi = boff + f * EN + (long long)(side == 0 ? eL : eU) * NN + i;
+      val = vv == 0 ? u[gi] : v[gi];
+    }
+    XS[(side * NA + vv * NF + f) * NNP + padded_node<N>(i)] = val;
+  }
+  __syncthreads();
+  // face-layer values and reference normal derivatives: the lower element at
+  // its upper face (layer N-1, derivative at xi = +1), the upper element at its
+  // lower face (layer 0, derivative at xi = -1)
+  for (int w = tid; w < 2 * NA * FN; w += NT) {
+    const int side = w / (NA * FN), r = w % (NA * FN), arr = r / FN, j = r % FN;
+    const int jn1 = j % N, jn2 = j / N;
+    const R* X = XS + (side * NA + arr) * NNP;
+    const int lay = side == 0 ? N - 1 : 0, dsel = side == 0 ? 1 : 0;
+    R d = R(0);
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      d = mad(ctab<P, R>(TO::dL + dsel * N + k), X[face_node_pad<N>(a, k, jn1, jn2)], d);
+    R* o = FL + ((side * NA + arr) * 2) * FNP;
+    const int jp = jn1 + NX * jn2;
+    o[jp] = X[face_node_pad<N>(a, lay, jn1, jn2)];
+    o[FNP + jp] = d;
+  }
+  __syncthreads();
+  pencil<P, N, N, 1, 0, 0, false, false, 4 * NA, FNP, Q * N, R, NX>(FL, F1, tid, NT);
+  __syncthreads();
+  pencil<P, Q, N, 1, 1, 0, false, false, 4 * NA, Q * N, FQ>(F1, TR, tid, NT);
+  __syncthreads();
+
+  {
+    const R area = R(0.25) * h0 * h1;
+    const R scL = R(2) / hL, scU = R(2) / hU;
+    const bool interior = hasL && hasU;
+    // boundary face: the one element's own side and outward normal
+    const int bside = hasL ? 0 : 1;
+    const R nrm = bside == 0 ? R(1) : R(-1);
+    const R sca = (bside == 0 ? scL : scU) * nrm;
+    int tag = kInterior, bface = -1;
+    if (!interior) {
+      bface = prm.side_off[2 * a + (bside == 0 ? 1 : 0)] + j0 + prm.ne[b0] * j1;
+      tag = prm.btag[bface];
+    }
+    const bool active = interior || !(tag == kWall || (tag == kInlet && MODE != kResidual));
+    const R delta = ph.cip * R(P * P) /
+                    (interior ? R(0.5) * (diagL + diagU) : (bside == 0 ? diagL : diagU));
+    const R phiapp = (tag >= kElectrode0)
+        ? (prm.phiapp_batch ? R(prm.phiapp_batch[bidx * 4 + (tag - kElectrode0)])
+                            : ph.phiapp[tag - kElectrode0])
+        : R(0);
+#pragma unroll 1
+    for (int pt = tid; pt < FQ; pt += NT) {
+      const int k1 = pt % Q, k2 = pt / Q;
+      R xp[3];
+      xp[a] = xa;
+      xp[b0] = lo0 + R(0.5) * (ctab<P, R>(TO::X + k1) + R(1)) * h0;
+      xp[b1] = lo1 + R(0.5) * (ctab<P, R>(TO::X + k2) + R(1)) * h1;
+      R uv[3];
+      velocity(ph, xp, uv);
+      const R w = ctab<P, R>(TO::W + k1) * ctab<P, R>(TO::W + k2) * area;
+      const R* T0p = TR + pt;
+      auto tr = [&](int side, int vv, int f, int comp) -> R {
+        return T0p[(((side * NA) + vv * NF + f) * 2 + comp) * FQ];
+      };
+      R oSL[NF], oTL[NF], oSU[NF], oTU[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) { oSL[f] = oTL[f] = oSU[f] = oTU[f] = R(0); }
+      if (interior) {
+        // the lower element's view: outward normal +e_a, derivatives along it
+        const R un = uv[a];
+        R cm[NF], dm[NF], cp[NF], dp[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          cm[f] = tr(0, 0, f, 0); dm[f] = tr(0, 0, f, 1) * scL;
+          cp[f] = tr(1, 0, f, 0); dp[f] = tr(1, 0, f, 1) * scU;
+        }
+        if (MODE == kResidual) {
+          face_interior_flux2<NF, R, R>(ph, cm, dm, cp, dp, un, delta, oSL, oTL, oTU);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) oSU[f] = -oSL[f];
+        } else {
+          R cm1[NF], dm1[NF], cp1[NF], dp1[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            cm1[f] = tr(0, 1, f, 0); dm1[f] = tr(0, 1, f, 1) * scL;
+            cp1[f] = tr(1, 1, f, 0); dp1[f] = tr(1, 1, f, 1) * scU;
+          }
+          if (MODE == kJvp) {
+            Tan<R> tm[NF], tdm[NF], tp[NF], tdp[NF], Sf[NF], Tf[NF], TfP[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              tm[f] = Tan<R>(cm[f], cm1[f]); tdm[f] = Tan<R>(dm[f], dm1[f]);
+              tp[f] = Tan<R>(cp[f], cp1[f]); tdp[f] = Tan<R>(dp[f], dp1[f]);
+            }
+            face_interior_flux2<NF, Tan<R>, R>(ph, tm, tdm, tp, tdp, un, delta, Sf, Tf, TfP);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              oSL[f] = Sf[f].d; oTL[f] = Tf[f].d; oSU[f] = -Sf[f].d; oTU[f] = TfP[f].d;
+            }
+          } else {
+            // J^T w: the rows of each side, differentiated with respect to both
+            // sides' states; the upper side's rows seen from the upper element
+            // (normal and normal derivatives flip)
+            R acm[NF], adm[NF], acp[NF], adp[NF], bcm[NF], bdm[NF], bcp[NF], bdp[NF];
+            R ncm[NF], ndm[NF], ncp[NF], ndp[NF], Sh[NF], Th[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              acm[f] = adm[f] = acp[f] = adp[f] = bcm[f] = bdm[f] = bcp[f] = bdp[f] = R(0);
+              Sh[f] = cm1[f]; Th[f] = dm1[f];
+            }
+            face_interior_adjoint<NF, R>(ph, cm, dm, cp, dp, un, delta, Sh, Th, acm, adm, acp, adp);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              ncm[f] = cp[f]; ndm[f] = -dp[f]; ncp[f] = cm[f]; ndp[f] = -dm[f];
+              Sh[f] = cp1[f]; Th[f] = -dp1[f];
+            }
+            face_interior_adjoint<NF, R>(ph, ncm, ndm, ncp, ndp, -un, delta, Sh, Th, bcm, bdm, bcp, bdp);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              oSL[f] = acm[f] + bcp[f]; oTL[f] = adm[f] - bdp[f];
+              oSU[f] = bcm[f] + acp[f]; oTU[f] = bdm[f] - adp[f];
+            }
+          }
+        }
+      } else if (active) {
+        const R un = uv[a] * nrm;
+        R cm[NF], dm[NF], g[NF], oS[NF], oT[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          cm[f] = tr(bside, 0, f, 0);
+          dm[f] = tr(bside, 0, f, 1) * sca;
+          g[f] = (tag == kDirichlet && prm.dirv)
+                     ? R(prm.dirv[((long long)f * prm.NBF + bface) * prm.Nfq + pt]) : R(0);
+          oS[f] = R(0); oT[f] = R(0);
+        }
+        if (MODE == kResidual) {
+          face_boundary_flux<NF, R, R>(ph, tag, cm, dm, g, un, delta, xp, phiapp, oS, oT);
+        } else {
+          R cm1[NF], dm1[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) { cm1[f] = tr(bside, 1, f, 0); dm1[f] = tr(bside, 1, f, 1) * sca; }
+          if (MODE == kJvp) {
+            Tan<R> tm[NF], tdm[NF], Sf[NF], Tf[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) { tm[f] = Tan<R>(cm[f], cm1[f]); tdm[f] = Tan<R>(dm[f], dm1[f]); }
+            face_boundary_flux<NF, Tan<R>, R>(ph, tag, tm, tdm, g, un, delta, xp, phiapp, Sf, Tf);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) { oS[f] = Sf[f].d; oT[f] = Tf[f].d; }
+          } else {
+            R acm[NF], adm[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acm[f] = adm[f] = R(0);
+            face_boundary_adjoint<NF, R>(ph, tag, cm, dm, g, un, delta, xp, phiapp, cm1, dm1, acm, adm);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) { oS[f] = acm[f]; oT[f] = adm[f]; }
+          }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          if (bside == 0) { oSL[f] = oS[f]; oTL[f] = oT[f]; }
+          else { oSU[f] = oS[f]; oTU[f] = oT[f]; }
+        }
+      }
+      // weights, and the normal derivative of each side's test functions along
+      // its own outward normal (+e_a for the lower side, -e_a for the upper)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        FC[((0 * 2 + 0) * NF + f) * FQ + pt] = w * oSL[f];
+        FC[((0 * 2 + 1) * NF + f) * FQ + pt] = w * scL * oTL[f];
+        FC[((1 * 2 + 0) * NF + f) * FQ + pt] = w * oSU[f];
+        FC[((1 * 2 + 1) * NF + f) * FQ + pt] = -(w * scU * oTU[f]);
+      }
+    }
+  }
+  __syncthreads();
+  // transposed 2D contraction back to the face nodes, both sides
+  pencil<P, Q, Q, 1, 1, 0, true, false, 4 * NF, FQ, Q * N>(FC, G1, tid, NT);
+  __syncthreads();
+  pencil<P, Q, N, 1, 0, 0, true, false, 4 * NF, Q * N, FNP, R, Q, NX>(G1, G2, tid, NT);
+  __syncthreads();
+  if (valid) {
+    R* fb = reinterpret_cast<R*>(prm.fbuf) + (long long)bidx * prm.fbuf_stride +
+            gid * 2 * 2 * NF * FN;
+    for (int w = tid; w < 2 * 2 * NF * FN; w += NT) {
+      const int c = w / FN, j = w % FN;   // c = (side * 2 + S/T) * NF + f
+      fb[w] = G2[c * FNP + (j % N) + NX * (j / N)];
     }
   }
 }
