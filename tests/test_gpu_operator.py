@@ -43,14 +43,26 @@ def _setup(cfg, seed=0, sources=True):
 
 
 SMALL = ["mms2d_n3", "mms2d_n4", "cube_n3_p1", "cube_n3_p2", "cube_n3_p3", "cube_n2_p4",
-         "channel_n1", "channel_n2", "reactor_n1_p2"]
+         "channel_n1", "channel_n2", "reactor_n1_p2", "cube_graded", "cube_dirichlet_graded"]
+
+# graded vertex coordinates: neighbouring elements differ in size along every axis,
+# so the two sides of a face have different lengths, normal scalings and diagonals
+GRADED = [np.array([0.0, 0.22, 0.61, 1.0]), np.array([0.0, 0.45, 0.7, 1.0]),
+          np.array([0.0, 0.3, 0.52, 1.0])]
 
 
 def _small(cfg):
+    import dataclasses
     if cfg == "mms2d_n4":
         return W.config("mms2d_n4", p=3)
     if cfg == "channel_n1":
         return W.config("channel_n1", p=2)
+    if cfg == "cube_graded":
+        return dataclasses.replace(W.config("cube_n3_p2"), coords=[c.copy() for c in GRADED])
+    if cfg == "cube_dirichlet_graded":
+        P = W.config("cube_n3_p3")
+        return dataclasses.replace(P, coords=[c.copy() for c in GRADED],
+                                   tags=[np.full_like(t, W.DIRICHLET) for t in P.tags])
     return W.config(cfg)
 
 
