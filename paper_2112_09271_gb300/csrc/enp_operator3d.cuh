@@ -70,9 +70,12 @@ __device__ __forceinline__ void pencil(const R* __restrict__ in, R* __restrict__
   constexpr int PA = DIR == 0 ? O1 : O0;          // pencil index ranges over the other dims
   constexpr int PB = DIR == 2 ? O1 : O2;
   constexpr int NP = PA * PB;
+  // work item w = c * NP + pp; (c, pp) advance by constant steps (no division
+  // per item), and the pencil's position is recomputed only when pp moves
+  int c = tid / NP, pp = tid % NP;
+  const int dc = NT / NP, dp = NT % NP;
 #pragma unroll 1
   for (int w = tid; w < NP * CNT; w += NT) {
-    const int c = w / NP, pp = w % NP;
     const int ia = pp % PA, ib = pp / PA;
     int ibase, obase;
     if (DIR == 0) { ibase = IX * (ia + E1 * ib); obase = OXX * (ia + O1 * ib); }
@@ -95,6 +98,9 @@ __device__ __forceinline__ void pencil(const R* __restrict__ in, R* __restrict__
       }
       dst[r * OS] = acc;
     }
+    c += dc;
+    pp += dp;
+    if (pp >= NP) { pp -= NP; ++c; }
   }
 }
 
@@ -736,18 +742,21 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
   // face-layer values and reference normal derivatives: the lower element at
   // its upper face (layer N-1, derivative at xi = +1), the upper element at its
   // lower face (layer 0, derivative at xi = -1)
+  // node (k along a, face node (j1, j2)) of a padded element array sits at
+  // fbase(j1, j2) + k * fstr
+  const int fstr = a == 0 ? 1 : (a == 1 ? NX : NX * N);
   for (int w = tid; w < 2 * NA * FN; w += NT) {
     const int side = w / (NA * FN), r = w % (NA * FN), arr = r / FN, j = r % FN;
     const int jn1 = j % N, jn2 = j / N;
-    const R* X = XS + (side * NA + arr) * NNP;
+    const int fbase = a == 0 ? NX * (jn1 + N * jn2) : (a == 1 ? jn1 + NX * N * jn2 : jn1 + NX * jn2);
+    const R* X = XS + (side * NA + arr) * NNP + fbase;
     const int lay = side == 0 ? N - 1 : 0, dsel = side == 0 ? 1 : 0;
     R d = R(0);
 #pragma unroll
-    for (int k = 0; k < N; ++k)
-      d = mad(ctab<P, R>(TO::dL + dsel * N + k), X[face_node_pad<N>(a, k, jn1, jn2)], d);
+    for (int k = 0; k < N; ++k) d = mad(ctab<P, R>(TO::dL + dsel * N + k), X[k * fstr], d);
     R* o = FL + ((side * NA + arr) * 2) * FNP;
     const int jp = jn1 + NX * jn2;
-    o[jp] = X[face_node_pad<N>(a, lay, jn1, jn2)];
+    o[jp] = X[lay * fstr];
     o[FNP + jp] = d;
   }
   __syncthreads();
