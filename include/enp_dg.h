@@ -239,8 +239,9 @@ typedef struct {
 
 /* Solve J(u_lin) x = b by flexible GMRES (the outer solver of Sec. 4.3, which
  * tolerates a preconditioner that varies between iterations), right-
- * preconditioned with the block-Jacobi inverse of the last setup (identity if
- * none), classical Gram-Schmidt applied twice. x holds the initial guess on
+ * preconditioned with the preconditioner of the last enp_block_jacobi_setup
+ * (block-Jacobi, plus the coarse potential correction when the two-level
+ * preconditioner is on; identity if none), classical Gram-Schmidt applied twice. x holds the initial guess on
  * entry. Every operating point of the batch is solved independently. stats is
  * a host pointer (may be NULL); the call synchronises.
  * Errors: NOT_CONVERGED (x holds the last iterate), NONFINITE, OOM, CUDA. */
