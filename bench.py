@@ -424,7 +424,9 @@ def main():
     applications = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32", "bj_apply_f32"]
     if args.only:
         ops, applications = [args.only], [args.only]
-    launches = {"residual_f64": 1, "jvp_f64": 1, "vjp_f64": 1, "jvp_f32": 1, "bj_apply_f32": 1,
+    op_l = 2 if prob.dim == 3 else 1   # hexahedra: a face launch, then an element launch
+    launches = {"residual_f64": op_l, "jvp_f64": op_l, "vjp_f64": op_l, "jvp_f32": op_l,
+                "bj_apply_f32": 1,
                 "recover_cm": 1, "inner_product": 2}
     launches_per_step = sum(launches.values())
     ip_out = np.zeros(1)
