@@ -406,13 +406,14 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
     R* FS = WK;  // [6][2][NF][FN]
     const R* fb = reinterpret_cast<const R*>(prm.fbuf) + (long long)bidx * prm.fbuf_stride;
     constexpr int PER = 2 * NF * FN;
-    for (int w = tid; w < 6 * PER; w += NT) {
-      const int s = w / PER, r = w % PER;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
       const int a = s >> 1, hi = s & 1;
       const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
       const long long gid = prm.foff[a] + (idx[a] + hi) +
                             (long long)(prm.ne[a] + 1) * (idx[b0] + (long long)prm.ne[b0] * idx[b1]);
-      FS[w] = fb[(gid * 2 + (hi ? 0 : 1)) * PER + r];
+      const R* src = fb + (gid * 2 + (hi ? 0 : 1)) * PER;
+      for (int r = tid; r < PER; r += NT) FS[s * PER + r] = src[r];
     }
     __syncthreads();
     // each row gathers its six face terms in side order (no two threads write
@@ -726,17 +727,24 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
   const R hU = hasU ? vertex<R>(prm, a, ia + 1) - xa : R(1);
   const R diagL = sqrt(hL * hL + h0 * h0 + h1 * h1), diagU = sqrt(hU * hU + h0 * h0 + h1 * h1);
 
-  // both elements' data (a missing side is zero and never read)
-  for (int t = tid; t < 2 * NA * NN; t += NT) {
-    const int side = t / (NA * NN), r = t % (NA * NN);
-    const int vv = r / (NF * NN), q = r % (NF * NN), f = q / NN, i = q % NN;
-    const bool has = side == 0 ? hasL : hasU;
-    R val = R(0);
-    if (has) {
-      const long long gi = boff + f * EN + (long long)(side == 0 ? eL : eU) * NN + i;
-      val = vv == 0 ? u[gi] : v[gi];
+  // both elements' data (a missing side is zero and never read); node-outer, so
+  // the padded offset is formed once per node
+  {
+    const long long gL = boff + (long long)(hasL ? eL : 0) * NN;
+    const long long gU = boff + (long long)(hasU ? eU : 0) * NN;
+    for (int i = tid; i < NN; i += NT) {
+      const int pi = padded_node<N>(i);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const long long o = f * EN + i;
+        XS[f * NNP + pi] = hasL ? u[gL + o] : R(0);
+        XS[(NA + f) * NNP + pi] = hasU ? u[gU + o] : R(0);
+        if (NA > NF) {
+          XS[(NF + f) * NNP + pi] = hasL ? v[gL + o] : R(0);
+          XS[(NA + NF + f) * NNP + pi] = hasU ? v[gU + o] : R(0);
+        }
+      }
     }
-    XS[(side * NA + vv * NF + f) * NNP + padded_node<N>(i)] = val;
   }
   __syncthreads();
   // face-layer values and reference normal derivatives: the lower element at
@@ -746,7 +754,8 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
   // fbase(j1, j2) + k * fstr
   const int fstr = a == 0 ? 1 : (a == 1 ? NX : NX * N);
   for (int w = tid; w < 2 * NA * FN; w += NT) {
-    const int side = w / (NA * FN), r = w % (NA * FN), arr = r / FN, j = r % FN;
+    const int sa = w / FN, j = w % FN;          // sa = side * NA + arr
+    const int side = sa >= NA ? 1 : 0, arr = sa - side * NA;
     const int jn1 = j % N, jn2 = j / N;
     const int fbase = a == 0 ? NX * (jn1 + N * jn2) : (a == 1 ? jn1 + NX * N * jn2 : jn1 + NX * jn2);
     const R* X = XS + (side * NA + arr) * NNP + fbase;
