@@ -53,8 +53,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # of the sources that kernel is built from (stale -> reported null): the
 # operator kernels from the operator headers, the block apply from the solver.
 TRAFFIC = {
-    ("c515ed536a93", "jvp_f64", "channel64_p3"): 697.63e6,   # face + element kernel
-    ("c515ed536a93", "jvp_f32", "channel64_p3"): 262.31e6,   # face + element kernel
+    ("c67d96fe2f34", "jvp_f64", "channel64_p3"): 696.50e6,   # face + element kernel
+    ("c67d96fe2f34", "jvp_f32", "channel64_p3"): 254.63e6,   # face + element kernel
+    ("c67d96fe2f34", "vjp_f64", "channel64_p3"): 693.85e6,   # face + element kernel
     ("7932dc7cae04", "bj_apply_f32", "channel64_p3"): 4934.11e6,
 }
 
