@@ -54,15 +54,24 @@ struct TabSmem {
 };
 
 // ----------------------------------------------------------------- physics
+// Component i (0..2) of a 3-vector held in registers, selected rather than
+// indexed, so that a run-time i keeps the vector out of local memory.
+template <class R>
+__device__ __forceinline__ R pick3(const R* v, int i) {
+  return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+
 template <class R>
 __device__ __forceinline__ void velocity(const PhysT<R>& p, const R* x, R* uv) {
-  uv[0] = uv[1] = uv[2] = R(0);
   if (p.vel_kind == 0) {
     uv[0] = p.vp[0]; uv[1] = p.vp[1]; uv[2] = p.vp[2];
   } else {  // plate flow u_A = 6 u_avg s (H - s) / H^2 (Sec. 5.2)
-    const int A = p.velA, Nn = p.velN;
-    const R s = x[Nn] - p.vp[2], H = p.vp[3];
-    uv[A] = p.vel_coef * s * (H - s);
+    const int A = p.velA;
+    const R s = pick3(x, p.velN) - p.vp[2], H = p.vp[3];
+    const R ua = p.vel_coef * s * (H - s);
+    uv[0] = A == 0 ? ua : R(0);
+    uv[1] = A == 1 ? ua : R(0);
+    uv[2] = A == 2 ? ua : R(0);
   }
 }
 
@@ -70,7 +79,7 @@ __device__ __forceinline__ void velocity(const PhysT<R>& p, const R* x, R* uv) {
 template <class C, class R>
 __device__ __forceinline__ C exchange_current(const PhysT<C>& p, const R* x) {
   if (p.J0axis < 0) return p.J0;
-  const C r = (x[p.J0axis] - p.J0lo - p.J0half) * p.J0inv_half;
+  const C r = (pick3(x, p.J0axis) - p.J0lo - p.J0half) * p.J0inv_half;
   return R(0.6) * p.J0 * (R(2) - r * r);
 }
 
@@ -244,7 +253,13 @@ __device__ __forceinline__ void face_interior_adjoint(const PhysT<R>& p, const R
 // Concentration of the Butler-Volmer oxidant (Eq. substitution if it is c_m).
 template <int NF, class S, class R, class C = R>
 __device__ __forceinline__ S oxidant_conc(const PhysT<C>& p, const S* c) {
-  if (p.bv_ox < NF - 1) return c[p.bv_ox + 1];
+  if (p.bv_ox < NF - 1) {  // selected, not indexed: c stays in registers
+    S o = c[1];
+#pragma unroll
+    for (int k = 1; k < NF - 1; ++k)
+      if (k == p.bv_ox) o = c[k + 1];
+    return o;
+  }
   S s = S(R(0));
 #pragma unroll
   for (int k = 0; k < NF - 1; ++k) s += p.z[k] * c[k + 1];
@@ -273,7 +288,9 @@ __device__ __forceinline__ void face_boundary_flux(const PhysT<C>& p, int tag, c
     S r = p.inv_cref * co;
     if (valof(p.gam) != R(1)) r = powv(r, valof(p.gam));
     const S Jn = exchange_current(p, x) * (expv(p.e1 * eta) - r * expv((-p.e2) * eta));
-    if (p.bv_ox < NF - 1) Sf[p.bv_ox + 1] = p.ox_species_scale * Jn;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k)
+      if (k == p.bv_ox) Sf[k + 1] = p.ox_species_scale * Jn;
     Sf[0] = p.ox_charge_scale * Jn;
   } else if (tag == kDirichlet) {
     S kap = S(R(0)), T0 = S(R(0)), S0 = S(R(0));
@@ -324,10 +341,14 @@ __device__ __forceinline__ void face_boundary_adjoint(const PhysT<R>& p, int tag
     const R dJdphi = J0 * (-p.e1 * E1 - r * p.e2 * E2);
     const R dJdco = -J0 * E2 * drdc;
     R Jh = p.ox_charge_scale * Sh[0];
-    if (p.bv_ox < NF - 1) Jh += p.ox_species_scale * Sh[p.bv_ox + 1];
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k)
+      if (k == p.bv_ox) Jh += p.ox_species_scale * Sh[k + 1];
     acm[0] += Jh * dJdphi;
     if (p.bv_ox < NF - 1) {
-      acm[p.bv_ox + 1] += Jh * dJdco;
+#pragma unroll
+      for (int k = 0; k < NF - 1; ++k)
+        if (k == p.bv_ox) acm[k + 1] += Jh * dJdco;
     } else {
 #pragma unroll
       for (int k = 0; k < NF - 1; ++k) acm[k + 1] += Jh * dJdco * p.zratio[k];

@@ -718,8 +718,9 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
   const int j0 = (int)(rr % prm.ne[b0]), j1 = (int)(rr / prm.ne[b0]);
   const bool hasL = ia > 0, hasU = ia < prm.ne[a];
   const int stride[3] = {1, prm.ne[0], prm.ne[0] * prm.ne[1]};
-  const int eU = ia * stride[a] + j0 * stride[b0] + j1 * stride[b1];  // valid when hasU
-  const int eL = eU - stride[a];                                      // valid when hasL
+  const int sa = pick3(stride, a);
+  const int eU = ia * sa + j0 * pick3(stride, b0) + j1 * pick3(stride, b1);  // valid when hasU
+  const int eL = eU - sa;                                                   // valid when hasL
   const R lo0 = vertex<R>(prm, b0, j0), lo1 = vertex<R>(prm, b1, j1);
   const R h0 = vertex<R>(prm, b0, j0 + 1) - lo0, h1 = vertex<R>(prm, b1, j1 + 1) - lo1;
   const R xa = vertex<R>(prm, a, ia);
@@ -797,12 +798,15 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
 #pragma unroll 1
     for (int pt = tid; pt < FQ; pt += NT) {
       const int k1 = pt % Q, k2 = pt / Q;
+      const R xb0 = lo0 + R(0.5) * (ctab<P, R>(TO::X + k1) + R(1)) * h0;
+      const R xb1 = lo1 + R(0.5) * (ctab<P, R>(TO::X + k2) + R(1)) * h1;
+      // (x, y, z) of the point by selection (a, b0, b1 are run-time axes)
       R xp[3];
-      xp[a] = xa;
-      xp[b0] = lo0 + R(0.5) * (ctab<P, R>(TO::X + k1) + R(1)) * h0;
-      xp[b1] = lo1 + R(0.5) * (ctab<P, R>(TO::X + k2) + R(1)) * h1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xp[c] = c == a ? xa : (c == b0 ? xb0 : xb1);
       R uv[3];
       velocity(ph, xp, uv);
+      const R ua = pick3(uv, a);
       const R w = ctab<P, R>(TO::W + k1) * ctab<P, R>(TO::W + k2) * area;
       const R* T0p = TR + pt;
       auto tr = [&](int side, int vv, int f, int comp) -> R {
@@ -813,7 +817,7 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
       for (int f = 0; f < NF; ++f) { oSL[f] = oTL[f] = oSU[f] = oTU[f] = R(0); }
       if (interior) {
         // the lower element's view: outward normal +e_a, derivatives along it
-        const R un = uv[a];
+        const R un = ua;
         R cm[NF], dm[NF], cp[NF], dp[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -869,7 +873,7 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
           }
         }
       } else if (active) {
-        const R un = uv[a] * nrm;
+        const R un = ua * nrm;
         R cm[NF], dm[NF], g[NF], oS[NF], oT[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
