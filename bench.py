@@ -53,9 +53,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # of the sources that kernel is built from (stale -> reported null): the
 # operator kernels from the operator headers, the block apply from the solver.
 TRAFFIC = {
-    ("c67d96fe2f34", "jvp_f64", "channel64_p3"): 696.50e6,   # face + element kernel
-    ("c67d96fe2f34", "jvp_f32", "channel64_p3"): 254.63e6,   # face + element kernel
-    ("c67d96fe2f34", "vjp_f64", "channel64_p3"): 693.85e6,   # face + element kernel
+    ("e71eeb0a6399", "jvp_f64", "channel64_p3"): 692.26e6,   # face + element kernel
+    ("e71eeb0a6399", "jvp_f32", "channel64_p3"): 244.93e6,   # face + element kernel
+    ("e71eeb0a6399", "vjp_f64", "channel64_p3"): 689.25e6,   # face + element kernel
     ("7932dc7cae04", "bj_apply_f32", "channel64_p3"): 4934.11e6,
 }
 
