@@ -105,8 +105,13 @@ typedef struct {
 
 /* Create an operator handle. Uploads the mesh, tags and basis tables, using
  * stream (a cudaStream_t, may be 0) for every later call. Synchronises once.
- * Errors: INVALID_ARG (bad descriptor), UNSUPPORTED (p, q, m or dim outside
- * the compiled set), OOM, CUDA. *out is NULL on failure. */
+ * On hexahedral meshes the handle also owns the face buffer through which the
+ * face kernel hands each face's terms to the element kernel: faces x 4 x m x
+ * (p+1)^2 x batch doubles (about 3 E of the faces; 154 MB per operating point
+ * for 64x32x16 elements at p = 3, m = 3). Calls on one handle share it and the
+ * solver workspace, so they must not overlap on the GPU (use one handle per
+ * concurrent stream). Errors: INVALID_ARG (bad descriptor), UNSUPPORTED (p, q,
+ * m or dim outside the compiled set), OOM, CUDA. *out is NULL on failure. */
 enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh,
                          const enp_physics_desc* phys, const enp_disc_desc* disc,
                          void* stream);
