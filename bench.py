@@ -199,7 +199,8 @@ def SOLVE_VARIANTS(enp):
     f64 = dict(bj_storage=enp.BJ_F64, mixed=False)
     mix = dict(bj_storage=enp.BJ_BF16, mixed=True)
     return [("fp64", 0, f64), ("mixed", 0, mix), ("fp64_two_level", 1, f64),
-            ("mixed_two_level", 1, mix), ("mixed_two_level_lag3", 1, dict(mix, pc_lag=3))]
+            ("mixed_two_level", 1, mix), ("mixed_two_level_lag3", 1, dict(mix, pc_lag=3)),
+            ("mixed_two_level_sweep", 1, dict(mix, sweep=1))]
 
 
 def run_solves(enp, W, name):
@@ -220,6 +221,8 @@ def run_solves(enp, W, name):
         u0[k] = prob.c_in[k - 1]
     out, sols = {"workload": name, "n_dof": prob.n_dof, "rtol": 1e-10}, {}
     for label, two, kw in SOLVE_VARIANTS(enp):
+        kw = dict(kw)
+        op.set_sweep(kw.pop("sweep", 0))
         op.set_preconditioner(two)
         u = torch.tensor(u0.reshape(-1), device="cuda")
         torch.cuda.synchronize()
@@ -247,7 +250,8 @@ def run_solves(enp, W, name):
     return out
 
 
-def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8), labels=("fp64", "mixed")):
+def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
+                      labels=("fp64", "mixed", "mixed_sweep")):
     """The operating-point sweep of the plate reactor (Sec. 5.2): `batch`
     applied cathode potentials from volts[0] to volts[1] (anode at 0), all
     solved in one batched Newton run per stage, with continuation in the
@@ -270,8 +274,10 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8), labels=("fp64", "
            "stage (max 0.25), /2 after a failed one; intermediate stages to 1e-6 in 10 iterations"}
     sols = {}
     kws = {"fp64": dict(bj_storage=enp.BJ_F64, mixed=False),
-           "mixed": dict(bj_storage=enp.BJ_F32, mixed=True)}
+           "mixed": dict(bj_storage=enp.BJ_F32, mixed=True),
+           "mixed_sweep": dict(bj_storage=enp.BJ_F32, mixed=True)}
     for label in labels:
+        op.set_sweep(1 if label.endswith("_sweep") else 0)
         u = torch.tensor(u0, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -289,11 +295,13 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8), labels=("fp64", "
                       "converged": st["status"] == 0,
                       "last_stage_relative_residual": last["residual_norm"] / last["initial_norm"],
                       "last_stage_residual_norm": last["residual_norm"]}
-    if "fp64" in sols and "mixed" in sols:
+    if "fp64" in sols:
         ref = sols["fp64"]
-        out["mixed_vs_fp64_relative_error"] = float(
-            np.linalg.norm(sols["mixed"] - ref) / np.linalg.norm(ref))
-        out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+        for lab in sols:
+            if lab != "fp64":
+                out[lab + "_vs_fp64_relative_error"] = float(
+                    np.linalg.norm(sols[lab] - ref) / np.linalg.norm(ref))
+                out["speedup_" + lab + "_over_fp64"] = out["fp64"]["seconds"] / out[lab]["seconds"]
     return out
 
 
@@ -575,7 +583,8 @@ def main():
         solve = run_solves(enp, W, args.solve_workload)
         full = args.reactor_workload.startswith("reactor192")
         batched = run_batched_solve(enp, W, args.reactor_workload,
-                                    labels=("mixed",) if full else ("fp64", "mixed"))
+                                    labels=("mixed", "mixed_sweep") if full
+                                    else ("fp64", "mixed", "mixed_sweep"))
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(prob)

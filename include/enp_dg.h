@@ -218,6 +218,23 @@ enp_status enp_set_preconditioner(enp_handle h, int two_level);
  * iterations by a quarter at 147k elements). Errors: INVALID_ARG. */
 enp_status enp_set_coarse_options(enp_handle h, int cycles, int smooth, double omega);
 
+/* Replace the block-Jacobi part of the preconditioner by one downwind block
+ * Gauss-Seidel sweep (on = 1; 0 restores block-Jacobi), hexahedral meshes:
+ * z = (D + L)^-1 r, D the element-diagonal blocks of the last setup and L the
+ * coupling of every element to its upstream neighbour along the flow axis (the
+ * plate-flow axis, or the largest component of a constant velocity, in its
+ * direction). The element planes across that axis are solved in flow order:
+ * each plane subtracts the face terms of J(u) z of the planes already solved
+ * (the face kernel restricted to the faces in between, at the u of the last
+ * setup) and applies its block inverses; 2 launches per plane. With upwind
+ * advection dominating, this carries information along the whole channel in
+ * one application, where block-Jacobi moves it one element per Krylov
+ * iteration (Pe = 1e4 in the plate reactor of Sec. 5.2). Combines with the
+ * two-level correction (added after the sweep). Takes effect at the next
+ * enp_block_jacobi_setup, which then also keeps a copy of u.
+ * Errors: INVALID_ARG, UNSUPPORTED (on = 1 on a 2D mesh). */
+enp_status enp_set_sweep(enp_handle h, int on);
+
 /* a0: device [batch][E][7] = the level-0 coarse operator of the last setup,
  * entries (self, -x, +x, -y, +y, -z, +z) of each element's row of
  * P^T J_PhiPhi P (zero where the neighbour does not exist).

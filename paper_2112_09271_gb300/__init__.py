@@ -167,6 +167,7 @@ _PROTOS = [
     ("enp_block_jacobi_apply", _I, [_V, _V, _V]),
     ("enp_set_preconditioner", _I, [_V, _I]),
     ("enp_set_coarse_options", _I, [_V, _I, _I, ctypes.c_double]),
+    ("enp_set_sweep", _I, [_V, _I]),
     ("enp_coarse_operator", _I, [_V, _V]),
     ("enp_fgmres_solve", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_fgmres_solve_f32", _I, [_V, _V, _V, _V, _V, _V]),
@@ -378,6 +379,10 @@ class Operator:
         """0: block-Jacobi; 1: block-Jacobi plus the coarse potential correction
         (takes effect at the next block_jacobi_setup)."""
         self._check(self._lib.enp_set_preconditioner(self.h, int(two_level)))
+
+    def set_sweep(self, on):
+        """1: downwind block Gauss-Seidel instead of block-Jacobi (next setup)."""
+        self._check(self._lib.enp_set_sweep(self.h, int(on)))
 
     def set_coarse_options(self, cycles=1, smooth=2, omega=1.0):
         """V-cycles per application, smoothing sweeps, prolongation over-correction."""

@@ -25,6 +25,12 @@ template <class R> int eb3d_get(int p, int nf, int mode);
 template <class R>
 cudaError_t prepare_tables(int p, const Tables& t);
 
+// J v face terms of the faces of plane ia of direction a only, into the face
+// buffer (hexahedra).
+template <class R>
+cudaError_t launch_face_plane(const OpParams& prm, const R* u, const R* v, int batch,
+                              cudaStream_t s, int a, int ia);
+
 }  // namespace enp
 
 struct enp_solver_ext;

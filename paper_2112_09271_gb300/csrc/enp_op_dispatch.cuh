@@ -65,7 +65,7 @@ static cudaError_t launch_3d(const OpParams& prm, const R* u, const R* v, R* out
     }
     const long long nf = prm.foff[3];
     dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
-    fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v);
+    fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v, -1, 0);
   }
   dim3 grid((prm.E + eb - 1) / eb, batch);
   kern<<<grid, eb * NT, smem, stream>>>(prm, u, v, out);
@@ -116,6 +116,43 @@ static cudaError_t launch_nf(int mode, const OpParams& prm, const Tables* t, con
                              const R* v, R* out, int batch, cudaStream_t s) {
   if (prm.NF == 2) return launch_mode<DIM, P, 2, R>(mode, prm, t, u, v, out, batch, s);
   if (prm.NF == 3) return launch_mode<DIM, P, 3, R>(mode, prm, t, u, v, out, batch, s);
+  return cudaErrorInvalidConfiguration;
+}
+
+// The face kernel of J v on the faces of plane ia of direction a only (the
+// upstream coupling of one plane of a block Gauss-Seidel sweep).
+template <int P, int NF, class R>
+static cudaError_t launch_face_plane_pn(const OpParams& prm, const R* u, const R* v, int batch,
+                                        cudaStream_t stream, int a, int ia) {
+  constexpr int TF = tpf3d<P, R>();
+  constexpr size_t per_face = (size_t)SmemF<P, NF, kJvp, TF>::total * sizeof(R);
+  constexpr int fpb_s = (int)((96 * 1024) / per_face);
+  constexpr int fpb = fpb_s < 1 ? 1 : (fpb_s * TF > kMaxThreads3D ? kMaxThreads3D / TF : fpb_s);
+  auto fk = face3d_kernel<P, NF, kJvp, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(fpb * per_face));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const long long nf = (long long)prm.ne[a == 0 ? 1 : 0] * prm.ne[a == 2 ? 1 : 2];
+  dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
+  fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v, a, ia);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_face_plane(const OpParams& prm, const R* u, const R* v, int batch,
+                              cudaStream_t s, int a, int ia) {
+  if (prm.dim != 3) return cudaErrorInvalidConfiguration;
+#define ENP_FP(PP)                                                                      \
+  case PP:                                                                              \
+    if (prm.NF == 2) return launch_face_plane_pn<PP, 2, R>(prm, u, v, batch, s, a, ia); \
+    if (prm.NF == 3) return launch_face_plane_pn<PP, 3, R>(prm, u, v, batch, s, a, ia); \
+    return cudaErrorInvalidConfiguration;
+  switch (prm.p) { ENP_FP(1) ENP_FP(2) ENP_FP(3) ENP_FP(4) }
+#undef ENP_FP
   return cudaErrorInvalidConfiguration;
 }
 

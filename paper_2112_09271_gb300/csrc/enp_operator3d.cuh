@@ -681,9 +681,13 @@ struct SmemF {
   static constexpr int total = raw + ((NT - raw % 32) % 32 + 32) % 32;
 };
 
+// pa < 0: every face of the mesh; pa >= 0: only the faces of plane pia of
+// direction pa (the upstream coupling of one plane in a block Gauss-Seidel
+// sweep), written to the same places of the face buffer.
 template <int P, int NF, int MODE, class R>
 __global__ void __launch_bounds__(kMaxThreads3D)
-face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v) {
+face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v, int pa,
+              int pia) {
   constexpr int NT = tpf3d<P, R>();
   using S = SmemF<P, NF, MODE, NT>;
   using TO = TabOff<P>;
@@ -701,21 +705,35 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
   R* G1 = FC + S::kFC;           // [2][2][NF][N][Q]
   R* G2 = G1 + S::kG1;           // [2][2][NF][FNP]
   const int FPB = blockDim.x / NT;
-  const long long nf = prm.foff[3];
+  const bool plane = pa >= 0;
+  const long long nf = plane ? (long long)prm.ne[pa == 0 ? 1 : 0] * prm.ne[pa == 2 ? 1 : 2]
+                             : prm.foff[3];
   const long long graw = (long long)blockIdx.x * FPB + fs;
   const bool valid = graw < nf;
-  const long long gid = valid ? graw : nf - 1;   // idle slots shadow a face, write nothing
+  const long long g = valid ? graw : nf - 1;     // idle slots shadow a face, write nothing
   const int bidx = blockIdx.y;
   const long long boff = (long long)bidx * prm.batch_stride;
   const long long EN = (long long)prm.E * NN;
 
-  const int a = (gid >= prm.foff[1]) + (gid >= prm.foff[2]);
+  int a, ia, j0, j1;
+  if (plane) {
+    a = pa;
+    ia = pia;
+    const int nb0 = prm.ne[a == 0 ? 1 : 0];
+    j0 = (int)(g % nb0);
+    j1 = (int)(g / nb0);
+  } else {
+    a = (g >= prm.foff[1]) + (g >= prm.foff[2]);
+    const long long fi = g - prm.foff[a];
+    const int na0 = prm.ne[a] + 1;
+    ia = (int)(fi % na0);
+    const long long rr = fi / na0;
+    const int nb0 = prm.ne[a == 0 ? 1 : 0];
+    j0 = (int)(rr % nb0);
+    j1 = (int)(rr / nb0);
+  }
   const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
-  const long long fi = gid - prm.foff[a];
-  const int na = prm.ne[a] + 1;
-  const int ia = (int)(fi % na);
-  const long long rr = fi / na;
-  const int j0 = (int)(rr % prm.ne[b0]), j1 = (int)(rr / prm.ne[b0]);
+  const long long gid = prm.foff[a] + ia + (long long)(prm.ne[a] + 1) * (j0 + (long long)prm.ne[b0] * j1);
   const bool hasL = ia > 0, hasU = ia < prm.ne[a];
   const int stride[3] = {1, prm.ne[0], prm.ne[0] * prm.ne[1]};
   const int sa = pick3(stride, a);

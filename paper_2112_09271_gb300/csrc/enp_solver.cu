@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -939,6 +940,72 @@ __global__ void gj_invert(const TB* __restrict__ blocks, T* __restrict__ work, T
     for (int r = lane; r < n; r += 32) o[(long long)c * n + r] = (TS)A[(long long)r * ld + c];
 }
 
+// One plane of the downwind block Gauss-Seidel sweep: the elements whose
+// coordinate along axis a is k, one per thread block. t = x_e minus the
+// upstream face terms J_(e,up) z_up that the face kernel left in the face buffer
+// (this element's side `side` of face plane `ia`: side 1 = its lower face, lifted
+// with dL(-1) onto node layer 0; side 0 = its upper face, dL(+1), layer N-1),
+// then z_e = Binv_e t. With upstream = 0 (the first plane) t = x_e.
+template <class TS, class TA, class TV>
+__global__ void sweep_plane_kernel(const TS* __restrict__ BT, const TV* __restrict__ x,
+                                   TV* __restrict__ z, int n, int NF, int N, long long EN,
+                                   long long bstride, int a, int k, int ne0, int ne1, int ne2,
+                                   int upstream, const TV* __restrict__ fb, long long fb_stride,
+                                   long long foff_a, int ia, int side,
+                                   const double* __restrict__ dL) {
+  extern __shared__ __align__(16) unsigned char ssm_raw[];
+  TA* ts = reinterpret_cast<TA*>(ssm_raw);
+  const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+  const int nb0 = a == 0 ? ne1 : ne0;
+  const int j0 = (int)(blockIdx.x % nb0), j1 = (int)(blockIdx.x / nb0);
+  const int stride[3] = {1, ne0, ne0 * ne1};
+  const int sa = a == 0 ? stride[0] : (a == 1 ? stride[1] : stride[2]);
+  const int sb0 = b0 == 0 ? stride[0] : stride[1];
+  const int sb1 = b1 == 1 ? stride[1] : stride[2];
+  const long long e = (long long)k * sa + (long long)j0 * sb0 + (long long)j1 * sb1;
+  const int b = blockIdx.y;
+  const int Np = N * N * N, FN = N * N;
+  const long long E = EN / Np;
+  const TV* xb = x + b * bstride;
+  const long long gid = foff_a + ia + (long long)((a == 0 ? ne0 : (a == 1 ? ne1 : ne2)) + 1) *
+                                          (j0 + (long long)(b0 == 0 ? ne0 : ne1) * j1);
+  const TV* fs = fb + b * fb_stride + (gid * 2 + side) * 2 * NF * FN;
+  const int lay = side == 1 ? 0 : N - 1;
+  const double* dl = dL + (side == 1 ? 0 : N);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const int f = c / Np, i = c % Np;
+    TA t = (TA)xb[f * EN + e * Np + i];
+    if (upstream) {
+      const int c3[3] = {i % N, (i / N) % N, i / (N * N)};
+      const int ka = a == 0 ? c3[0] : (a == 1 ? c3[1] : c3[2]);
+      const int j = a == 0 ? c3[1] + N * c3[2] : (a == 1 ? c3[0] + N * c3[2] : c3[0] + N * c3[1]);
+      const TA sv = (TA)fs[(0 * NF + f) * FN + j];
+      const TA tv = (TA)fs[(1 * NF + f) * FN + j];
+      TA add = (TA)dl[ka] * tv;
+      if (ka == lay) add += sv;
+      t -= add;
+    }
+    ts[c] = t;
+  }
+  __syncthreads();
+  const TS* B = BT + ((long long)b * E + e) * (long long)n * n;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    TA acc[8] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    int c = 0;
+    for (; c + 8 <= n; c += 8) {
+      TS bv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) bv[q] = B[(long long)(c + q) * n + r];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += (TA)bv[q] * ts[c + q];
+    }
+    for (; c < n; ++c) acc[0] += (TA)B[(long long)c * n + r] * ts[c];
+    const TA sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    const int f = r / Np, i = r % Np;
+    z[b * bstride + f * EN + e * Np + i] = (TV)sum;
+  }
+}
+
 // y_e = Binv_e x_e with the inverse stored transposed (BT[c][r]); accumulation in TA.
 template <class TS, class TA, class TV>
 __global__ void bj_apply_kernel(const TS* __restrict__ BT, const TV* __restrict__ x,
@@ -1016,7 +1083,17 @@ struct SolverState {
   size_t gbuf_bytes = 0;
   const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
   int gkey_i[4] = {0, 0, 0, 0};
+  // preconditioner generation: bumped whenever its configuration changes or a
+  // buffer it reads is reallocated, so that a captured FGMRES cycle is replayed
+  // only with the preconditioner it was captured with
+  unsigned long long pc_gen = 1, gkey_gen = 0;
   // two-level preconditioner: element-mean potential correction
+  bool sweep = false;             // downwind block Gauss-Seidel (enp_set_sweep)
+  bool sweep_ready = false;
+  int sweep_axis = 0, sweep_dir = 1;
+  double* upc64 = nullptr;        // the linearisation point of the last setup
+  float* upc32 = nullptr;
+  size_t upc64_count = 0, upc32_count = 0;
   bool coarse = false;            // enabled by enp_set_preconditioner
   int coarse_cycles = 1;          // V-cycles per application (enp_set_coarse_options)
   int coarse_smooth = 2;          // Gauss-Seidel sweeps before and after the coarse step
@@ -1264,6 +1341,12 @@ cudaError_t coarse_setup(enp_handle h, const double* u) {
       (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
     return e;
   S.coarse_direct = flag == 0;
+  {
+    const size_t n0 = (size_t)S.levels[0].n * B;
+    if ((e = ensure(&S.cx_acc, S.cx_acc_count, n0)) != cudaSuccess ||
+        (e = ensure(&S.cb_keep, S.cb_keep_count, n0)) != cudaSuccess)
+      return e;
+  }
   S.coarse_ready = true;
   return cudaSuccess;
 }
@@ -1326,11 +1409,11 @@ cudaError_t coarse_apply(enp_handle h, const TV* r, TV* z) {
                                                                                P.batch_stride);
   vcycle(h, 0);
   if (S.coarse_cycles > 1) {
-    // further cycles on the level-0 residual: x += V(b - A0 x)
+    // further cycles on the level-0 residual: x += V(b - A0 x); the buffers
+    // were allocated by the setup (no allocation here: this may be captured)
     const size_t n0 = (size_t)L0.n * B;
-    cudaError_t e = ensure(&S.cx_acc, S.cx_acc_count, n0);
-    if (e == cudaSuccess) e = ensure(&S.cb_keep, S.cb_keep_count, n0);
-    if (e != cudaSuccess) return e;
+    if (!S.cx_acc || !S.cb_keep || S.cx_acc_count < n0 || S.cb_keep_count < n0)
+      return cudaErrorInvalidValue;
     cudaMemcpyAsync(S.cb_keep, L0.b, sizeof(float) * n0, cudaMemcpyDeviceToDevice, h->stream);
     cudaMemcpyAsync(S.cx_acc, L0.x, sizeof(float) * n0, cudaMemcpyDeviceToDevice, h->stream);
     const dim3 g0(grid_for(L0.n), B);
@@ -1360,6 +1443,7 @@ void enp_solver_free(enp_handle h) {
   }
   cudaFree(S.cwork); cudaFree(S.cdense); cudaFree(S.cinv);
   cudaFree(S.cx_acc); cudaFree(S.cb_keep);
+  cudaFree(S.upc64); cudaFree(S.upc32);
   if (S.gexec) cudaGraphExecDestroy(S.gexec);
   if (S.gstream) cudaStreamDestroy(S.gstream);
   cudaFree(S.gbuf);
@@ -1408,8 +1492,15 @@ enp_status enp_block_diagonal(enp_handle h, const double* u, double* blocks) {
 }
 
 enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
+  // buffers the preconditioner's apply reads; a reallocation invalidates any
+  // captured FGMRES cycle
+  auto pc_ptrs = [](const SolverState& Q) {
+    return std::vector<const void*>{Q.binv, Q.cinv, Q.upc64, Q.upc32, Q.cx_acc, Q.cb_keep,
+                                    Q.levels.empty() ? nullptr : (const void*)Q.levels[0].A32};
+  };
   if (!h || !u || storage < 0 || storage > 2) return ENP_ERR_INVALID_ARG;
   SolverState& S = state_of(h);
+  const std::vector<const void*> pc_before = pc_ptrs(S);
   const OpParams& P = h->prm;
   const int nb = P.NF * P.Np;
   const long long nblk = (long long)h->batch * P.E;
@@ -1495,6 +1586,19 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
   if (S.coarse) {
     if ((e = coarse_setup(h, u)) != cudaSuccess) return cuda_err(h, e, "coarse setup");
   }
+  S.sweep_ready = false;
+  if (S.sweep) {
+    // the sweep's upstream couplings are J v face terms at this u: keep a copy
+    const long long ntot = h->n_dof * h->batch;
+    if ((e = ensure(&S.upc64, S.upc64_count, (size_t)ntot)) != cudaSuccess ||
+        (e = ensure(&S.upc32, S.upc32_count, (size_t)ntot)) != cudaSuccess)
+      return cuda_err(h, e, "cudaMalloc sweep state");
+    cudaMemcpyAsync(S.upc64, u, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, h->stream);
+    enp::convert_kernel<double, float><<<grid_for(ntot), 256, 0, h->stream>>>(u, S.upc32, ntot);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(h, e, "sweep setup");
+    S.sweep_ready = true;
+  }
+  if (pc_ptrs(S) != pc_before) ++S.pc_gen;
   return ENP_OK;
 }
 
@@ -1507,9 +1611,12 @@ static cudaError_t bj_apply_plain(enp_handle h, const TV* x, TV* y);
 // The preconditioner: block-Jacobi, plus the coarse potential correction when
 // the two-level preconditioner is enabled and set up.
 template <class TV>
+static cudaError_t sweep_apply(enp_handle h, const TV* x, TV* z);
+
+template <class TV>
 static cudaError_t bj_apply_any(enp_handle h, const TV* x, TV* y) {
   SolverState& S = state_of(h);
-  cudaError_t e = bj_apply_plain<TV>(h, x, y);
+  cudaError_t e = (S.sweep && S.sweep_ready) ? sweep_apply<TV>(h, x, y) : bj_apply_plain<TV>(h, x, y);
   if (e == cudaSuccess && S.coarse && S.coarse_ready) e = coarse_apply<TV>(h, x, y);
   return e;
 }
@@ -1538,6 +1645,51 @@ static cudaError_t bj_apply_plain(enp_handle h, const TV* x, TV* y) {
   return cudaGetLastError();
 }
 
+// Downwind block Gauss-Seidel: z = (D + L)^-1 x with D the element blocks and L
+// the couplings of each element to its upstream neighbour along the flow axis;
+// the element planes are solved in flow order, each after its upstream face
+// terms (J v of the planes already solved, restricted to the faces in between).
+template <class TV>
+static cudaError_t sweep_apply(enp_handle h, const TV* x, TV* z) {
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  const int B = h->batch;
+  const int nb = S.nb;
+  const long long EN = (long long)P.E * P.Np;
+  const long long ntot = h->n_dof * B;
+  cudaError_t e = cudaMemsetAsync(z, 0, sizeof(TV) * ntot, h->stream);
+  if (e != cudaSuccess) return e;
+  const int a = S.sweep_axis, dir = S.sweep_dir;
+  const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+  const int nplane = P.ne[b0] * P.ne[b1];
+  const int nk = P.ne[a];
+  const TV* upc = std::is_same<TV, double>::value ? reinterpret_cast<const TV*>(S.upc64)
+                                                  : reinterpret_cast<const TV*>(S.upc32);
+  const double* dL = reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->d_tab) +
+                                                     offsetof(enp::Tables, dL));
+  const TV* fb = reinterpret_cast<const TV*>(P.fbuf);
+  const int threads = std::min(256, ((nb + 31) / 32) * 32);
+  for (int step = 0; step < nk; ++step) {
+    const int k = dir > 0 ? step : nk - 1 - step;
+    const int up = step > 0 ? 1 : 0;
+    const int ia = dir > 0 ? k : k + 1;      // the face plane between k and its upstream plane
+    const int side = dir > 0 ? 1 : 0;        // this plane's side of it
+    if (up && (e = enp::launch_face_plane<TV>(P, upc, z, B, h->stream, a, ia)) != cudaSuccess)
+      return e;
+    const dim3 g(nplane, B);
+#define ENP_SWEEP(TS, TA)                                                                          \
+  enp::sweep_plane_kernel<TS, TA, TV><<<g, threads, sizeof(TA) * nb, h->stream>>>(                 \
+      reinterpret_cast<const TS*>(S.binv), x, z, nb, P.NF, P.n, EN, P.batch_stride, a, k,          \
+      P.ne[0], P.ne[1], P.ne[2], up, fb, P.fbuf_stride, P.foff[a], ia, side, dL)
+    if (S.storage == 0) ENP_SWEEP(double, double);
+    else if (S.storage == 1) ENP_SWEEP(float, float);
+    else ENP_SWEEP(__nv_bfloat16, float);
+#undef ENP_SWEEP
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 extern "C" enp_status enp_set_preconditioner(enp_handle h, int two_level) {
   if (!h) return ENP_ERR_INVALID_ARG;
   if (two_level < 0 || two_level > 1) {
@@ -1551,6 +1703,37 @@ extern "C" enp_status enp_set_preconditioner(enp_handle h, int two_level) {
   SolverState& S = state_of(h);
   S.coarse = two_level == 1;
   S.coarse_ready = false;
+  ++S.pc_gen;
+  return ENP_OK;
+}
+
+extern "C" enp_status enp_set_sweep(enp_handle h, int on) {
+  if (!h) return ENP_ERR_INVALID_ARG;
+  if (on < 0 || on > 1) {
+    h->err = "on must be 0 or 1";
+    return ENP_ERR_INVALID_ARG;
+  }
+  if (on == 1 && h->prm.dim != 3) {
+    h->err = "the sweep needs a hexahedral mesh";
+    return ENP_ERR_UNSUPPORTED;
+  }
+  SolverState& S = state_of(h);
+  S.sweep = on == 1;
+  S.sweep_ready = false;
+  ++S.pc_gen;
+  // the flow axis and direction: the plate-flow axis (velocity >= 0), or the
+  // largest component of a constant velocity
+  const auto& pd = h->prm.pd;
+  if (pd.vel_kind == 1) {
+    S.sweep_axis = pd.velA;
+    S.sweep_dir = 1;
+  } else {
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+      if (std::fabs(pd.vp[d]) > std::fabs(pd.vp[ax])) ax = d;
+    S.sweep_axis = ax;
+    S.sweep_dir = pd.vp[ax] < 0.0 ? -1 : 1;
+  }
   return ENP_OK;
 }
 
@@ -1564,6 +1747,7 @@ extern "C" enp_status enp_set_coarse_options(enp_handle h, int cycles, int smoot
   S.coarse_cycles = cycles;
   S.coarse_smooth = smooth;
   S.coarse_omega = (float)omega;
+  ++S.pc_gen;
   return ENP_OK;
 }
 
@@ -1829,7 +2013,7 @@ static enp_status fgmres_graph(enp_handle h, const TV* ulin, const TV* b, TV* x,
   const bool same = S.gexec && S.gkey[0] == (const void*)S.V && S.gkey[1] == S.binv &&
                     S.gkey[2] == (const void*)S.gbuf && S.gkey[3] == (const void*)S.dsmall &&
                     S.gkey_i[0] == m && S.gkey_i[1] == S.storage && S.gkey_i[2] == (int)sizeof(TV) &&
-                    S.gkey_i[3] == B;
+                    S.gkey_i[3] == B && S.gkey_gen == S.pc_gen;
   if (!same) {
     if (S.gexec) { cudaGraphExecDestroy(S.gexec); S.gexec = nullptr; }
     cudaGraph_t graph = nullptr;
@@ -1860,6 +2044,7 @@ static enp_status fgmres_graph(enp_handle h, const TV* ulin, const TV* b, TV* x,
     if (e != cudaSuccess) { S.gexec = nullptr; cudaEventDestroy(ev); return fail_cuda(e, "capture FGMRES cycle"); }
     S.gkey[0] = S.V; S.gkey[1] = S.binv; S.gkey[2] = S.gbuf; S.gkey[3] = S.dsmall;
     S.gkey_i[0] = m; S.gkey_i[1] = S.storage; S.gkey_i[2] = (int)sizeof(TV); S.gkey_i[3] = B;
+    S.gkey_gen = S.pc_gen;
   }
   std::vector<int> hj(B);
   int hflag[2] = {0, 0};

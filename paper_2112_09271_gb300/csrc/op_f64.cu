@@ -6,3 +6,5 @@ template cudaError_t enp::prepare_tables<double>(int, const Tables&);
 template int enp::eb3d_max<double>(int, int, int);
 template void enp::eb3d_set<double>(int, int, int, int);
 template int enp::eb3d_get<double>(int, int, int);
+template cudaError_t enp::launch_face_plane<double>(const OpParams&, const double*, const double*, int,
+                                                 cudaStream_t, int, int);
