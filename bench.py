@@ -53,10 +53,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # of the sources that kernel is built from (stale -> reported null): the
 # operator kernels from the operator headers, the block apply from the solver.
 TRAFFIC = {
-    ("e71eeb0a6399", "jvp_f64", "channel64_p3"): 692.26e6,   # face + element kernel
-    ("e71eeb0a6399", "jvp_f32", "channel64_p3"): 244.93e6,   # face + element kernel
-    ("e71eeb0a6399", "vjp_f64", "channel64_p3"): 689.25e6,   # face + element kernel
-    ("7932dc7cae04", "bj_apply_f32", "channel64_p3"): 4934.11e6,
+    ("451a1176cccc", "jvp_f64", "channel64_p3"): 692.34e6,   # face + element kernel
+    ("451a1176cccc", "jvp_f32", "channel64_p3"): 244.96e6,   # face + element kernel
+    ("451a1176cccc", "vjp_f64", "channel64_p3"): 689.70e6,   # face + element kernel
+    ("f8819b239f0b", "bj_apply_f32", "channel64_p3"): 4933.86e6,
 }
 
 KERNEL_SOURCES = {
