@@ -48,7 +48,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_gloo_timing_and_units():
     import torch.multiprocessing as mp
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of this multi-threaded process
     out = mgr.dict()
     port = _free_port()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
