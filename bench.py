@@ -56,24 +56,40 @@ TRAFFIC = {
     ("451a1176cccc", "jvp_f64", "channel64_p3"): 692.34e6,   # face + element kernel
     ("451a1176cccc", "jvp_f32", "channel64_p3"): 244.96e6,   # face + element kernel
     ("451a1176cccc", "vjp_f64", "channel64_p3"): 689.70e6,   # face + element kernel
-    ("f8819b239f0b", "bj_apply_f32", "channel64_p3"): 4933.86e6,
+    ("dfe77693e020", "bj_apply_f32", "channel64_p3"): 4933.86e6,
 }
 
 KERNEL_SOURCES = {
     "operator": ("enp_operator.cuh", "enp_operator3d.cuh", "enp_common.cuh"),
-    "solver": ("enp_solver.cu",),
 }
 
 
+def _function_text(src, signature):
+    """The text of the definition that starts at `signature` (through its
+    closing brace at column 0)."""
+    i = src.index(signature)
+    return src[i:src.index("\n}\n", i) + 3]
+
+
+def _solver_apply_text():
+    """The block apply's own source: its kernel and its host launcher."""
+    with open(os.path.join(ROOT, "paper_2112_09271_gb300", "csrc", "enp_solver.cu")) as fh:
+        src = fh.read()
+    return (_function_text(src, "__global__ void bj_apply_kernel(") +
+            _function_text(src, "static cudaError_t bj_apply_plain(enp_handle h, const TV* x, TV* y) {"))
+
+
 def _kernel_hash(kind=None):
-    """Hash of the sources of one kernel family ('operator' or 'solver'), or of
+    """Hash of the sources a kernel family is built from: 'operator' (the
+    operator headers), 'solver' (the block-apply kernel and its launcher), or
     both (None)."""
-    files = (KERNEL_SOURCES[kind] if kind else
-             KERNEL_SOURCES["operator"] + KERNEL_SOURCES["solver"])
     h = hashlib.sha1()
-    for f in files:
-        with open(os.path.join(ROOT, "paper_2112_09271_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    if kind in (None, "operator"):
+        for f in KERNEL_SOURCES["operator"]:
+            with open(os.path.join(ROOT, "paper_2112_09271_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    if kind in (None, "solver"):
+        h.update(_solver_apply_text().encode())
     return h.hexdigest()[:12]
 
 

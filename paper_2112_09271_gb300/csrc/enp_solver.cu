@@ -269,24 +269,11 @@ __global__ void scale_batched(const double* __restrict__ x, const double* __rest
     y[k] = sc[k / n] * x[k];
 }
 
-__global__ void axpby_kernel(double a, const double* __restrict__ x, double bcoef,
-                             const double* __restrict__ y, double* __restrict__ z, long long n) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    z[k] = a * x[k] + bcoef * y[k];
-}
-
 template <class TX, class TY>
 __global__ void convert_kernel(const TX* __restrict__ x, TY* __restrict__ y, long long n) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x)
     y[k] = (TY)x[k];
-}
-
-__global__ void count_nonfinite(const double* __restrict__ x, long long n, int* __restrict__ flag) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    if (!isfinite(x[k])) { atomicOr(flag, 1); return; }
 }
 
 // ------------------------------------------------------------------ FGMRES state
