@@ -3,11 +3,16 @@
 python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl native|reference]
 
 A step is one pass of the hot path over one synthetic state of the workload
-(inputs resident in HBM): R(u), J(u)v and J(u)^T w in FP64, the single-precision
-J(u)v of the mixed-precision inner solve, one block-Jacobi apply (FP32-stored
-inverses), the c_m recovery and one device inner product. `value` counts
-degrees of freedom times operator applications (R, J v FP64, J^T w, J v FP32,
-block apply) per second, in GDOF/s, summed over ranks. Each step is timed with
+(inputs resident in HBM): R(u), J(u)v and J(u)^T w of the FP64-accurate
+operator in both of its arithmetics (native FP64, and double-float on the FP32
+pipe), the single-precision J(u)v of the mixed-precision inner solve, one
+block-Jacobi apply (FP32-stored inverses), the c_m recovery and one device
+inner product. `value` is the metric's quantity: the FP64-accurate J(u)v in
+GDOF/s (unknown degrees of freedom per second of one application, in the faster
+of the two arithmetics, both parity-tested against the oracle at 1e-12),
+summed over ranks; the FP64, double-float and FP32 J v rates, the fraction of
+the HBM roofline and the FP64 vs mixed solve times are top-level keys, and the
+whole step's blend under `step_blend_GDOF_s`. Each operator is timed with
 CUDA events on the launching stream; between steps a 512 MB buffer is written
 to flush the 129 MB L2 (outside the events). The block-Jacobi setup, FGMRES and
 Newton rows run in a full solve of the cube16_p3 workload after the timed
@@ -48,6 +53,10 @@ FALLBACK_HBM_GBS = 6800.0
 # FMA loop at 1.99 GHz; 152 SMs x 2 x 2 flop x 2.07 GHz = 1.26 TFLOP/s nominal).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# A double-float multiply-add of a sum-factorised contraction takes 12 FP32
+# instructions (TwoProd with the cross terms: 4, TwoSum: 6, error sum: 2): its
+# issue-limited rate in FP64-equivalent flops.
+DF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
 
 # DRAM traffic per launch of a kernel from one ncu capture, keyed by the hash
 # of the sources that kernel is built from (stale -> reported null): the
@@ -119,8 +128,9 @@ def contraction_flops(dim, p, nf, mode):
 
 
 def algorithmic_bytes_per_dof(mode, word):
-    """Each vector read or written once (Sec. 8(d) of the design): R reads u and
-    writes r; J v and J^T w read u and v (or w) and write the result."""
+    """Each vector read or written once, geometry and velocity computed on the
+    fly: R reads u and writes r; J v and J^T w read u and v (or w) and write
+    the result."""
     return {"res": 2, "jvp": 3, "vjp": 3}[mode] * word
 
 
@@ -184,8 +194,9 @@ class ClockSampler:
 
 def cpu_baseline(prob, budget_s=12.0):
     """The oracle as it stands on the host cores, on a bounded sample of the
-    workload's elements: R(u) and J(u)v rows of randomly chosen elements, in
-    batches that grow until about budget_s seconds of CPU time are spent."""
+    workload's elements: J(u)v rows (the metric's operator) of randomly chosen
+    elements, in batches that grow until about budget_s seconds of CPU time are
+    spent."""
     import oracle
     import workloads as W
     orc = oracle.Oracle(prob)
@@ -196,17 +207,16 @@ def cpu_baseline(prob, budget_s=12.0):
     while t_ops < budget_s:
         el = rng.choice(prob.E, n_el, replace=False)
         t0 = time.perf_counter()
-        orc.residual(u, elems=el)
         orc.jvp(u, v, elems=el)
         dt = time.perf_counter() - t0
         t_ops += dt
         n_total += n_el
-        dofs += 2 * n_el * prob.n_fields * prob.Np
+        dofs += n_el * prob.n_fields * prob.Np
         want = n_el * (budget_s - t_ops) / max(dt, 1e-4)
         n_el = int(max(1, min(prob.E, want, 8 * n_el)))
     return {"value": dofs / t_ops / 1e9, "unit": "GDOF/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": f"R(u) and J(u)v rows of {n_total} randomly chosen elements (with "
+            "sample": f"J(u)v rows of {n_total} randomly chosen elements (with "
                       f"repeats) of {prob.name} ({prob.E} elements), {t_ops:.1f} s of CPU time"}
 
 
@@ -372,7 +382,8 @@ def run_reference(args, rank, world):
             "ms_per_step": 1e3 * wall / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": prob.name, "n_dof": prob.n_dof, "p": prob.p,
-                       "elements": prob.E, "fields": prob.n_fields, "l2": "sampled rows (CPU)"},
+                       "elements": prob.E, "fields": prob.n_fields, "l2": "sampled rows (CPU)",
+                       "value": "FP64 J(u)v rows of the oracle, GDOF/s"},
             "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": cb["cores"],
                              "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0,
@@ -395,7 +406,8 @@ def main():
                          "plate reactor, mixed precision only, about 13 minutes)")
     ap.add_argument("--only", default=None,
                     help="time one operator alone (for profiling): residual_f64, jvp_f64, "
-                         "vjp_f64, jvp_f32, bj_apply_f32; no autotune, solves or e2e; or "
+                         "vjp_f64, residual_df32, jvp_df32, vjp_df32, jvp_f32, bj_apply_f32; "
+                         "no autotune, solves or e2e; or "
                          "fgmres_f64 / fgmres_f32: FGMRES(50) cycles with the two-level "
                          "preconditioner on the solve workload")
     args = ap.parse_args()
@@ -437,31 +449,37 @@ def main():
     jv32 = torch.empty_like(u32)
     cm = torch.empty(prob.E * prob.Np, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tuned = {}
     if args.only:
-        tuned = [0] * 5
         if args.only == "bj_apply_f32":
             op.block_jacobi_setup(u, enp.BJ_F32)
     else:
-        tuned = op.autotune()                  # launch shape per operator, before any timing
+        # launch shape per operator and arithmetic, before any timing
+        for ar, code in (("f64", enp.ARITH_F64), ("df32", enp.ARITH_DF32)):
+            op.set_arithmetic(code)
+            tuned[ar] = op.autotune()
+        op.set_arithmetic(enp.ARITH_F64)
         op.block_jacobi_setup(u, enp.BJ_F32)   # preconditioner set up once, outside the steps
-    ops = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32", "bj_apply_f32", "recover_cm",
-           "inner_product"]
-    applications = ["residual_f64", "jvp_f64", "vjp_f64", "jvp_f32", "bj_apply_f32"]
+    fp64_ops = ["residual_f64", "jvp_f64", "vjp_f64", "residual_df32", "jvp_df32", "vjp_df32"]
+    ops = fp64_ops + ["jvp_f32", "bj_apply_f32", "recover_cm", "inner_product"]
+    applications = fp64_ops + ["jvp_f32", "bj_apply_f32"]
     if args.only:
         ops, applications = [args.only], [args.only]
     op_l = 2 if prob.dim == 3 else 1   # hexahedra: a face launch, then an element launch
-    launches = {"residual_f64": op_l, "jvp_f64": op_l, "vjp_f64": op_l, "jvp_f32": op_l,
-                "bj_apply_f32": 1,
-                "recover_cm": 1, "inner_product": 2}
-    launches_per_step = sum(launches.values())
+    launches = {nm: op_l for nm in fp64_ops + ["jvp_f32"]}
+    launches.update({"bj_apply_f32": 1, "recover_cm": 1, "inner_product": 2})
+    launches_per_step = sum(launches[nm] for nm in ops)
     ip_out = np.zeros(1)
 
     def run_op(name):
-        if name == "residual_f64":
+        if name in fp64_ops:
+            op.set_arithmetic(enp.ARITH_DF32 if name.endswith("_df32") else enp.ARITH_F64)
+        kind = name.rsplit("_", 1)[0]
+        if name in fp64_ops and kind == "residual":
             op.residual(u, out=r)
-        elif name == "jvp_f64":
+        elif name in fp64_ops and kind == "jvp":
             op.jvp(u, v, out=jv)
-        elif name == "vjp_f64":
+        elif name in fp64_ops and kind == "vjp":
             op.vjp(u, w, out=jtw)
         elif name == "jvp_f32":
             op.jvp_f32(u32, v32, out=jv32)
@@ -510,9 +528,6 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms_step = pdist.max_over_ranks(total_ms / args.steps, device="cuda")
-    units = n * len(applications)
-    value = world * units / (ms_step * 1e-3) / 1e9
-
     per_op = {nm: {"ms": t_ops[nm] / args.steps,
                    "GDOF_s": n / (t_ops[nm] / args.steps * 1e-3) / 1e9} for nm in ops}
     if args.only:
@@ -524,28 +539,43 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
-    # roofline of the dominant kernel (the FP64 operator: ALU-bound on GB300)
-    dom = max(("residual_f64", "jvp_f64", "vjp_f64"), key=lambda k: t_ops[k])
-    if t_ops["jvp_f64"] >= 0.95 * t_ops[dom]:
-        dom = "jvp_f64"  # the metric's operator, when within 5 % of the slowest
-    mode = {"residual_f64": "res", "jvp_f64": "jvp", "vjp_f64": "vjp"}[dom]
-    fl = contraction_flops(prob.dim, prob.p, prob.n_fields, mode) * prob.E * op.batch
-    dom_s = t_ops[dom] / args.steps * 1e-3
-    achieved = fl / dom_s / 1e12
+    # the headline: the FP64-accurate J v, in the faster of its two arithmetics
+    ms_jv = {ar: pdist.max_over_ranks(t_ops["jvp_" + ar] / args.steps, device="cuda")
+             for ar in ("f64", "df32")}
+    head = min(ms_jv, key=ms_jv.get)
+    head_op = "jvp_" + head
+    value = world * n / (ms_jv[head] * 1e-3) / 1e9
+    blend = world * n * len(applications) / (ms_step * 1e-3) / 1e9
+    op.set_arithmetic(enp.ARITH_DF32 if head == "df32" else enp.ARITH_F64)
+
+    # roofline of the headline kernel pair (face + element launch of J v): bound by
+    # the arithmetic pipe it runs on; its HBM fraction alongside
+    fl = contraction_flops(prob.dim, prob.p, prob.n_fields, "jvp") * prob.E * op.batch
+    dom_s = ms_jv[head] * 1e-3
     hbm, hbm_kind = read_peaks()
-    hbm_bytes = algorithmic_bytes_per_dof(mode, 8) * n
+    hbm_bytes = algorithmic_bytes_per_dof("jvp", 8) * n
     kh = _kernel_hash("operator")
-    traffic = TRAFFIC.get((kh, dom, prob.name))
-    roof = {"bound": "alu", "kernel": f"face3d_kernel + op3d_kernel <p={prob.p},NF={prob.n_fields},"
-                                      f"{mode},double> (one operator application = the two "
-                                      f"launches, timed together)",
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (measured FMA loop 1.20)",
-            "traffic": traffic,
+    traffic = TRAFFIC.get((kh, head_op, prob.name))
+    if head == "df32":
+        peak = DF32_PEAK_TFLOPS
+        peak_kind = ("derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 FP32 instructions per "
+                     "double-float multiply-add x 2 flop")
+        kname = f"face3d_kernel + op3d_kernel <p={prob.p},NF={prob.n_fields},jvp,df> (double-float)"
+    else:
+        peak = FP64_PEAK_TFLOPS
+        peak_kind = "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (measured FMA loop 1.20)"
+        kname = f"face3d_kernel + op3d_kernel <p={prob.p},NF={prob.n_fields},jvp,double>"
+    achieved = fl / dom_s / 1e12
+    hbm_frac = hbm_bytes / dom_s / 1e9 / hbm
+    roof = {"bound": "alu", "kernel": kname + " (one operator application = the two launches, "
+                                              "timed together)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "traffic": traffic,
             "hbm_achieved_GBs": hbm_bytes / dom_s / 1e9, "hbm_peak_GBs": hbm,
-            "hbm_frac": hbm_bytes / dom_s / 1e9 / hbm, "hbm_peak_kind": hbm_kind,
-            "flops_per_launch": fl, "algorithmic_bytes_per_launch": hbm_bytes}
+            "hbm_frac": hbm_frac, "hbm_peak_kind": hbm_kind,
+            "flops_per_launch": fl, "flops_kind": "sum-factorised contraction flops of the "
+            "volume and the faces each element owns (pointwise physics excluded)",
+            "algorithmic_bytes_per_launch": hbm_bytes}
     nb = prob.n_fields * prob.Np
     bj_bytes = prob.E * (nb * nb * 4 + 2 * nb * 8)  # FP32 inverse + FP64 x in, y out
     bj_s = t_ops["bj_apply_f32"] / args.steps * 1e-3
@@ -554,30 +584,26 @@ def main():
                 "frac": bj_bytes / bj_s / 1e9 / hbm, "peak_kind": hbm_kind,
                 "bytes_per_launch": bj_bytes,
                 "traffic": TRAFFIC.get((_kernel_hash("solver"), "bj_apply_f32", prob.name))}
-    f32_fl = contraction_flops(prob.dim, prob.p, prob.n_fields, "jvp") * prob.E
     f32_s = t_ops["jvp_f32"] / args.steps * 1e-3
-    per_op["jvp_f32"]["fp32_TFLOPs"] = f32_fl / f32_s / 1e12
-    per_op["jvp_f32"]["fp32_frac"] = f32_fl / f32_s / 1e12 / FP32_PEAK_TFLOPS
+    per_op["jvp_f32"]["fp32_TFLOPs"] = fl / op.batch / f32_s / 1e12
+    per_op["jvp_f32"]["fp32_frac"] = fl / op.batch / f32_s / 1e12 / FP32_PEAK_TFLOPS
     per_op["jvp_f32"]["hbm_frac"] = algorithmic_bytes_per_dof("jvp", 4) * n / f32_s / 1e9 / hbm
+    per_op["jvp_f32"]["traffic"] = TRAFFIC.get((kh, "jvp_f32", prob.name))
+    for ar in ("f64", "df32"):
+        t = t_ops["jvp_" + ar] / args.steps * 1e-3
+        per_op["jvp_" + ar]["hbm_frac"] = hbm_bytes / t / 1e9 / hbm
 
-    # end to end through the C ABI with host buffers: H2D of u, v, w (pinned),
-    # the operators, D2H of the results, every step
-    hu, hv, hw = (x.cpu().pin_memory() for x in (u, v, w))
-    hr, hj, ht = (torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3))
-    hj32 = torch.empty(n, dtype=torch.float32).pin_memory()
-    hz = torch.empty(n, dtype=torch.float64).pin_memory()
-    du, dv, dw = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
+    # end to end through the C ABI with host buffers, every step: H2D of u and v
+    # (pinned), the FP64-accurate J v, D2H of the result
+    hu, hv = (x.cpu().pin_memory() for x in (u, v))
+    hj = torch.empty(n, dtype=torch.float64).pin_memory()
+    du, dv = torch.empty_like(u), torch.empty_like(v)
 
     def e2e_step():
-        du.copy_(hu, non_blocking=True); dv.copy_(hv, non_blocking=True)
-        dw.copy_(hw, non_blocking=True)
-        op.residual(du, out=r); op.jvp(du, dv, out=jv); op.vjp(du, dw, out=jtw)
-        du32, dv32 = du.float(), dv.float()
-        op.jvp_f32(du32, dv32, out=jv32)
-        op.block_jacobi_apply(dv, out=z)
-        hr.copy_(r, non_blocking=True); hj.copy_(jv, non_blocking=True)
-        ht.copy_(jtw, non_blocking=True); hj32.copy_(jv32, non_blocking=True)
-        hz.copy_(z, non_blocking=True)
+        du.copy_(hu, non_blocking=True)
+        dv.copy_(hv, non_blocking=True)
+        op.jvp(du, dv, out=jv)
+        hj.copy_(jv, non_blocking=True)
 
     for _ in range(3):
         e2e_step()
@@ -589,9 +615,9 @@ def main():
     s1.record(stream)
     s1.synchronize()
     e2e_ms = pdist.max_over_ranks(s0.elapsed_time(s1) / e_steps, device="cuda")
-    e2e = {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
-           "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 4 * n * 8 + n * 4,
-           "ms_per_step": e2e_ms}
+    e2e = {"value": world * n / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
+           "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8,
+           "ms_per_step": e2e_ms, "arith": head}
 
     del flush
     solve = batched = None
@@ -605,19 +631,35 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(prob)
     if rank == 0:
+        solve_seconds = None
+        if solve:
+            solve_seconds = {k: solve[k]["seconds"] for k in solve
+                             if isinstance(solve[k], dict) and "seconds" in solve[k]}
+            solve_seconds["workload"] = solve["workload"]
         line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic",
+                "dtype": "f64 in/out; " + ("double-float (2 x f32) arithmetic" if head == "df32"
+                                           else "f64 arithmetic"),
+                "data": "synthetic",
                 "config": {"workload": prob.name, "elements": prob.E, "p": prob.p,
                            "fields": prob.n_fields, "n_dof": prob.n_dof,
                            "n_dof_incl_cm": prob.n_dof // prob.n_fields * (prob.n_fields + 1),
-                           "step": "R f64, J v f64, J^T w f64, J v f32, block-Jacobi apply "
-                                   "(FP32 inverses), c_m recovery, inner product",
+                           "value": "FP64-accurate J(u)v, one application, GDOF/s (" + head +
+                                    " arithmetic, the faster of f64 and df32)",
+                           "step": "R, J v, J^T w in f64 and in df32 arithmetic, J v f32, "
+                                   "block-Jacobi apply (FP32 inverses), c_m recovery, inner "
+                                   "product",
                            "applications_per_step": len(applications),
-                           "elements_per_block": dict(zip(["residual_f64", "jvp_f64", "vjp_f64",
-                                                           "jvp_f32", "residual_f32"], tuned)),
+                           "elements_per_block": {ar: dict(zip(["residual", "jvp", "vjp",
+                                                                "jvp_f32", "residual_f32"], t))
+                                                  for ar, t in tuned.items()},
                            "l2": "flushed between steps (512 MB write)"},
+                "jvp_GDOF_s": {"f64": n / (ms_jv["f64"] * 1e-3) / 1e9,
+                               "df32": n / (ms_jv["df32"] * 1e-3) / 1e9,
+                               "f32": per_op["jvp_f32"]["GDOF_s"]},
+                "hbm_frac": hbm_frac, "solve_seconds": solve_seconds,
+                "step_blend_GDOF_s": blend,
                 "ops": per_op, "roofline": roof, "roofline_hbm": roof_hbm, "solve": solve,
                 "batched_solve": batched,
                 "cpu_baseline": cb, "e2e": e2e,

@@ -38,7 +38,8 @@ typedef enum {
   ENP_ERR_OOM = 3,           /* device allocation failed */
   ENP_ERR_NONFINITE = 4,     /* a NaN/Inf was found where the call checks for one */
   ENP_ERR_NOT_CONVERGED = 5, /* an iterative solve stopped at its iteration limit */
-  ENP_ERR_TIMEOUT = 6,       /* a device-side loop hit its safety cap */
+  ENP_ERR_TIMEOUT = 6,       /* reserved: no call of this build returns it (no device-side
+                                waits; host-driven loops end at their iteration limits) */
   ENP_ERR_UNSUPPORTED = 7    /* a valid configuration this build does not implement */
 } enp_status;
 
@@ -141,6 +142,27 @@ enp_status enp_set_phi_app(enp_handle h, const double* phi_app);
 /* Physical coordinates of the volume Gauss points [E][q^dim][3] and of the
  * boundary-face Gauss points [NBF][q^(dim-1)][3] (device pointers, either NULL). */
 enp_status enp_quadrature_points(enp_handle h, double* xq, double* xbq);
+
+/* Arithmetic of the FP64 residual, J v and J^T w on hexahedral meshes
+ * (enp_residual, enp_jvp, enp_vjp, and the FP64 residual and J v inside the
+ * Newton and FGMRES solvers); vectors stay FP64 in and out either way. Block
+ * columns (enp_block_diagonal, FP64 block-Jacobi setup), dR/dtheta and the
+ * sweep's face terms always use the FP64 kernels.
+ *   ENP_ARITH_F64  (default): native FP64 arithmetic. GB300 issues 2 FP64
+ *                  fused multiply-adds per clock per SM, so this path is bound
+ *                  by the FP64 pipe.
+ *   ENP_ARITH_DF32: double-float arithmetic on the FP32 pipe (each value the
+ *                  unevaluated sum of two binary32 numbers, about 48 significant
+ *                  bits; error-free TwoSum/TwoProd building blocks). Agrees with
+ *                  the FP64 evaluation to about 1e-14 relative; magnitudes below
+ *                  2^-126 are flushed to zero and above 2^127 overflow.
+ * The paper computes in FP64 (Sec. 4.3); this is an implementation choice of
+ * the same operator. On 2D meshes the call is accepted and the operator stays
+ * FP64. Takes effect at the next call. Errors: INVALID_ARG. */
+#define ENP_ARITH_F64 0
+#define ENP_ARITH_DF32 1
+enp_status enp_set_arithmetic(enp_handle h, int arith);
+enp_status enp_get_arithmetic(enp_handle h, int* arith);
 
 /* r = R(u): the left-hand sides of Eq. NPDG (rows f = 1..m-1) and Eq. chargeDG
  * (rows f = 0), tested with every basis function. u, r: [batch][m][E][Np]. */
@@ -374,7 +396,9 @@ enp_status enp_param_vjp(enp_handle h, const double* u, const double* w, double*
  * device synchronisation. It needs no handle.
  *   out[b] = <x_b, y_b> for b < batch, x and y device arrays [batch][n],
  *   out a device array of batch doubles; asynchronous on `stream` (a
- *   cudaStream_t, may be 0). Same reduction order as enp_inner_product.
+ *   cudaStream_t, may be 0). The same kernels, grid and summation order as
+ *   enp_inner_product on a handle with n DOFs and `batch` operating points,
+ *   so the two give the same bits.
  * The partial sums live in one fixed array of ENP_NOALLOC_MAX_BATCH x 608
  * doubles in the library's static device memory, held by every GPU that loads
  * the library until the process exits. batch > ENP_NOALLOC_MAX_BATCH returns

@@ -22,7 +22,8 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libenp_dg.so")
-SOURCES = ["enp_api.cu", "op_f64.cu", "op_f32.cu", "enp_solver.cu", "enp_noalloc.cu"]
+SOURCES = ["enp_api.cu", "op_f64.cu", "op_f32.cu", "op_df.cu", "op_df_p1.cu", "op_df_p2.cu",
+           "op_df_p3.cu", "op_df_p4.cu", "enp_solver.cu", "enp_noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC",
               "--expt-relaxed-constexpr"]
@@ -141,6 +142,7 @@ class ContinuationStats(ctypes.Structure):
 
 
 BJ_F64, BJ_F32, BJ_BF16 = 0, 1, 2
+ARITH_F64, ARITH_DF32 = 0, 1
 
 _lib = None
 
@@ -178,6 +180,8 @@ _PROTOS = [
     ("enp_param_jacobian", _I, [_V, _V, _V]),
     ("enp_param_vjp", _I, [_V, _V, _V, _V]),
     ("enp_inner_product_noalloc", _I, [_V, _V, _LL, _I, _V, _V]),
+    ("enp_set_arithmetic", _I, [_V, _I]),
+    ("enp_get_arithmetic", _I, [_V, ctypes.POINTER(_I)]),
     ("enp_last_error", ctypes.c_char_p, [_V]),
 ]
 
@@ -292,6 +296,17 @@ class Operator:
     def _new(self, like_dtype):
         import torch
         return torch.empty(self.n, dtype=like_dtype, device="cuda")
+
+    def set_arithmetic(self, arith):
+        """Arithmetic of the FP64 operator on hexahedra: ARITH_F64 (native FP64)
+        or ARITH_DF32 (double-float on the FP32 pipe; R, J v and J^T w)."""
+        self._check(self._lib.enp_set_arithmetic(self.h, int(arith)))
+
+    @property
+    def arithmetic(self):
+        c = ctypes.c_int()
+        self._check(self._lib.enp_get_arithmetic(self.h, ctypes.byref(c)))
+        return c.value
 
     def set_sources(self, src=None, dirichlet=None):
         import torch

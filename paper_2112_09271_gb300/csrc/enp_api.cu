@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/enp_dg.h"
@@ -306,6 +307,8 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
   P.batch_stride = (long long)P.NF * P.E * P.Np;
   fill_phys<double>(P, P.pd);
   fill_phys<float>(P, P.pf);
+  fill_phys<enp::df>(P, P.pdf);
+  P.arith = enp::kArithF64;
   P.batch = disc->batch;
   P.n_theta = 2 * P.m + 3;
   h->batch = disc->batch;
@@ -326,8 +329,18 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
       e = cudaMemcpy(h->d_xvf[a], cf.data(), sizeof(float) * (P.ne[a] + 1), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload coords (FP32)"); enp_dg_destroy(h); return s; }
     P.xvf[a] = h->d_xvf[a];
+    std::vector<float2> cd(P.ne[a] + 1);
+    for (int i = 0; i <= P.ne[a]; ++i) {
+      const enp::df x(mesh->coords[a][i]);
+      cd[i] = make_float2(x.hi, x.lo);
+    }
+    e = cudaMalloc(&h->d_xvdf[a], sizeof(float2) * (P.ne[a] + 1));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->d_xvdf[a], cd.data(), sizeof(float2) * (P.ne[a] + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload coords (double-float)"); enp_dg_destroy(h); return s; }
+    P.xvdf[a] = h->d_xvdf[a];
   }
-  for (int a = dim; a < 3; ++a) { P.xv[a] = nullptr; P.xvf[a] = nullptr; }
+  for (int a = dim; a < 3; ++a) { P.xv[a] = nullptr; P.xvf[a] = nullptr; P.xvdf[a] = nullptr; }
   e = cudaMalloc(&h->d_btag, tags.size());
   if (e == cudaSuccess) e = cudaMemcpy(h->d_btag, tags.data(), tags.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_tab, sizeof(Tables));
@@ -352,6 +365,7 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
   }
   e = enp::prepare_tables<double>(P.p, h->htab);
   if (e == cudaSuccess) e = enp::prepare_tables<float>(P.p, h->htab);
+  if (e == cudaSuccess && dim == 3) e = enp::prepare_tables_df(P.p, h->htab);
   if (e != cudaSuccess) { enp_status s = cuda_fail(h, e, "upload constant tables"); enp_dg_destroy(h); return s; }
   *out = h;
   return ENP_OK;
@@ -360,7 +374,7 @@ enp_status enp_dg_create(enp_handle* out, const enp_mesh_desc* mesh, const enp_p
 enp_status enp_dg_destroy(enp_handle h) {
   if (!h) return ENP_ERR_INVALID_ARG;
   enp_solver_free(h);
-  for (int a = 0; a < 3; ++a) { cudaFree(h->d_xv[a]); cudaFree(h->d_xvf[a]); }
+  for (int a = 0; a < 3; ++a) { cudaFree(h->d_xv[a]); cudaFree(h->d_xvf[a]); cudaFree(h->d_xvdf[a]); }
   cudaFree(h->d_btag);
   cudaFree(h->d_tab);
   cudaFree(h->d_src);
@@ -524,8 +538,17 @@ enp_status enp_param_jacobian(enp_handle h, const double* u, double* dRdtheta) {
 // each operator mode on this handle's mesh (three launches each, CUDA events)
 // and keep the fastest. The block-column pass follows the J v choice.
 template <class R>
-static cudaError_t tune_mode(enp_handle h, int mode, R* u, R* v, R* out, int* chosen) {
-  const OpParams& P = h->prm;
+static cudaError_t tune_launch(int mode, const OpParams& P, const Tables* t, enp::io_t<R>* u,
+                               enp::io_t<R>* v, enp::io_t<R>* out, cudaStream_t s) {
+  if constexpr (std::is_same<R, enp::df>::value) return enp::launch_op_df(mode, P, u, v, out, 1, s);
+  else return enp::launch_op<R>(mode, P, t, u, v, out, 1, s);
+}
+
+template <class R>
+static cudaError_t tune_mode(enp_handle h, int mode, enp::io_t<R>* u, enp::io_t<R>* v,
+                             enp::io_t<R>* out, int* chosen) {
+  OpParams P = h->prm;
+  P.arith = enp::kArithF64;  // launch_op<double> then runs the FP64 kernels themselves
   const int mx = enp::eb3d_max<R>(P.p, P.NF, mode);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -535,10 +558,10 @@ static cudaError_t tune_mode(enp_handle h, int mode, R* u, R* v, R* out, int* ch
   cudaError_t err = cudaSuccess;
   for (int eb = 1; eb <= mx && err == cudaSuccess; ++eb) {
     enp::eb3d_set<R>(P.p, P.NF, mode, eb);
-    err = enp::launch_op<R>(mode, P, h->d_tab, u, v, out, 1, h->stream);
+    err = tune_launch<R>(mode, P, h->d_tab, u, v, out, h->stream);
     if (err != cudaSuccess) break;
     cudaEventRecord(e0, h->stream);
-    for (int r = 0; r < 3; ++r) enp::launch_op<R>(mode, P, h->d_tab, u, v, out, 1, h->stream);
+    for (int r = 0; r < 3; ++r) tune_launch<R>(mode, P, h->d_tab, u, v, out, h->stream);
     cudaEventRecord(e1, h->stream);
     err = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -566,15 +589,35 @@ enp_status enp_autotune(enp_handle h, int* chosen) {
   o = v + n;
   cudaMemsetAsync(u, 0, 3 * n * sizeof(double), h->stream);
   int c[5] = {0, 0, 0, 0, 0};
-  e = tune_mode<double>(h, enp::kResidual, u, v, o, &c[0]);
-  if (e == cudaSuccess) e = tune_mode<double>(h, enp::kJvp, u, v, o, &c[1]);
-  if (e == cudaSuccess) e = tune_mode<double>(h, enp::kVjp, u, v, o, &c[2]);
+  if (h->prm.arith == enp::kArithDF) {  // the FP64-accurate operator runs in double-float
+    e = tune_mode<enp::df>(h, enp::kResidual, u, v, o, &c[0]);
+    if (e == cudaSuccess) e = tune_mode<enp::df>(h, enp::kJvp, u, v, o, &c[1]);
+    if (e == cudaSuccess) e = tune_mode<enp::df>(h, enp::kVjp, u, v, o, &c[2]);
+  } else {
+    e = tune_mode<double>(h, enp::kResidual, u, v, o, &c[0]);
+    if (e == cudaSuccess) e = tune_mode<double>(h, enp::kJvp, u, v, o, &c[1]);
+    if (e == cudaSuccess) e = tune_mode<double>(h, enp::kVjp, u, v, o, &c[2]);
+  }
   if (e == cudaSuccess) e = tune_mode<float>(h, enp::kJvp, (float*)u, (float*)v, (float*)o, &c[3]);
   if (e == cudaSuccess) e = tune_mode<float>(h, enp::kResidual, (float*)u, (float*)v, (float*)o, &c[4]);
   cudaFree(u);
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
   if (chosen)
     for (int i = 0; i < 5; ++i) chosen[i] = c[i];
+  return ENP_OK;
+}
+
+enp_status enp_set_arithmetic(enp_handle h, int arith) {
+  if (!h) return ENP_ERR_INVALID_ARG;
+  if (arith != ENP_ARITH_F64 && arith != ENP_ARITH_DF32)
+    return fail(h, ENP_ERR_INVALID_ARG, "arith must be ENP_ARITH_F64 or ENP_ARITH_DF32");
+  h->prm.arith = (arith == ENP_ARITH_DF32 && h->prm.dim == 3) ? enp::kArithDF : enp::kArithF64;
+  return ENP_OK;
+}
+
+enp_status enp_get_arithmetic(enp_handle h, int* arith) {
+  if (!h || !arith) return ENP_ERR_INVALID_ARG;
+  *arith = h->prm.arith == enp::kArithDF ? ENP_ARITH_DF32 : ENP_ARITH_F64;
   return ENP_OK;
 }
 

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "enp_df.cuh"
+
 namespace enp {
 
 constexpr int kMaxSpecies = 4;
@@ -24,6 +26,10 @@ constexpr int kMaxQ = kMaxP + 2;
 enum OpMode : int { kResidual = 0, kJvp = 1, kVjp = 2, kBlockCol = 3, kParam = 4 };
 
 enum FaceTag : int { kInterior = 0, kWall = 1, kInlet = 2, kOutlet = 3, kDirichlet = 4, kElectrode0 = 5 };
+
+// Arithmetic of the FP64-accurate operator (R, J v, J^T w, block columns,
+// dR/dtheta on hexahedra): native FP64, or double-float on the FP32 pipe.
+enum Arith : int { kArithF64 = 0, kArithDF = 1 };
 
 // Physical coefficients in the arithmetic type T of a kernel, converted once on
 // the host so that the pointwise code does no FP64 conversions in FP32 kernels.
@@ -49,6 +55,7 @@ struct OpParams {
   int side_off[7];
   const double* xv[3];        // device: per-axis vertex coordinates
   const float* xvf[3];        // the same in FP32, for FP32 kernels
+  const float2* xvdf[3];      // the same as double-float pairs (hi, lo)
   const uint8_t* btag;        // device: boundary tags, side-major
   // physics (Sec. 2): mu_k = D_k / RT; migration coefficient z_k mu_k F;
   // a_k = F z_k (D_k - D_m); kappa_k so that kappa = sum_k kappa_k c_k (Eq. charge2)
@@ -70,6 +77,8 @@ struct OpParams {
   long long batch_stride;     // entries per operating point (NF * E * Np)
   PhysT<double> pd;           // the coefficients above, in each kernel arithmetic type
   PhysT<float> pf;
+  PhysT<df> pdf;
+  int arith;                  // Arith of the FP64-accurate operator
   double RT;
   int batch;                  // operating points
   int n_theta;                // parameters of dR/dtheta: D_1..D_m, c_in_1..c_in_{m-1}, phi_app_0..3
@@ -87,6 +96,11 @@ template <class R> __host__ __device__ __forceinline__ const PhysT<R>& phys(cons
 template <class R> __device__ __forceinline__ R vertex(const OpParams& p, int a, int i);
 template <> __device__ __forceinline__ double vertex<double>(const OpParams& p, int a, int i) { return p.xv[a][i]; }
 template <> __device__ __forceinline__ float vertex<float>(const OpParams& p, int a, int i) { return p.xvf[a][i]; }
+template <> __device__ __forceinline__ df vertex<df>(const OpParams& p, int a, int i) {
+  const float2 c = p.xvdf[a][i];
+  return df(c.x, c.y);
+}
+template <> __host__ __device__ __forceinline__ const PhysT<df>& phys<df>(const OpParams& p) { return p.pdf; }
 template <> __host__ __device__ __forceinline__ const PhysT<double>& phys<double>(const OpParams& p) { return p.pd; }
 template <> __host__ __device__ __forceinline__ const PhysT<float>& phys<float>(const OpParams& p) { return p.pf; }
 
@@ -124,6 +138,8 @@ template <class R> __device__ __forceinline__ Tan<R> absv(Tan<R> x) {
   R s = x.v > R(0) ? R(1) : (x.v < R(0) ? R(-1) : R(0));  // d|x|/dx = 0 at x = 0
   return Tan<R>(absv(x.v), s * x.d);
 }
+__device__ __forceinline__ double sqrtv(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrtv(float x) { return sqrtf(x); }
 __device__ __forceinline__ double expv(double x) { return exp(x); }
 __device__ __forceinline__ float expv(float x) { return expf(x); }
 template <class R> __device__ __forceinline__ Tan<R> expv(Tan<R> x) { R e = expv(x.v); return Tan<R>(e, e * x.d); }

@@ -9,9 +9,28 @@ namespace enp {
 // Launch the operator kernel for (dim, p, NF) chosen at run time.
 // mode: 0 residual, 1 J v, 2 J^T w. Returns cudaErrorInvalidConfiguration if the
 // shape is not compiled.
+// R = double, float or df (double-float arithmetic on FP64 vectors: io_t<df> =
+// double). With prm.arith == kArithDF, launch_op<double> on hexahedra runs the
+// double-float kernels.
 template <class R>
-cudaError_t launch_op(int mode, const OpParams& prm, const Tables* tabs, const R* u, const R* v,
-                      R* out, int batch, cudaStream_t stream);
+cudaError_t launch_op(int mode, const OpParams& prm, const Tables* tabs, const io_t<R>* u,
+                      const io_t<R>* v, io_t<R>* out, int batch, cudaStream_t stream);
+
+// The double-float hexahedral operator: R, J v and J^T w (modes 0..2) of
+// degree prm.p (op_df.cu), compiled one degree per translation unit
+// (op_df_p1.cu .. op_df_p4.cu), each with its own constant tables.
+cudaError_t launch_op_df(int mode, const OpParams& prm, const double* u, const double* v,
+                         double* out, int batch, cudaStream_t stream);
+cudaError_t prepare_tables_df(int p, const Tables& t);
+#define ENP_DF_DECL(PP)                                                                      \
+  cudaError_t launch_df_p##PP(int mode, const OpParams& prm, const double* u, const double* v, \
+                              double* out, int batch, cudaStream_t s);                        \
+  cudaError_t upload_tables_df_p##PP(const Tables& t);
+ENP_DF_DECL(1)
+ENP_DF_DECL(2)
+ENP_DF_DECL(3)
+ENP_DF_DECL(4)
+#undef ENP_DF_DECL
 
 bool shape_supported(int dim, int p, int nf);
 
@@ -42,6 +61,7 @@ struct enp_dg {
   enp::Tables* d_tab = nullptr;
   double* d_xv[3] = {nullptr, nullptr, nullptr};
   float* d_xvf[3] = {nullptr, nullptr, nullptr};
+  float2* d_xvdf[3] = {nullptr, nullptr, nullptr};
   uint8_t* d_btag = nullptr;
   double* d_src = nullptr;
   double* d_dir = nullptr;

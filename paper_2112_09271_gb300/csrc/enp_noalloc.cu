@@ -5,9 +5,10 @@
 // application that owns all device memory through its own pool and forbids
 // other allocations, or a latency-critical loop that cannot afford cudaMalloc's
 // cost and implicit device synchronisation. For them, enp_inner_product_noalloc
-// computes the same reduction with the partial sums in the fixed array below,
-// which lives in the library's static device memory: every GPU that loads the
-// library holds it (ENP_NOALLOC_MAX_BATCH x 608 doubles) until the process exits.
+// computes the same reduction (same kernels, grid and summation order, hence
+// the same bits) with the partial sums in the fixed array below, which lives in
+// the library's static device memory: every GPU that loads the library holds
+// it (ENP_NOALLOC_MAX_BATCH x 608 doubles) until the process exits.
 //
 // Host code must not pass `g_noalloc_partials` itself to a kernel: in host code
 // that name is a host-side stand-in, not a device address. The device address
@@ -16,56 +17,16 @@
 #include <mutex>
 
 #include "../../include/enp_dg.h"
+#include "enp_reduce.cuh"
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kBlocks = 608;  // 4 blocks per SM on 152 SMs: partials per operating point
 constexpr int kMaxDevices = 64;
 
-static __device__ __align__(256) double g_noalloc_partials[ENP_NOALLOC_MAX_BATCH * kBlocks];
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// One partial sum of <x_b, y_b> per thread block, in a fixed order: a
-// grid-stride loop per thread, a shuffle tree per warp, then the warps in order.
-// Every slot read later by the finishing kernel is written here first, so the
-// array needs no clearing between calls.
-__global__ void __launch_bounds__(kThreads)
-dot_partial_noalloc(const double* __restrict__ x, const double* __restrict__ y, long long n,
-                    double* __restrict__ part) {
-  __shared__ double red[kThreads / 32];
-  const int b = blockIdx.y;
-  const double* xb = x + (long long)b * n;
-  const double* yb = y + (long long)b * n;
-  double acc = 0.0;
-  for (long long k = blockIdx.x * (long long)kThreads + threadIdx.x; k < n;
-       k += (long long)gridDim.x * kThreads)
-    acc += xb[k] * yb[k];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  acc = warp_sum(acc);
-  if (lane == 0) red[warp] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
-    part[(long long)b * gridDim.x + blockIdx.x] = s;
-  }
-}
-
-// out[b] = sum of the partials of operating point b, in block order.
-__global__ void dot_finish_noalloc(const double* __restrict__ part, int nparts,
-                                   double* __restrict__ out) {
-  const int b = blockIdx.x;
-  double s = 0.0;
-  for (int k = threadIdx.x; k < nparts; k += 32) s += part[(long long)b * nparts + k];
-  s = warp_sum(s);
-  if (threadIdx.x == 0) out[b] = s;
-}
+// One partial per reduction block and operating point: the same reduction
+// (kernels, grid and order) as enp_inner_product, whose partials live in
+// handle-owned scratch.
+static __device__ __align__(256) double g_noalloc_partials[ENP_NOALLOC_MAX_BATCH * enp::kRedBlocks];
 
 std::mutex g_mutex;
 double* g_ptr[kMaxDevices] = {nullptr};
@@ -96,7 +57,15 @@ extern "C" enp_status enp_inner_product_noalloc(const double* x, const double* y
   enp_status st = scratch_on_current_device(&part);
   if (st != ENP_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  dot_partial_noalloc<<<dim3(kBlocks, batch), kThreads, 0, s>>>(x, y, n, part);
-  dot_finish_noalloc<<<batch, 32, 0, s>>>(part, kBlocks, out);
+  // every partial slot the finishing kernel reads is written first by the
+  // partial kernel of the same call: the array needs no clearing
+  const int W = vec_width<double>(n, 0, x, y);
+  const int nb = red_blocks(n, W);
+  const dim3 g(nb, batch);
+  if (W == 1)
+    enp::multidot_partial<double, 1><<<g, enp::kRedThreads, 0, s>>>(x, 0, 1, y, n, n, part);
+  else
+    enp::multidot_partial<double, 2><<<g, enp::kRedThreads, 0, s>>>(x, 0, 1, y, n, n, part);
+  enp::finish_partials<<<batch, 32, 0, s>>>(part, nb, batch, out);
   return cudaGetLastError() == cudaSuccess ? ENP_OK : ENP_ERR_CUDA;
 }

@@ -2,15 +2,43 @@
 // For kBlockCol, `batch` is the number of block columns (NF * Np): grid.y runs
 // over the columns.
 #pragma once
+#include <mutex>
+
 #include "enp_internal.h"
 #include "enp_operator.cuh"
 #include "enp_operator3d.cuh"
 
 namespace enp {
 
-// Elements per block of the hexahedral kernel, per (p, fields, mode) of this
-// translation unit's arithmetic type; 0 = the default (shared memory near 96 KB).
-static int g_eb3d[kMaxP + 1][4][5] = {};
+// The dynamic shared-memory limit of a kernel is a per-device attribute: each
+// launch site keeps, per device, whether it has raised the limit (thread-safe).
+struct SmemAttr {
+  std::mutex mu;
+  bool done[64] = {};
+};
+template <class K>
+static cudaError_t raise_smem_limit(SmemAttr& st, K kern, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64)
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  std::lock_guard<std::mutex> g(st.mu);
+  if (st.done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) st.done[dev] = true;
+  return e;
+}
+
+// Elements per block of the hexahedral kernel, per (p, fields, mode) and
+// arithmetic type; 0 = the default (shared memory near 96 KB). One table per
+// type for the whole library (the double-float kernels span several
+// translation units).
+template <class R>
+inline int (&eb3d_table())[kMaxP + 1][4][5] {
+  static int t[kMaxP + 1][4][5] = {};
+  return t;
+}
 
 template <int P, int NF, int MODE, class R>
 static int default_eb() {
@@ -33,22 +61,18 @@ static int max_eb() {
 
 // Hexahedra: the thread-per-pencil kernel with EB elements per block.
 template <int P, int NF, int MODE, class R>
-static cudaError_t launch_3d(const OpParams& prm, const R* u, const R* v, R* out, int batch,
-                             cudaStream_t stream) {
+static cudaError_t launch_3d(const OpParams& prm, const io_t<R>* u, const io_t<R>* v, io_t<R>* out,
+                             int batch, cudaStream_t stream) {
   constexpr int NT = tpe3d<P, R>();
   using S3 = Smem3<P, NF, MODE, NT>;
   constexpr size_t per_el = (size_t)S3::total * sizeof(R);
-  int eb = g_eb3d[P][NF][MODE];
+  int eb = eb3d_table<R>()[P][NF][MODE];
   if (eb <= 0) eb = default_eb<P, NF, MODE, R>();
   const size_t smem = (size_t)eb * per_el;
   auto kern = op3d_kernel<P, NF, MODE, R>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)max_eb<P, NF, MODE, R>() * per_el));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemAttr attr;
+  cudaError_t ea = raise_smem_limit(attr, kern, (size_t)max_eb<P, NF, MODE, R>() * per_el);
+  if (ea != cudaSuccess) return ea;
   if constexpr (S3::kFB) {
     // the faces first: each face once, both sides' terms into the face buffer
     constexpr int TF = tpf3d<P, R>();
@@ -56,13 +80,9 @@ static cudaError_t launch_3d(const OpParams& prm, const R* u, const R* v, R* out
     constexpr int fpb_s = (int)((96 * 1024) / per_face);
     constexpr int fpb = fpb_s < 1 ? 1 : (fpb_s * TF > kMaxThreads3D ? kMaxThreads3D / TF : fpb_s);
     auto fk = face3d_kernel<P, NF, MODE, R>;
-    static bool fconfigured = false;
-    if (!fconfigured) {
-      cudaError_t e = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(fpb * per_face));
-      if (e != cudaSuccess) return e;
-      fconfigured = true;
-    }
+    static SmemAttr fattr;
+    cudaError_t ef = raise_smem_limit(fattr, fk, fpb * per_face);
+    if (ef != cudaSuccess) return ef;
     const long long nf = prm.foff[3];
     dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
     fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v, -1, 0);
@@ -73,47 +93,55 @@ static cudaError_t launch_3d(const OpParams& prm, const R* u, const R* v, R* out
 }
 
 template <int DIM, int P, int NF, int MODE, class R>
-static cudaError_t launch_one(const OpParams& prm, const Tables* tabs, const R* u, const R* v,
-                              R* out, int batch, cudaStream_t stream) {
+static cudaError_t launch_one(const OpParams& prm, const Tables* tabs, const io_t<R>* u,
+                              const io_t<R>* v, io_t<R>* out, int batch, cudaStream_t stream) {
   if constexpr (DIM == 3) {
     (void)tabs;
     return launch_3d<P, NF, MODE, R>(prm, u, v, out, batch, stream);
-  }
+  } else {
   using M = WarpSmem<DIM, P, NF, MODE>;
   constexpr size_t per_warp = (size_t)M::total * sizeof(R);
   constexpr int WPB = per_warp * 4 <= 96 * 1024 ? 4 : (per_warp * 2 <= 110 * 1024 ? 2 : 1);
   const size_t smem = ((size_t)TabSmem<P>::total + (size_t)WPB * M::total) * sizeof(R);
   auto kern = op_kernel<DIM, P, NF, MODE, WPB, R>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemAttr attr;
+  cudaError_t ea = raise_smem_limit(attr, kern, smem);
+  if (ea != cudaSuccess) return ea;
   dim3 grid((prm.E + WPB - 1) / WPB, batch);
   kern<<<grid, WPB * 32, smem, stream>>>(prm, tabs, u, v, out);
   return cudaGetLastError();
+  }
 }
 
 template <int DIM, int P, int NF, class R>
-static cudaError_t launch_mode(int mode, const OpParams& prm, const Tables* t, const R* u,
-                               const R* v, R* out, int batch, cudaStream_t s) {
-  switch (mode) {
-    case kResidual: return launch_one<DIM, P, NF, kResidual, R>(prm, t, u, v, out, batch, s);
-    case kJvp: return launch_one<DIM, P, NF, kJvp, R>(prm, t, u, v, out, batch, s);
-    case kVjp: return launch_one<DIM, P, NF, kVjp, R>(prm, t, u, v, out, batch, s);
-    case kBlockCol: return launch_one<DIM, P, NF, kBlockCol, R>(prm, t, u, v, out, batch, s);
-    case kParam:
-      if constexpr (DIM == 3) return launch_one<DIM, P, NF, kParam, R>(prm, t, u, v, out, batch, s);
-      return cudaErrorNotSupported;
+static cudaError_t launch_mode(int mode, const OpParams& prm, const Tables* t, const io_t<R>* u,
+                               const io_t<R>* v, io_t<R>* out, int batch, cudaStream_t s) {
+  if constexpr (std::is_same<R, df>::value) {
+    // double-float: the residual, J v and J^T w (block columns and dR/dtheta
+    // stay with the FP64 kernels)
+    switch (mode) {
+      case kResidual: return launch_one<DIM, P, NF, kResidual, R>(prm, t, u, v, out, batch, s);
+      case kJvp: return launch_one<DIM, P, NF, kJvp, R>(prm, t, u, v, out, batch, s);
+      case kVjp: return launch_one<DIM, P, NF, kVjp, R>(prm, t, u, v, out, batch, s);
+    }
+    return cudaErrorNotSupported;
+  } else {
+    switch (mode) {
+      case kResidual: return launch_one<DIM, P, NF, kResidual, R>(prm, t, u, v, out, batch, s);
+      case kJvp: return launch_one<DIM, P, NF, kJvp, R>(prm, t, u, v, out, batch, s);
+      case kVjp: return launch_one<DIM, P, NF, kVjp, R>(prm, t, u, v, out, batch, s);
+      case kBlockCol: return launch_one<DIM, P, NF, kBlockCol, R>(prm, t, u, v, out, batch, s);
+      case kParam:
+        if constexpr (DIM == 3) return launch_one<DIM, P, NF, kParam, R>(prm, t, u, v, out, batch, s);
+        return cudaErrorNotSupported;
+    }
+    return cudaErrorInvalidValue;
   }
-  return cudaErrorInvalidValue;
 }
 
 template <int DIM, int P, class R>
-static cudaError_t launch_nf(int mode, const OpParams& prm, const Tables* t, const R* u,
-                             const R* v, R* out, int batch, cudaStream_t s) {
+static cudaError_t launch_nf(int mode, const OpParams& prm, const Tables* t, const io_t<R>* u,
+                             const io_t<R>* v, io_t<R>* out, int batch, cudaStream_t s) {
   if (prm.NF == 2) return launch_mode<DIM, P, 2, R>(mode, prm, t, u, v, out, batch, s);
   if (prm.NF == 3) return launch_mode<DIM, P, 3, R>(mode, prm, t, u, v, out, batch, s);
   return cudaErrorInvalidConfiguration;
@@ -129,13 +157,9 @@ static cudaError_t launch_face_plane_pn(const OpParams& prm, const R* u, const R
   constexpr int fpb_s = (int)((96 * 1024) / per_face);
   constexpr int fpb = fpb_s < 1 ? 1 : (fpb_s * TF > kMaxThreads3D ? kMaxThreads3D / TF : fpb_s);
   auto fk = face3d_kernel<P, NF, kJvp, R>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(fpb * per_face));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemAttr attr;
+  cudaError_t ea = raise_smem_limit(attr, fk, fpb * per_face);
+  if (ea != cudaSuccess) return ea;
   const long long nf = (long long)prm.ne[a == 0 ? 1 : 0] * prm.ne[a == 2 ? 1 : 2];
   dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
   fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v, a, ia);
@@ -160,7 +184,8 @@ cudaError_t launch_face_plane(const OpParams& prm, const R* u, const R* v, int b
 // (p, fields, mode), and setting the value launches use (0 = default).
 template <class R>
 int eb3d_max(int p, int nf, int mode) {
-#define ENP_EBM(PP, NFF, MM) if (p == PP && nf == NFF && mode == MM) return max_eb<PP, NFF, MM, R>();
+#define ENP_EBM(PP, NFF, MM) \
+  if (p == PP && nf == NFF && mode == MM && (MM <= kVjp || !std::is_same<R, df>::value)) return max_eb<PP, NFF, MM, R>();
 #define ENP_EBM_P(PP) ENP_EBM(PP, 2, 0) ENP_EBM(PP, 2, 1) ENP_EBM(PP, 2, 2) ENP_EBM(PP, 2, 3) ENP_EBM(PP, 2, 4) \
   ENP_EBM(PP, 3, 0) ENP_EBM(PP, 3, 1) ENP_EBM(PP, 3, 2) ENP_EBM(PP, 3, 3) ENP_EBM(PP, 3, 4)
   ENP_EBM_P(1) ENP_EBM_P(2) ENP_EBM_P(3) ENP_EBM_P(4)
@@ -171,12 +196,12 @@ int eb3d_max(int p, int nf, int mode) {
 
 template <class R>
 void eb3d_set(int p, int nf, int mode, int eb) {
-  if (p >= 1 && p <= kMaxP && nf >= 2 && nf <= 3 && mode >= 0 && mode <= 4) g_eb3d[p][nf][mode] = eb;
+  if (p >= 1 && p <= kMaxP && nf >= 2 && nf <= 3 && mode >= 0 && mode <= 4) eb3d_table<R>()[p][nf][mode] = eb;
 }
 
 template <class R>
 int eb3d_get(int p, int nf, int mode) {
-  if (p >= 1 && p <= kMaxP && nf >= 2 && nf <= 3 && mode >= 0 && mode <= 4) return g_eb3d[p][nf][mode];
+  if (p >= 1 && p <= kMaxP && nf >= 2 && nf <= 3 && mode >= 0 && mode <= 4) return eb3d_table<R>()[p][nf][mode];
   return 0;
 }
 
@@ -188,8 +213,13 @@ cudaError_t prepare_tables(int p, const Tables& t) {
 }
 
 template <class R>
-cudaError_t launch_op(int mode, const OpParams& prm, const Tables* t, const R* u, const R* v,
-                      R* out, int batch, cudaStream_t s) {
+cudaError_t launch_op(int mode, const OpParams& prm, const Tables* t, const io_t<R>* u,
+                      const io_t<R>* v, io_t<R>* out, int batch, cudaStream_t s) {
+  if constexpr (std::is_same<R, double>::value) {
+    // R, J v and J^T w in double-float arithmetic on hexahedra
+    if (prm.arith == kArithDF && prm.dim == 3 && mode <= kVjp)
+      return launch_op_df(mode, prm, u, v, out, batch, s);
+  }
   if (prm.dim == 3) {
     switch (prm.p) {
       case 1: return launch_nf<3, 1, R>(mode, prm, t, u, v, out, batch, s);
@@ -197,7 +227,8 @@ cudaError_t launch_op(int mode, const OpParams& prm, const Tables* t, const R* u
       case 3: return launch_nf<3, 3, R>(mode, prm, t, u, v, out, batch, s);
       case 4: return launch_nf<3, 4, R>(mode, prm, t, u, v, out, batch, s);
     }
-  } else if (prm.dim == 2) {
+  }
+  if (prm.dim == 2) {
     switch (prm.p) {
       case 1: return launch_nf<2, 1, R>(mode, prm, t, u, v, out, batch, s);
       case 2: return launch_nf<2, 2, R>(mode, prm, t, u, v, out, batch, s);
@@ -208,3 +239,13 @@ cudaError_t launch_op(int mode, const OpParams& prm, const Tables* t, const R* u
 }
 
 }  // namespace enp
+
+// The double-float hexahedral kernels of one degree PP (op_df_pPP.cu): the
+// launcher and the upload of that translation unit's constant tables.
+#define ENP_DF_DEGREE(PP)                                                                    \
+  cudaError_t enp::launch_df_p##PP(int mode, const OpParams& prm, const double* u,             \
+                                   const double* v, double* out, int batch, cudaStream_t s) { \
+    if (prm.dim != 3) return cudaErrorInvalidConfiguration;                                   \
+    return launch_nf<3, PP, df>(mode, prm, nullptr, u, v, out, batch, s);                     \
+  }                                                                                           \
+  cudaError_t enp::upload_tables_df_p##PP(const Tables& t) { return upload_const_tables(PP, t); }

@@ -20,6 +20,7 @@ namespace enp {
 constexpr int kTabSz = 96;  // per degree: B (Q*N), Dq (Q*Q), dL (2N), wq (Q), xq (Q)
 static __constant__ double c_tabd[kMaxP + 1][kTabSz];
 static __constant__ float c_tabf[kMaxP + 1][kTabSz];
+static __constant__ float2 c_tabdf[kMaxP + 1][kTabSz];   // (hi, lo) double-float pairs
 
 // Upload the tables of degree p to this translation unit's constant banks on
 // the current device.
@@ -27,21 +28,28 @@ static inline cudaError_t upload_const_tables(int p, const Tables& t) {
   const int n = p + 1, q = p + 2;
   double d[kTabSz] = {0};
   float f[kTabSz] = {0};
+  float2 w[kTabSz];
   int o = 0;
   for (int i = 0; i < q * n; ++i) d[o++] = t.B[i];
   for (int i = 0; i < q * q; ++i) d[o++] = t.Dq[i];
   for (int i = 0; i < 2 * n; ++i) d[o++] = t.dL[i];
   for (int i = 0; i < q; ++i) d[o++] = t.wq[i];
   for (int i = 0; i < q; ++i) d[o++] = t.xq[i];
-  for (int i = 0; i < kTabSz; ++i) f[i] = (float)d[i];
+  for (int i = 0; i < kTabSz; ++i) {
+    f[i] = (float)d[i];
+    const df x(d[i]);
+    w[i] = make_float2(x.hi, x.lo);
+  }
   cudaError_t e = cudaMemcpyToSymbol(c_tabd, d, sizeof(d), sizeof(d) * p);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tabf, f, sizeof(f), sizeof(f) * p);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tabdf, w, sizeof(w), sizeof(w) * p);
   return e;
 }
 
 template <int P, class R>
 __device__ __forceinline__ R ctab(int i) {
   if constexpr (std::is_same<R, double>::value) return c_tabd[P][i];
+  else if constexpr (std::is_same<R, df>::value) return df(c_tabdf[P][i].x, c_tabdf[P][i].y);
   else return c_tabf[P][i];
 }
 template <int P> struct TabOff {
@@ -88,15 +96,44 @@ __device__ __forceinline__ void pencil(const R* __restrict__ in, R* __restrict__
     for (int k = 0; k < COLS; ++k) x[k] = src[k * IS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
-      R acc = ACC ? dst[r * OS] : R(0);
+      if constexpr (std::is_same<R, df>::value) {
+        // double-float dot product: the leading parts summed with TwoSum, the
+        // product errors, cross terms and sum errors gathered in one binary32
+        // term, one renormalisation per output
+        float s = 0.f, t = 0.f;
+        if (ACC) { s = dst[r * OS].hi; t = dst[r * OS].lo; }
 #pragma unroll
-      for (int k = 0; k < COLS; ++k) {
-        int idx;
-        if (TAB == 0) idx = T::B + (TRANS ? k * T::N + r : r * T::N + k);
-        else idx = T::Dq + (TRANS ? k * T::Q + r : r * T::Q + k);
-        acc = mad(ctab<P, R>(idx), x[k], acc);
+        for (int k = 0; k < COLS; ++k) {
+          int idx;
+          if (TAB == 0) idx = T::B + (TRANS ? k * T::N + r : r * T::N + k);
+          else idx = T::Dq + (TRANS ? k * T::Q + r : r * T::Q + k);
+          const float2 m = c_tabdf[P][idx];
+          const float p = __fmul_rn(m.x, x[k].hi);
+          float e = __fmaf_rn(m.x, x[k].hi, -p);
+          e = __fmaf_rn(m.x, x[k].lo, e);
+          e = __fmaf_rn(m.y, x[k].hi, e);
+          if (!ACC && k == 0) {
+            s = p;
+            t = e;
+          } else {
+            float s2, err;
+            two_sum(s, p, s2, err);
+            s = s2;
+            t = __fadd_rn(t, __fadd_rn(err, e));
+          }
+        }
+        dst[r * OS] = fast_two_sum(s, t);
+      } else {
+        R acc = ACC ? dst[r * OS] : R(0);
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) {
+          int idx;
+          if (TAB == 0) idx = T::B + (TRANS ? k * T::N + r : r * T::N + k);
+          else idx = T::Dq + (TRANS ? k * T::Q + r : r * T::Q + k);
+          acc = mad(ctab<P, R>(idx), x[k], acc);
+        }
+        dst[r * OS] = acc;
       }
-      dst[r * OS] = acc;
     }
     c += dc;
     pp += dp;
@@ -162,7 +199,7 @@ __device__ PhysT<Tan<R>> seed_phys(const PhysT<R>& p, int m, int j) {
 template <int P, class R>
 __host__ __device__ constexpr int tpe3d() {
   if constexpr (std::is_same<R, double>::value) return (P + 2) * (P + 2);
-  else return P <= 1 ? 32 : (P == 2 ? 64 : 128);
+  else return P <= 1 ? 32 : (P == 2 ? 64 : 128);   // FP32 and double-float: the FP32 pipe
 }
 
 template <int P, int NF, int MODE, int NT>
@@ -208,8 +245,8 @@ constexpr int kMaxThreads3D = 256;
 
 template <int P, int NF, int MODE, class R>
 __global__ void __launch_bounds__(kMaxThreads3D)
-op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v,
-            R* __restrict__ out) {
+op3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __restrict__ v,
+            io_t<R>* __restrict__ out) {
   using S = Smem3<P, NF, MODE, tpe3d<P, R>()>;
   using TO = TabOff<P>;
   constexpr int N = S::N, Q = S::Q, NN = S::NN, NQ = S::NQ, FN = S::FN, FQ = S::FQ;
@@ -249,15 +286,15 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
     sc[a] = R(2) / h[a];
     diag2 += h[a] * h[a];
   }
-  const R diag = sqrt(diag2);
+  const R diag = sqrtv(diag2);
   const R detJ = R(0.125) * h[0] * h[1] * h[2];
 
   for (int t = tid; t < NF * NN; t += NT) {
     const int f = t / NN, i = t % NN;
     const long long gi = boff + f * EN + (long long)ee * NN + i;
     const int pi = f * NNP + padded_node<N>(i);
-    XA[pi] = u[gi];
-    if (NV == 2) XA[NF * NNP + pi] = kBlk ? R(t == col ? 1 : 0) : v[gi];
+    XA[pi] = R(u[gi]);
+    if (NV == 2) XA[NF * NNP + pi] = kBlk ? R(t == col ? 1 : 0) : R(v[gi]);
   }
   // neighbour data of a face, fetched into registers one face ahead so that the
   // global loads overlap the computation of the previous stage
@@ -274,7 +311,7 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
       if (t < NA * NN) {
         const int vv = t / (NF * NN), r = t % (NF * NN), f = r / NN, i = r % NN;
         const long long gi = boff + f * EN + (long long)en * NN + i;
-        pf[k] = vv == 0 ? u[gi] : (kBlk ? R(0) : v[gi]);
+        pf[k] = vv == 0 ? R(u[gi]) : (kBlk ? R(0) : R(v[gi]));
       }
     }
   };
@@ -466,7 +503,7 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
         d2 += hc * hc;
         if (c == a) hn = hc;
       }
-      diagn = sqrt(d2);
+      diagn = sqrtv(d2);
 #pragma unroll
       for (int k = 0; k < PF; ++k) {
         const int t = tid + k * NT;
@@ -641,11 +678,11 @@ op3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v
     if (kBlk) {
       const long long nb = NF * NN;
       for (int t = tid; t < NF * NN; t += NT)
-        out[((long long)e * nb + t) * nb + col] = RO[(t / NN) * NNP + padded_node<N>(t % NN)];
+        out[((long long)e * nb + t) * nb + col] = to_io(RO[(t / NN) * NNP + padded_node<N>(t % NN)]);
     } else {
       for (int t = tid; t < NF * NN; t += NT) {
         const int f = t / NN, i = t % NN;
-        out[ooff + f * EN + (long long)e * NN + i] = RO[f * NNP + padded_node<N>(i)];
+        out[ooff + f * EN + (long long)e * NN + i] = to_io(RO[f * NNP + padded_node<N>(i)]);
       }
     }
   }
@@ -686,8 +723,8 @@ struct SmemF {
 // sweep), written to the same places of the face buffer.
 template <int P, int NF, int MODE, class R>
 __global__ void __launch_bounds__(kMaxThreads3D)
-face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__ v, int pa,
-              int pia) {
+face3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __restrict__ v,
+              int pa, int pia) {
   constexpr int NT = tpf3d<P, R>();
   using S = SmemF<P, NF, MODE, NT>;
   using TO = TabOff<P>;
@@ -744,7 +781,7 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
   const R xa = vertex<R>(prm, a, ia);
   const R hL = hasL ? xa - vertex<R>(prm, a, ia - 1) : R(1);
   const R hU = hasU ? vertex<R>(prm, a, ia + 1) - xa : R(1);
-  const R diagL = sqrt(hL * hL + h0 * h0 + h1 * h1), diagU = sqrt(hU * hU + h0 * h0 + h1 * h1);
+  const R diagL = sqrtv(hL * hL + h0 * h0 + h1 * h1), diagU = sqrtv(hU * hU + h0 * h0 + h1 * h1);
 
   // both elements' data (a missing side is zero and never read); node-outer, so
   // the padded offset is formed once per node
@@ -756,11 +793,11 @@ face3d_kernel(const OpParams prm, const R* __restrict__ u, const R* __restrict__
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const long long o = f * EN + i;
-        XS[f * NNP + pi] = hasL ? u[gL + o] : R(0);
-        XS[(NA + f) * NNP + pi] = hasU ? u[gU + o] : R(0);
+        XS[f * NNP + pi] = hasL ? R(u[gL + o]) : R(0);
+        XS[(NA + f) * NNP + pi] = hasU ? R(u[gU + o]) : R(0);
         if (NA > NF) {
-          XS[(NF + f) * NNP + pi] = hasL ? v[gL + o] : R(0);
-          XS[(NA + NF + f) * NNP + pi] = hasU ? v[gU + o] : R(0);
+          XS[(NF + f) * NNP + pi] = hasL ? R(v[gL + o]) : R(0);
+          XS[(NA + NF + f) * NNP + pi] = hasU ? R(v[gU + o]) : R(0);
         }
       }
     }

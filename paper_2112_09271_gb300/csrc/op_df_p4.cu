@@ -1,0 +1,3 @@
+// Double-float hexahedral operator kernels of degree p = 4 (R, J v, J^T w).
+#include "enp_op_dispatch.cuh"
+ENP_DF_DEGREE(4)
