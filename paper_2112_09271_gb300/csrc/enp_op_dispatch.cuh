@@ -26,6 +26,10 @@ static cudaError_t raise_smem_limit(SmemAttr& st, K kern, size_t bytes) {
   std::lock_guard<std::mutex> g(st.mu);
   if (st.done[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // shared memory, not L1, bounds the resident blocks of these kernels
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess) st.done[dev] = true;
   return e;
 }

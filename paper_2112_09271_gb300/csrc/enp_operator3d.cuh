@@ -15,6 +15,10 @@
 
 #include "enp_operator.cuh"
 
+#ifndef ENP_DF_MIN_BLOCKS
+#define ENP_DF_MIN_BLOCKS 3
+#endif
+
 namespace enp {
 
 constexpr int kTabSz = 96;  // per degree: B (Q*N), Dq (Q*Q), dL (2N), wq (Q), xq (Q)
@@ -242,9 +246,14 @@ struct Smem3 {
 // Largest thread block of the hexahedral kernel; the elements per block (EB,
 // chosen at launch by the autotuner) satisfy EB * tpe3d <= this.
 constexpr int kMaxThreads3D = 256;
+// Resident blocks per SM the register allocation is sized for: the
+// double-float kernels are issue-bound on the FP32 pipe and need more warps in
+// flight than their natural register count allows.
+template <class R> struct MinBlocks3D { static constexpr int value = 1; };
+template <> struct MinBlocks3D<df> { static constexpr int value = ENP_DF_MIN_BLOCKS; };
 
 template <int P, int NF, int MODE, class R>
-__global__ void __launch_bounds__(kMaxThreads3D)
+__global__ void __launch_bounds__(kMaxThreads3D, MinBlocks3D<R>::value)
 op3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __restrict__ v,
             io_t<R>* __restrict__ out) {
   using S = Smem3<P, NF, MODE, tpe3d<P, R>()>;
@@ -722,7 +731,7 @@ struct SmemF {
 // direction pa (the upstream coupling of one plane in a block Gauss-Seidel
 // sweep), written to the same places of the face buffer.
 template <int P, int NF, int MODE, class R>
-__global__ void __launch_bounds__(kMaxThreads3D)
+__global__ void __launch_bounds__(kMaxThreads3D, MinBlocks3D<R>::value)
 face3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __restrict__ v,
               int pa, int pia) {
   constexpr int NT = tpf3d<P, R>();
