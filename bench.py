@@ -221,38 +221,60 @@ def cpu_baseline(prob, budget_s=12.0):
 
 
 def SOLVE_VARIANTS(enp):
-    """(label, two-level preconditioner, Newton options) of the full solves."""
+    """(label, two-level preconditioner, Newton options) of the full solves.
+    `arith` is the arithmetic of the FP64 residual and J v (native FP64 or
+    double-float); `guess` starts from the initial guess of Sec. 4.3 instead
+    of Phi = 0."""
     f64 = dict(bj_storage=enp.BJ_F64, mixed=False)
     mix = dict(bj_storage=enp.BJ_BF16, mixed=True)
+    df = dict(f64, arith=enp.ARITH_DF32)
     return [("fp64", 0, f64), ("mixed", 0, mix), ("fp64_two_level", 1, f64),
+            ("fp64_df32_two_level", 1, df),
             ("mixed_two_level", 1, mix), ("mixed_two_level_lag3", 1, dict(mix, pc_lag=3)),
-            ("mixed_two_level_sweep", 1, dict(mix, sweep=1))]
+            ("mixed_two_level_sweep", 1, dict(mix, sweep=1)),
+            ("mixed_two_level_paper_guess", 1, dict(mix, guess=1))]
 
 
-def run_solves(enp, W, name):
+CHANNEL_SOLVE_VARIANTS = ("fp64_df32_two_level", "mixed_two_level", "mixed_two_level_paper_guess")
+
+
+def run_solves(enp, W, name, labels=None, reference="fp64"):
     """Newton with backtracking line search and preconditioned FGMRES(50)
     (inner rtol 1e-3, as in the paper) from c = c_in, Phi = 0 to
-    ||R|| <= 1e-10 ||R_0||: FP64 throughout, then mixed (FP32 inner operator and
-    Krylov vectors, BF16 block inverses assembled in FP32) with the FP64 outer
+    ||R|| <= 1e-10 ||R_0||: FP64 throughout (native, or double-float arithmetic
+    for the residual and J v), then mixed (FP32 inner operator and Krylov
+    vectors, BF16 block inverses assembled in FP32) with the FP64 outer
     residual; each with block-Jacobi alone and with the two-level
     preconditioner (block-Jacobi plus the coarse element-mean potential
-    correction). Wall time on the device, and each solution's distance from the
-    FP64 block-Jacobi one."""
+    correction); and from the initial guess of Sec. 4.3 (c = c_in, Phi from the
+    charge equation at constant c, inner rtol 1e-2), its time included. Wall
+    time on the device, and each solution's distance from the `reference`
+    one."""
     import torch
     prob = W.config(name)
     op = enp.Operator(prob)
-    op.autotune()
+    for code in (enp.ARITH_F64, enp.ARITH_DF32):
+        op.set_arithmetic(code)
+        op.autotune()
     u0 = np.zeros((prob.n_fields, prob.E, prob.Np))
     for k in range(1, prob.n_fields):
         u0[k] = prob.c_in[k - 1]
     out, sols = {"workload": name, "n_dof": prob.n_dof, "rtol": 1e-10}, {}
     for label, two, kw in SOLVE_VARIANTS(enp):
+        if labels is not None and label not in labels:
+            continue
         kw = dict(kw)
         op.set_sweep(kw.pop("sweep", 0))
+        op.set_arithmetic(kw.pop("arith", enp.ARITH_F64))
+        guess = kw.pop("guess", 0)
         op.set_preconditioner(two)
         u = torch.tensor(u0.reshape(-1), device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        gst = None
+        if guess:
+            gst = op.initial_guess(u, rtol=1e-8, krylov_rtol=1e-2, krylov_restart=50,
+                                   raise_on_fail=False, **kw)
         st = op.newton_solve(u, max_it=30, rtol=1e-10, krylov_restart=50, krylov_max_it=4000,
                              krylov_rtol=1e-3, raise_on_fail=False, **kw)
         torch.cuda.synchronize()
@@ -264,20 +286,27 @@ def run_solves(enp, W, name):
                       "krylov_seconds": st["krylov_seconds"],
                       "converged": bool(st["converged"]),
                       "final_relative_residual": st["residual_norm"] / st["initial_norm"]}
-    ref = sols["fp64"]
-    others = [k for k in sols if k != "fp64"]
+        if gst is not None:
+            out[label]["initial_guess"] = {
+                "newton_iterations": gst["iterations"],
+                "krylov_iterations": gst["krylov_iterations"],
+                "converged": bool(gst["converged"])}
+    op.set_arithmetic(enp.ARITH_F64)
+    ref = sols[reference]
+    others = [k for k in sols if k != reference]
     for label in others:
-        out[label + "_vs_fp64_relative_error"] = float(
+        out[label + "_vs_" + reference + "_relative_error"] = float(
             np.linalg.norm(sols[label] - ref) / np.linalg.norm(ref))
-    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    if "mixed" in sols:
+        out["speedup_mixed_over_fp64"] = out[reference]["seconds"] / out["mixed"]["seconds"]
     best = min(others, key=lambda k: out[k]["seconds"])
     out["best"] = best
-    out["speedup_best_over_fp64"] = out["fp64"]["seconds"] / out[best]["seconds"]
+    out["speedup_best_over_" + reference] = out[reference]["seconds"] / out[best]["seconds"]
     return out
 
 
 def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
-                      labels=("fp64", "mixed", "mixed_sweep")):
+                      labels=("fp64", "mixed", "mixed_sweep", "mixed_paper_guess")):
     """The operating-point sweep of the plate reactor (Sec. 5.2): `batch`
     applied cathode potentials from volts[0] to volts[1] (anode at 0), all
     solved in one batched Newton run per stage, with continuation in the
@@ -285,7 +314,10 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
     reach of Newton from a plain guess), the two-level preconditioner and FGMRES
     restart cycles replayed from a captured CUDA graph. FP64 and mixed (FP32
     inner operator, FP32 block inverses); initial guess c = c_in,
-    Phi = phi_app / 2 at the first stage; the last stage to 1e-10 relative."""
+    Phi = phi_app / 2 at the first stage, or (`_paper_guess`) the initial guess
+    of Sec. 4.3 at the first stage's potentials (Phi from the charge equation
+    at c = c_in, inner rtol 1e-2, its time included); the last stage to 1e-10
+    relative."""
     import torch
     prob = W.config(name)
     phis = 38.92 * np.linspace(volts[0], volts[1], batch)  # F/RT at 298.15 K
@@ -301,12 +333,18 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
     sols = {}
     kws = {"fp64": dict(bj_storage=enp.BJ_F64, mixed=False),
            "mixed": dict(bj_storage=enp.BJ_F32, mixed=True),
-           "mixed_sweep": dict(bj_storage=enp.BJ_F32, mixed=True)}
+           "mixed_sweep": dict(bj_storage=enp.BJ_F32, mixed=True),
+           "mixed_paper_guess": dict(bj_storage=enp.BJ_F32, mixed=True)}
     for label in labels:
         op.set_sweep(1 if label.endswith("_sweep") else 0)
         u = torch.tensor(u0, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        gst = None
+        if label.endswith("_paper_guess"):
+            op.set_phi_app(target * step0)
+            gst = op.initial_guess(u, rtol=1e-8, krylov_rtol=1e-2, graph=True,
+                                   raise_on_fail=False, **kws[label])
         st = op.newton_continuation(u, target, step0=step0, graph=True, raise_on_fail=False,
                                     **kws[label])
         torch.cuda.synchronize()
@@ -321,6 +359,10 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
                       "converged": st["status"] == 0,
                       "last_stage_relative_residual": last["residual_norm"] / last["initial_norm"],
                       "last_stage_residual_norm": last["residual_norm"]}
+        if gst is not None:
+            out[label]["initial_guess"] = {"newton_iterations": gst["iterations"],
+                                           "krylov_iterations": gst["krylov_iterations"],
+                                           "converged": bool(gst["converged"])}
     if "fp64" in sols:
         ref = sols["fp64"]
         for lab in sols:
@@ -404,6 +446,9 @@ def main():
     ap.add_argument("--reactor-workload", default="reactor_n2_p2",
                     help="workload of the batched 0.1-0.8 V sweep (reactor192_p2: the full "
                          "plate reactor, mixed precision only, about 13 minutes)")
+    ap.add_argument("--channel-solve", type=int, default=0,
+                    help="1: also solve channel64_p3 (3 species, 6.3M DOFs) to 1e-10, FP64 "
+                         "(double-float arithmetic) and mixed (FP32 inner, BF16 inverses)")
     ap.add_argument("--only", default=None,
                     help="time one operator alone (for profiling): residual_f64, jvp_f64, "
                          "vjp_f64, residual_df32, jvp_df32, vjp_df32, jvp_f32, bj_apply_f32; "
@@ -620,13 +665,16 @@ def main():
            "ms_per_step": e2e_ms, "arith": head}
 
     del flush
-    solve = batched = None
+    solve = batched = solve_channel = None
     if rank == 0 and not args.no_solve:
         solve = run_solves(enp, W, args.solve_workload)
         full = args.reactor_workload.startswith("reactor192")
         batched = run_batched_solve(enp, W, args.reactor_workload,
-                                    labels=("mixed", "mixed_sweep") if full
-                                    else ("fp64", "mixed", "mixed_sweep"))
+                                    labels=("mixed", "mixed_sweep", "mixed_paper_guess") if full
+                                    else ("fp64", "mixed", "mixed_sweep", "mixed_paper_guess"))
+        if args.channel_solve:
+            solve_channel = run_solves(enp, W, "channel64_p3", labels=CHANNEL_SOLVE_VARIANTS,
+                                       reference="fp64_df32_two_level")
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(prob)
@@ -636,6 +684,11 @@ def main():
             solve_seconds = {k: solve[k]["seconds"] for k in solve
                              if isinstance(solve[k], dict) and "seconds" in solve[k]}
             solve_seconds["workload"] = solve["workload"]
+        if solve_channel:
+            solve_seconds = solve_seconds or {}
+            solve_seconds["channel64_p3"] = {
+                k: solve_channel[k]["seconds"] for k in solve_channel
+                if isinstance(solve_channel[k], dict) and "seconds" in solve_channel[k]}
         line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -661,6 +714,7 @@ def main():
                 "hbm_frac": hbm_frac, "solve_seconds": solve_seconds,
                 "step_blend_GDOF_s": blend,
                 "ops": per_op, "roofline": roof, "roofline_hbm": roof_hbm, "solve": solve,
+                "solve_channel": solve_channel,
                 "batched_solve": batched,
                 "cpu_baseline": cb, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,

@@ -244,8 +244,8 @@ enp_status enp_set_coarse_options(enp_handle h, int cycles, int smooth, double o
  * Gauss-Seidel sweep (on = 1; 0 restores block-Jacobi), hexahedral meshes:
  * z = (D + L)^-1 r, D the element-diagonal blocks of the last setup and L the
  * coupling of every element to its upstream neighbour along the flow axis (the
- * plate-flow axis, or the largest component of a constant velocity, in its
- * direction). The element planes across that axis are solved in flow order:
+ * plate-flow axis in the sign of its mean speed, or the largest component of a
+ * constant velocity, in its direction). The element planes across that axis are solved in flow order:
  * each plane subtracts the face terms of J(u) z of the planes already solved
  * (the face kernel restricted to the faces in between, at the u of the last
  * setup) and applies its block inverses; 2 launches per plane. With upwind
@@ -331,6 +331,24 @@ typedef struct {
 enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* opts,
                             enp_newton_stats* stats);
 
+/* The initial guess of Sec. 4.3 ("Implementation"), in place on u: every
+ * concentration at its inlet value c_k^in (every node, every operating point),
+ * and the potential from the charge-conservation equation (Eq. chargeDG) at
+ * these constant concentrations, starting from the potential in u. With
+ * Butler-Volmer electrodes that equation is nonlinear in Phi, so it is solved
+ * by the Newton method of enp_newton_solve on the potential rows alone: the
+ * species rows of the system are replaced by c_k - c_k^in, with unit rows in
+ * J and in the element blocks, so the concentrations stay at c^in and the
+ * preconditioner (block-Jacobi, plus the coarse potential correction when the
+ * two-level preconditioner is on) acts on the potential block. The paper
+ * solves each linear system of this step with its potential-block solver to a
+ * relative tolerance of 1e-2: opts->krylov.rtol = 1e-2 follows it. The
+ * downwind sweep is not used here. The preconditioner of the last setup is
+ * replaced (set up again before a separate enp_block_jacobi_apply).
+ * Synchronises. Errors as enp_newton_solve. */
+enp_status enp_initial_guess(enp_handle h, double* u, const enp_newton_opts* opts,
+                             enp_newton_stats* stats);
+
 /* Continuation in the applied potential for operating points that Newton
  * cannot reach from a plain initial guess (strongly driven Butler-Volmer
  * electrodes, Eq. bv, Sec. 5.2): solves R(u; lambda Phi_app) = 0 for a rising
@@ -388,6 +406,11 @@ enp_status enp_param_jacobian(enp_handle h, const double* u, double* dRdtheta);
 /* dtheta[b][j] = <w_b, dR_b/dtheta_j>: the parameter part of the adjoint.
  * w: device [batch][m][E][Np]; dtheta: host [batch][n_theta]. Synchronises. */
 enp_status enp_param_vjp(enp_handle h, const double* u, const double* w, double* dtheta);
+
+/* dtheta[j] = sum_b <w_b, dR_b/dtheta_j>: the same, summed over the operating
+ * points on the device (in batch order), for one parameter vector shared by the
+ * whole batch. dtheta: host [n_theta]. Synchronises. */
+enp_status enp_param_vjp_total(enp_handle h, const double* u, const double* w, double* dtheta);
 
 /* enp_inner_product without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc,

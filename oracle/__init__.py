@@ -260,6 +260,42 @@ class Oracle:
         return u, hist
 
 
+def potential_initial_guess(orc, prob, phi0, rtol=1e-12, max_it=30, c_armijo=1e-4):
+    """The initial guess of Sec. 4.3 ("Implementation"): every concentration at
+    its inlet value c_k^in, and the potential from the charge-conservation
+    equation at these constant concentrations, R_Phi(Phi; c^in) = 0 (the rows of
+    Eq. chargeDG). With Butler-Volmer electrodes that equation is nonlinear in
+    Phi, so it is solved by Newton's method with backtracking on ||R_Phi||, each
+    step a direct solve with the Phi-Phi block of the assembled Jacobian (the
+    paper hands the same equation to its potential-block solver). phi0: the
+    starting potential [E * Np]. Returns (u [n_dof], history of ||R_Phi||)."""
+    import scipy.sparse.linalg as spla
+    n_phi = prob.E * prob.Np
+    u = np.zeros(prob.n_dof)
+    u[:n_phi] = _f64(phi0)
+    for k in range(prob.m - 1):
+        u[(k + 1) * n_phi:(k + 2) * n_phi] = prob.c_in[k]
+    r = orc.residual(u)[:n_phi]
+    r0 = np.linalg.norm(r)
+    hist = [r0]
+    for _ in range(max_it):
+        if np.linalg.norm(r) <= rtol * max(r0, 1e-300):
+            break
+        A = orc.jacobian(u).tocsr()[:n_phi, :n_phi].tocsc()
+        dphi = spla.spsolve(A, -r)
+        lam, nr = 1.0, np.linalg.norm(r)
+        while True:
+            ut = u.copy()
+            ut[:n_phi] += lam * dphi
+            rt = orc.residual(ut)[:n_phi]
+            if np.linalg.norm(rt) <= (1 - c_armijo * lam) * nr or lam < 1e-4:
+                break
+            lam *= 0.5
+        u, r = ut, rt
+        hist.append(np.linalg.norm(r))
+    return u, hist
+
+
 def recover_cm(prob, u):
     """The eliminated concentration c_m = -(1/z_m) sum_{k<m} z_k c_k
     (Eq. substitution), node by node: [E * Np]."""

@@ -175,10 +175,12 @@ _PROTOS = [
     ("enp_fgmres_solve_f32", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_newton_solve", _I, [_V, _V, _V, _V]),
     ("enp_newton_continuation", _I, [_V, _V, _V, _V, _V, _V]),
+    ("enp_initial_guess", _I, [_V, _V, _V, _V]),
     ("enp_autotune", _I, [_V, _V]),
     ("enp_param_count", _I, [_V, ctypes.POINTER(_I)]),
     ("enp_param_jacobian", _I, [_V, _V, _V]),
     ("enp_param_vjp", _I, [_V, _V, _V, _V]),
+    ("enp_param_vjp_total", _I, [_V, _V, _V, _V]),
     ("enp_inner_product_noalloc", _I, [_V, _V, _LL, _I, _V, _V]),
     ("enp_set_arithmetic", _I, [_V, _I]),
     ("enp_get_arithmetic", _I, [_V, ctypes.POINTER(_I)]),
@@ -445,6 +447,27 @@ class Operator:
         out["status"] = rc
         return out
 
+    def initial_guess(self, u, max_it=30, rtol=1e-8, atol=0.0, armijo_c=1e-4,
+                      max_backtracks=12, bj_storage=BJ_F64, mixed=False, krylov_restart=50,
+                      krylov_max_it=4000, krylov_rtol=1e-2, raise_on_fail=True, graph=False,
+                      pc_lag=1):
+        """The initial guess of Sec. 4.3 in place on u: c = c_in everywhere and
+        Phi from the charge-conservation equation at constant c, by Newton from
+        the Phi in u (inner FGMRES to 1e-2, as the paper); returns the stats."""
+        import torch
+        o = NewtonOpts(max_it, rtol, atol, armijo_c, max_backtracks, bj_storage, int(mixed),
+                       KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0, int(graph)),
+                       int(pc_lag))
+        st = NewtonStats()
+        rc = self._lib.enp_initial_guess(self.h, _dptr(u, torch.float64), ctypes.byref(o),
+                                         ctypes.byref(st))
+        if rc != ENP_OK and raise_on_fail:
+            self._check(rc)
+        out = {k: getattr(st, k) for k, _ in NewtonStats._fields_ if k != "history"}
+        out["history"] = list(st.history[: st.iterations + 1])
+        out["status"] = rc
+        return out
+
     def newton_continuation(self, u, phi_app, step0=0.125, step_max=0.25, step_min=1.0 / 512,
                             grow=1.5, stage_rtol=1e-6, stage_max_it=10, max_it=30, rtol=1e-10,
                             atol=0.0, armijo_c=1e-4, max_backtracks=12, bj_storage=BJ_F64,
@@ -505,6 +528,16 @@ class Operator:
                                             ctypes.c_void_p(out.ctypes.data)))
         return out
 
+    def param_vjp_total(self, u, w):
+        """sum_b <w_b, dR_b/dtheta_j>, summed over operating points on the
+        device: numpy [n_theta]."""
+        import torch
+        out = np.zeros(self.n_theta)
+        self._check(self._lib.enp_param_vjp_total(self.h, _dptr(u, torch.float64),
+                                                  _dptr(w, torch.float64),
+                                                  ctypes.c_void_p(out.ctypes.data)))
+        return out
+
     def vjp(self, u, w, out=None):
         import torch
         out = self._new(torch.float64) if out is None else out
@@ -535,7 +568,7 @@ def residual_function(op):
             gu = op.vjp(u.detach().contiguous(), g) if ctx.needs_input_grad[0] else None
             gt = None
             if ctx.needs_input_grad[1]:
-                d = op.param_vjp(u.detach().contiguous(), g).sum(axis=0)
+                d = op.param_vjp_total(u.detach().contiguous(), g)
                 gt = torch.tensor(d, dtype=torch.float64, device=u.device)
             return gu, gt
 

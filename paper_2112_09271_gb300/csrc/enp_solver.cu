@@ -143,6 +143,57 @@ __global__ void scale_batched(const double* __restrict__ x, const double* __rest
     y[k] = sc[k / n] * x[k];
 }
 
+// Potential-only operator (the initial guess of Sec. 4.3): the species rows of
+// J v are the identity, y_species = v_species.
+template <class T>
+__global__ void species_rows_copy(const T* __restrict__ v, T* __restrict__ y, long long EN,
+                                  int NF, long long bstride, int B) {
+  const long long per = (long long)(NF - 1) * EN;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per * B;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / per, i = EN + t % per;
+    y[b * bstride + i] = v[b * bstride + i];
+  }
+}
+
+// ... and the species rows of the residual are c_k - c_k^in.
+__global__ void species_rows_offset(const double* __restrict__ u, double* __restrict__ r,
+                                    long long EN, int NF, long long bstride, int B, double c0,
+                                    double c1, double c2) {
+  const double cin[3] = {c0, c1, c2};
+  const long long per = (long long)(NF - 1) * EN;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per * B;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / per, i = EN + t % per;
+    r[b * bstride + i] = u[b * bstride + i] - cin[(t % per) / EN];
+  }
+}
+
+// ... and the species rows of every element-diagonal block are unit rows
+// (blocks [nblk][nb][nb] row-major, rows f * Np + i).
+template <class T>
+__global__ void block_species_identity(T* __restrict__ blk, long long nblk, int nb, int Np) {
+  const long long per = (long long)(nb - Np) * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per * nblk;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long k = t / per, rc = t % per;
+    const int row = Np + (int)(rc / nb), col = (int)(rc % nb);
+    blk[k * nb * nb + (long long)row * nb + col] = row == col ? T(1) : T(0);
+  }
+}
+
+// c_k = c_k^in at every node of every operating point.
+__global__ void species_fill(double* __restrict__ u, long long EN, int NF, long long bstride, int B,
+                             double c0, double c1, double c2) {
+  const double cin[3] = {c0, c1, c2};
+  const long long per = (long long)(NF - 1) * EN;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per * B;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / per, i = EN + t % per;
+    u[b * bstride + i] = cin[(t % per) / EN];
+  }
+}
+
 template <class TX, class TY>
 __global__ void convert_kernel(const TX* __restrict__ x, TY* __restrict__ y, long long n) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -950,6 +1001,7 @@ struct SolverState {
   unsigned long long pc_gen = 1, gkey_gen = 0;
   // two-level preconditioner: element-mean potential correction
   bool sweep = false;             // downwind block Gauss-Seidel (enp_set_sweep)
+  bool potential_only = false;    // the potential rows alone (enp_initial_guess)
   bool sweep_ready = false;
   int sweep_axis = 0, sweep_dir = 1;
   double* upc64 = nullptr;        // the linearisation point of the last setup
@@ -1002,7 +1054,33 @@ cudaError_t ensure(P** p, size_t& have, size_t want_count) {
   return e;
 }
 
-// Batched dot products <V_i, w>_b for i < nd, into dsmall[0 .. batch*nd).
+// J(u) v as the solvers apply it; in potential-only mode (the initial guess)
+// the species rows are the identity.
+template <class TV>
+cudaError_t apply_jv(enp_handle h, const OpParams& P, const TV* ulin, const TV* v, TV* out, int B) {
+  cudaError_t e = enp::launch_op<TV>(enp::kJvp, P, h->d_tab, ulin, v, out, B, h->stream);
+  if (e == cudaSuccess && state_of(h).potential_only) {
+    const long long EN = (long long)P.E * P.Np;
+    enp::species_rows_copy<TV><<<grid_for((P.NF - 1) * EN * B), 256, 0, h->stream>>>(
+        v, out, EN, P.NF, P.batch_stride, B);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// R(u) as the Newton solver evaluates it; in potential-only mode the species
+// rows are c_k - c_k^in.
+cudaError_t apply_residual(enp_handle h, const double* u, double* r, int B) {
+  const OpParams& P = h->prm;
+  cudaError_t e = enp::launch_op<double>(enp::kResidual, P, h->d_tab, u, nullptr, r, B, h->stream);
+  if (e == cudaSuccess && state_of(h).potential_only) {
+    const long long EN = (long long)P.E * P.Np;
+    enp::species_rows_offset<<<grid_for((P.NF - 1) * EN * B), 256, 0, h->stream>>>(
+        u, r, EN, P.NF, P.batch_stride, B, P.cin[0], P.cin[1], P.cin[2]);
+    e = cudaGetLastError();
+  }
+  return e;
+}
 
 // Partials of <V_i, w>_b (i < nd) into S.part; *nparts = the partials per dot.
 template <class T>
@@ -1371,6 +1449,9 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     S.nb = nb;
     enp_status st = enp_block_diagonal(h, u, S.blocks);
     if (st != ENP_OK) return st;
+    if (S.potential_only)
+      enp::block_species_identity<double><<<grid_for((long long)(nb - P.Np) * nb * nblk), 256, 0,
+                                            h->stream>>>(S.blocks, nblk, nb, P.Np);
   } else {
     const long long ntot = h->n_dof * h->batch;
     if ((e = ensure(&S.blocks32, S.blocks32_count, nn * nblk)) != cudaSuccess ||
@@ -1386,6 +1467,9 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
                                 S.blocks32 + b * bsz, nb, h->stream);
       if (e != cudaSuccess) return cuda_err(h, e, "FP32 block columns");
     }
+    if (S.potential_only)
+      enp::block_species_identity<float><<<grid_for((long long)(nb - P.Np) * nb * nblk), 256, 0,
+                                           h->stream>>>(S.blocks32, nblk, nb, P.Np);
   }
   S.storage = storage;
   cudaMemsetAsync(S.d_flag, 0, sizeof(int), h->stream);
@@ -1564,12 +1648,12 @@ extern "C" enp_status enp_set_sweep(enp_handle h, int on) {
   S.sweep = on == 1;
   S.sweep_ready = false;
   ++S.pc_gen;
-  // the flow axis and direction: the plate-flow axis (velocity >= 0), or the
-  // largest component of a constant velocity
+  // the flow axis and direction: the plate-flow axis in the sign of its mean
+  // speed, or the largest component of a constant velocity
   const auto& pd = h->prm.pd;
   if (pd.vel_kind == 1) {
     S.sweep_axis = pd.velA;
-    S.sweep_dir = 1;
+    S.sweep_dir = pd.vp[4] < 0.0 ? -1 : 1;
   } else {
     int ax = 0;
     for (int d = 1; d < 3; ++d)
@@ -1676,7 +1760,7 @@ static enp_status fgmres_any(enp_handle h, const TV* ulin, const TV* b, TV* x,
   dim3 gv(gx, B);
   const int tb = std::min(B, 256), gbk = (B + tb - 1) / tb;
   auto apply_A = [&](const TV* in, TV* outv) -> cudaError_t {
-    return enp::launch_op<TV>(enp::kJvp, P, h->d_tab, ulin, in, outv, B, h->stream);
+    return apply_jv<TV>(h, P, ulin, in, outv, B);
   };
   std::vector<int> hj(B);
   std::vector<double> hres(B), hb(B);
@@ -1851,7 +1935,7 @@ static enp_status fgmres_graph(enp_handle h, const TV* ulin, const TV* b, TV* x,
   if ((e = multidot<TV>(h, bg, 0, 1, bg, K.bn2)) != cudaSuccess) { cudaEventDestroy(ev); return fail_cuda(e, "fgmres norm"); }
   enp::krylov_tolerance<<<gbk, tb, 0, h->stream>>>(K, B, o->rtol, o->atol);
   auto apply_A = [&](const TV* in, TV* outv) -> cudaError_t {
-    return enp::launch_op<TV>(enp::kJvp, P, h->d_tab, ug, in, outv, B, h->stream);
+    return apply_jv<TV>(h, P, ug, in, outv, B);
   };
   const bool same = S.gexec && S.gkey[0] == (const void*)S.V && S.gkey[1] == S.binv &&
                     S.gkey[2] == (const void*)S.gbuf && S.gkey[3] == (const void*)S.dsmall &&
@@ -2021,7 +2105,7 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
   const int gx = grid_for(ntot);
   enp_status status = ENP_OK;
   std::vector<double> rn, r0, tol(B), lam(B), mask(B), rnew;
-  if ((e = enp::launch_op<double>(enp::kResidual, h->prm, h->d_tab, u, nullptr, r, B, h->stream)) != cudaSuccess ||
+  if ((e = apply_residual(h, u, r, B)) != cudaSuccess ||
       (e = norms(r, rn)) != cudaSuccess) { cleanup(); return cuda_err(h, e, "newton residual"); }
   r0 = rn;
   for (int b = 0; b < B; ++b) {
@@ -2085,7 +2169,7 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
     for (int bt = 0;; ++bt) {
       cudaMemcpyAsync(dlam, lam.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream);
       enp::axpy_batched<<<gx, 256, 0, h->stream>>>(u, dlam, du, ut, n, B);
-      if ((e = enp::launch_op<double>(enp::kResidual, h->prm, h->d_tab, ut, nullptr, rt, B, h->stream)) != cudaSuccess ||
+      if ((e = apply_residual(h, ut, rt, B)) != cudaSuccess ||
           (e = norms(rt, rnew)) != cudaSuccess) { cleanup(); return cuda_err(h, e, "newton line search"); }
       bool all_acc = true;
       for (int b = 0; b < B; ++b) {
@@ -2115,6 +2199,33 @@ extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton
   }
   cleanup();
   return status;
+}
+
+extern "C" enp_status enp_initial_guess(enp_handle h, double* u, const enp_newton_opts* o,
+                                        enp_newton_stats* st) {
+  if (!h || !u || !o) return ENP_ERR_INVALID_ARG;
+  const OpParams& P = h->prm;
+  SolverState& S = state_of(h);
+  const int B = h->batch;
+  const long long EN = (long long)P.E * P.Np;
+  enp::species_fill<<<grid_for((P.NF - 1) * EN * B), 256, 0, h->stream>>>(
+      u, EN, P.NF, P.batch_stride, B, P.cin[0], P.cin[1], P.cin[2]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(h, e, "initial concentrations");
+  // Newton on the potential rows with the concentrations held: the species rows
+  // of the system are c - c^in (zero here) with unit Jacobian rows, so every
+  // Newton step leaves c = c^in; the sweep (which couples species across
+  // elements) is off meanwhile
+  const bool sweep = S.sweep;
+  S.sweep = false;
+  S.potential_only = true;
+  ++S.pc_gen;
+  enp_status s = enp_newton_solve(h, u, o, st);
+  S.potential_only = false;
+  S.sweep = sweep;
+  S.sweep_ready = false;
+  ++S.pc_gen;
+  return s;
 }
 
 extern "C" enp_status enp_newton_continuation(enp_handle h, double* u, const double* phi_app,
@@ -2181,9 +2292,20 @@ extern "C" enp_status enp_newton_continuation(enp_handle h, double* u, const dou
 
 // dtheta[b][j] = <w_b, dR_b/dtheta_j> for theta = (D_1..D_m, c_in_1..c_in_{m-1},
 // phi_app_0..phi_app_3): the parameter part of the adjoint.
-extern "C" enp_status enp_param_vjp(enp_handle h, const double* u, const double* w,
-                                    double* dtheta) {
-  if (!h || !u || !w || !dtheta) return ENP_ERR_INVALID_ARG;
+namespace enp {
+// out[j] = sum over operating points b (in order) of v[b][j].
+__global__ void sum_over_batch_kernel(const double* __restrict__ v, int B, int nt,
+                                      double* __restrict__ out) {
+  for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < B; ++b) s += v[(long long)b * nt + j];
+    out[j] = s;
+  }
+}
+}  // namespace enp
+
+// <w_b, dR_b/dtheta_j> for every operating point into S.dsmall[b][j] (device).
+static enp_status param_dots(enp_handle h, const double* u, const double* w, size_t extra) {
   SolverState& S = state_of(h);
   const int nt = h->prm.n_theta, B = h->batch;
   const long long n = h->n_dof;
@@ -2191,10 +2313,37 @@ extern "C" enp_status enp_param_vjp(enp_handle h, const double* u, const double*
   if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc parameter Jacobian");
   enp_status st = enp_param_jacobian(h, u, S.dRdtheta);
   if (st != ENP_OK) return st;
-  if ((e = small(h, (size_t)B * nt)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc small");
+  if ((e = small(h, (size_t)B * nt + extra)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc small");
   if ((e = multidot<double>(h, S.dRdtheta, (long long)B * n, nt, w, S.dsmall)) != cudaSuccess)
     return cuda_err(h, e, "parameter dots");
-  e = cudaMemcpyAsync(dtheta, S.dsmall, sizeof(double) * B * nt, cudaMemcpyDeviceToHost, h->stream);
+  return ENP_OK;
+}
+
+extern "C" enp_status enp_param_vjp_total(enp_handle h, const double* u, const double* w,
+                                          double* dtheta) {
+  if (!h || !u || !w || !dtheta) return ENP_ERR_INVALID_ARG;
+  const int nt = h->prm.n_theta, B = h->batch;
+  enp_status st = param_dots(h, u, w, (size_t)nt);
+  if (st != ENP_OK) return st;
+  SolverState& S = state_of(h);
+  double* tot = S.dsmall + (size_t)B * nt;
+  enp::sum_over_batch_kernel<<<1, 32, 0, h->stream>>>(S.dsmall, B, nt, tot);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dtheta, tot, sizeof(double) * nt, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "parameter vjp (total)");
+}
+
+extern "C" enp_status enp_param_vjp(enp_handle h, const double* u, const double* w,
+                                    double* dtheta) {
+  if (!h || !u || !w || !dtheta) return ENP_ERR_INVALID_ARG;
+  const int nt = h->prm.n_theta, B = h->batch;
+  enp_status st = param_dots(h, u, w, 0);
+  if (st != ENP_OK) return st;
+  SolverState& S = state_of(h);
+  cudaError_t e = cudaMemcpyAsync(dtheta, S.dsmall, sizeof(double) * B * nt, cudaMemcpyDeviceToHost,
+                                  h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "parameter vjp");
 }

@@ -87,3 +87,31 @@ def test_param_jacobian_unsupported_in_2d():
     with pytest.raises(enp.EnpError) as ei:
         op.param_jacobian(_cuda(W.random_state(W.config("mms2d_n3"), 1)))
     assert ei.value.status == enp.ENP_ERR_UNSUPPORTED
+
+
+def test_param_vjp_total_sums_the_operating_points_on_the_device():
+    """Batched autograd: one parameter vector shared by the batch gets the sum
+    over operating points of <w_b, dR_b/dtheta>, formed in the library."""
+    import dataclasses
+
+    import torch
+    enp = _enp()
+    P = W.config("reactor_n1_p2")
+    B = 2
+    phis = np.array([[0.2 * 38.92, 0.0, 0.0, 0.0], [0.5 * 38.92, 0.0, 0.0, 0.0]])
+    op = enp.Operator(P, batch=B)
+    op.set_phi_app(phis)
+    us = [W.random_state(P, 30 + b) for b in range(B)]
+    ws = [W.random_vector(P, 40 + b) for b in range(B)]
+    u, w = _cuda(np.concatenate(us)), _cuda(np.concatenate(ws))
+    per_point = op.param_vjp(u, w)
+    total = op.param_vjp_total(u, w)
+    assert np.array_equal(total, per_point[0] + per_point[1])
+    ref = sum(oracle.Oracle(dataclasses.replace(P, bv_phi_app=list(phis[b]))).param_jacobian(us[b])
+              @ ws[b] for b in range(B))
+    assert np.abs(total - ref).max() <= 1e-12 * np.abs(ref).max()
+    # the autograd Function's parameter gradient is that total
+    fn = enp.residual_function(op)
+    th = torch.zeros(op.n_theta, dtype=torch.float64, device="cuda", requires_grad=True)
+    fn(u, th).backward(w)
+    assert np.array_equal(th.grad.cpu().numpy(), total)

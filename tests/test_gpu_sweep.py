@@ -32,15 +32,18 @@ def _cuda(x):
     return torch.tensor(np.asarray(x), device="cuda")
 
 
-def _lower_block_system(orc, P, u):
+def _lower_block_system(orc, P, u, axis=0, direction=1):
     """D + L from the assembled Jacobian: keep the entries whose column element
-    is the row element or its upstream x-neighbour."""
+    is the row element or its upstream neighbour along `axis` for flow in
+    `direction` (+1: the neighbour at the lower index, -1: at the higher)."""
     import scipy.sparse as sp
     J = orc.jacobian(u).tocoo()
     er = (J.row // P.Np) % P.E
     ec = (J.col // P.Np) % P.E
-    nx = P.n_el[0]
-    keep = (ec == er) | ((ec == er - 1) & (er % nx > 0))
+    stride = [1, P.n_el[0], P.n_el[0] * P.n_el[1]][axis]
+    ia = (er // stride) % P.n_el[axis]
+    has_up = ia > 0 if direction > 0 else ia < P.n_el[axis] - 1
+    keep = (ec == er) | ((ec == er - direction * stride) & has_up)
     return sp.csr_matrix((J.data[keep], (J.row[keep], J.col[keep])), shape=J.shape)
 
 
@@ -68,6 +71,37 @@ def test_sweep_solves_the_lower_block_system(cfg):
     op.block_jacobi_setup(_cuda(u), enp.BJ_F64)
     z = op.block_jacobi_apply(_cuda(r)).cpu().numpy()
     ref = spla.spsolve(_lower_block_system(orc, P, u).tocsc(), r)
+    assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# constant velocities whose largest component points along -x, +y and -z, and
+# plate flow with a negative mean speed (flow towards -x): the sweep's axis,
+# direction and upstream face follow the flow
+FLOWS = {"-x": (0, -1, [-1.0, 0.3, 0.2]), "+y": (1, 1, [0.2, 1.0, 0.1]),
+         "-z": (2, -1, [0.1, 0.2, -1.0])}
+
+
+@pytest.mark.parametrize("flow", ["-x", "+y", "-z", "plate-x"])
+def test_sweep_follows_the_flow_direction(flow):
+    import scipy.sparse.linalg as spla
+    enp = _enp()
+    P = W.config("cube_n3_p2")
+    if flow == "plate-x":
+        vp = list(P.vel_params)
+        vp[4] = -vp[4]
+        P = dataclasses.replace(P, vel_params=vp)
+        axis, direction = 0, -1
+    else:
+        axis, direction, vel = FLOWS[flow]
+        P = dataclasses.replace(P, vel_kind=W.VEL_CONSTANT, vel_params=vel + [0.0] * 5)
+    orc = oracle.Oracle(P)
+    u = W.random_state(P, 2)
+    r = W.random_vector(P, 5)
+    op = enp.Operator(P)
+    op.set_sweep(1)
+    op.block_jacobi_setup(_cuda(u), enp.BJ_F64)
+    z = op.block_jacobi_apply(_cuda(r)).cpu().numpy()
+    ref = spla.spsolve(_lower_block_system(orc, P, u, axis, direction).tocsc(), r)
     assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
