@@ -230,12 +230,14 @@ def SOLVE_VARIANTS(enp):
     df = dict(f64, arith=enp.ARITH_DF32)
     return [("fp64", 0, f64), ("mixed", 0, mix), ("fp64_two_level", 1, f64),
             ("fp64_df32_two_level", 1, df),
+            ("fp64_df32_two_level_pc32", 1, dict(df, bj_storage=enp.BJ_F32)),
             ("mixed_two_level", 1, mix), ("mixed_two_level_lag3", 1, dict(mix, pc_lag=3)),
             ("mixed_two_level_sweep", 1, dict(mix, sweep=1)),
             ("mixed_two_level_paper_guess", 1, dict(mix, guess=1))]
 
 
-CHANNEL_SOLVE_VARIANTS = ("fp64_df32_two_level", "mixed_two_level", "mixed_two_level_paper_guess")
+CHANNEL_SOLVE_VARIANTS = ("fp64_df32_two_level", "fp64_df32_two_level_pc32", "mixed_two_level",
+                          "mixed_two_level_paper_guess")
 
 
 def run_solves(enp, W, name, labels=None, reference="fp64"):

@@ -143,11 +143,11 @@ enp_status enp_set_phi_app(enp_handle h, const double* phi_app);
  * boundary-face Gauss points [NBF][q^(dim-1)][3] (device pointers, either NULL). */
 enp_status enp_quadrature_points(enp_handle h, double* xq, double* xbq);
 
-/* Arithmetic of the FP64 residual, J v and J^T w on hexahedral meshes
- * (enp_residual, enp_jvp, enp_vjp, and the FP64 residual and J v inside the
- * Newton and FGMRES solvers); vectors stay FP64 in and out either way. Block
- * columns (enp_block_diagonal, FP64 block-Jacobi setup), dR/dtheta and the
- * sweep's face terms always use the FP64 kernels.
+/* Arithmetic of the FP64 operator on hexahedral meshes: enp_residual,
+ * enp_jvp, enp_vjp, enp_block_diagonal (and the FP64 block-Jacobi setup), and
+ * the FP64 residual and J v inside the Newton and FGMRES solvers; vectors stay
+ * FP64 in and out either way. dR/dtheta and the sweep's face terms always use
+ * the FP64 kernels.
  *   ENP_ARITH_F64  (default): native FP64 arithmetic. GB300 issues 2 FP64
  *                  fused multiply-adds per clock per SM, so this path is bound
  *                  by the FP64 pipe.

@@ -16,7 +16,7 @@ template <class R>
 cudaError_t launch_op(int mode, const OpParams& prm, const Tables* tabs, const io_t<R>* u,
                       const io_t<R>* v, io_t<R>* out, int batch, cudaStream_t stream);
 
-// The double-float hexahedral operator: R, J v and J^T w (modes 0..2) of
+// The double-float hexahedral operator: R, J v, J^T w and block columns of
 // degree prm.p (op_df.cu), compiled one degree per translation unit
 // (op_df_p1.cu .. op_df_p4.cu), each with its own constant tables.
 cudaError_t launch_op_df(int mode, const OpParams& prm, const double* u, const double* v,

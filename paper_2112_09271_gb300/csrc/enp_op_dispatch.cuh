@@ -121,12 +121,13 @@ template <int DIM, int P, int NF, class R>
 static cudaError_t launch_mode(int mode, const OpParams& prm, const Tables* t, const io_t<R>* u,
                                const io_t<R>* v, io_t<R>* out, int batch, cudaStream_t s) {
   if constexpr (std::is_same<R, df>::value) {
-    // double-float: the residual, J v and J^T w (block columns and dR/dtheta
-    // stay with the FP64 kernels)
+    // double-float: the residual, J v, J^T w and block columns (dR/dtheta
+    // stays with the FP64 kernels)
     switch (mode) {
       case kResidual: return launch_one<DIM, P, NF, kResidual, R>(prm, t, u, v, out, batch, s);
       case kJvp: return launch_one<DIM, P, NF, kJvp, R>(prm, t, u, v, out, batch, s);
       case kVjp: return launch_one<DIM, P, NF, kVjp, R>(prm, t, u, v, out, batch, s);
+      case kBlockCol: return launch_one<DIM, P, NF, kBlockCol, R>(prm, t, u, v, out, batch, s);
     }
     return cudaErrorNotSupported;
   } else {
@@ -189,7 +190,7 @@ cudaError_t launch_face_plane(const OpParams& prm, const R* u, const R* v, int b
 template <class R>
 int eb3d_max(int p, int nf, int mode) {
 #define ENP_EBM(PP, NFF, MM) \
-  if (p == PP && nf == NFF && mode == MM && (MM <= kVjp || !std::is_same<R, df>::value)) return max_eb<PP, NFF, MM, R>();
+  if (p == PP && nf == NFF && mode == MM && (MM != kParam || !std::is_same<R, df>::value)) return max_eb<PP, NFF, MM, R>();
 #define ENP_EBM_P(PP) ENP_EBM(PP, 2, 0) ENP_EBM(PP, 2, 1) ENP_EBM(PP, 2, 2) ENP_EBM(PP, 2, 3) ENP_EBM(PP, 2, 4) \
   ENP_EBM(PP, 3, 0) ENP_EBM(PP, 3, 1) ENP_EBM(PP, 3, 2) ENP_EBM(PP, 3, 3) ENP_EBM(PP, 3, 4)
   ENP_EBM_P(1) ENP_EBM_P(2) ENP_EBM_P(3) ENP_EBM_P(4)
@@ -220,8 +221,8 @@ template <class R>
 cudaError_t launch_op(int mode, const OpParams& prm, const Tables* t, const io_t<R>* u,
                       const io_t<R>* v, io_t<R>* out, int batch, cudaStream_t s) {
   if constexpr (std::is_same<R, double>::value) {
-    // R, J v and J^T w in double-float arithmetic on hexahedra
-    if (prm.arith == kArithDF && prm.dim == 3 && mode <= kVjp)
+    // R, J v, J^T w and block columns in double-float arithmetic on hexahedra
+    if (prm.arith == kArithDF && prm.dim == 3 && mode != kParam)
       return launch_op_df(mode, prm, u, v, out, batch, s);
   }
   if (prm.dim == 3) {

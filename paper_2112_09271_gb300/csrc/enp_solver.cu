@@ -852,6 +852,156 @@ __global__ void gj_invert(const TB* __restrict__ blocks, T* __restrict__ work, T
     for (int r = lane; r < n; r += 32) o[(long long)c * n + r] = (TS)A[(long long)r * ld + c];
 }
 
+// Gauss-Jordan inversion of one n x n block per thread block with the whole
+// matrix in registers (FP32 arithmetic): warp w owns the rows i = w + NW r
+// (r < RPW), lane l the columns j = l + 32 c (c < CPL); entries beyond n are
+// identity padding that no step changes. Partial pivoting without row
+// exchanges: step k pivots in place on (p, k), p the row not yet used with the
+// largest |M_pk| (the exchange step of Gauss-Jordan elimination):
+//   M_pj <- M_pj / M_pk (j != k),  M_pk <- 1 / M_pk,
+//   M_ik <- -M_ik / M_pk (i != p), M_ij <- M_ij - M_ik M_pj / M_pk otherwise;
+// after n steps with rows p_0..p_{n-1}, M_{p_k, j} = inv(A)_{k, p_j}. Two
+// barriers per step: the lanes owning column k publish it (double-buffered,
+// with |M_ik| or -1 for used rows), every warp finds the pivot from it in the
+// same order (so all agree), the warp owning row p publishes that row. The
+// inverse is staged in shared memory and written transposed, out[e][c][r] =
+// inv[r][c], in type TS. A pivot not above piv_rtol max|A_ij| (exactly zero
+// when piv_rtol = 0), or not finite, sets *singular.
+template <class TB, class TS, int NW, int RPW, int CPL>
+__global__ void __launch_bounds__(NW * 32, 1)
+gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
+               int* __restrict__ singular, float piv_rtol) {
+  constexpr int NR = NW * RPW;   // padded rows
+  constexpr int NC = 32 * CPL;   // padded columns
+  extern __shared__ __align__(16) unsigned char gsm[];
+  float* stage = reinterpret_cast<float*>(gsm);        // [n][n] transposed inverse
+  __shared__ float colv[2][NR], cola[2][NR];
+  __shared__ float rowv[NC];
+  __shared__ int piv[NC], stepof[NR];
+  __shared__ float s_wmax[NW];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const long long e = blockIdx.x;
+  const TB* src = blocks + e * (long long)n * n;
+  float M[RPW][CPL];
+  float amax = 0.f;
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int i = w + NW * r;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int j = lane + 32 * c;
+      const float a = (i < n && j < n) ? (float)src[(long long)i * n + j] : (i == j ? 1.f : 0.f);
+      M[r][c] = a;
+      if (i < n && j < n) amax = fmaxf(amax, fabsf(a));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, o));
+  if (lane == 0) s_wmax[w] = amax;
+  unsigned used = 0u;  // bit r: row w + NW r already a pivot row (same in every lane)
+  // column 0, published by lane 0 of every warp
+  if (lane == 0) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int i = w + NW * r;
+      colv[0][i] = M[r][0];
+      cola[0][i] = i < n ? fabsf(M[r][0]) : -1.f;
+    }
+  }
+  __syncthreads();
+  float thr = 0.f;
+  if (piv_rtol > 0.f) {
+    float mx = 0.f;
+    for (int t = 0; t < NW; ++t) mx = fmaxf(mx, s_wmax[t]);
+    thr = piv_rtol * mx;
+  }
+  bool bad = false;
+  for (int k = 0; k < n; ++k) {
+    const int buf = k & 1;
+    // the pivot row: argmax of |M_ik| over unused rows, ties to the lower row
+    float best = -1.f;
+    int bi = 0;
+    for (int t = lane; t < n; t += 32) {
+      const float v = cola[buf][t];
+      if (v > best) { best = v; bi = t; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (!(best > thr) || !isfinite(best)) { bad = true; break; }  // the same in every thread
+    const int p = bi;
+    const float pinv = 1.f / colv[buf][p];
+    if (w == p % NW) {
+      const int rp = p / NW;
+      used |= 1u << rp;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) v = r == rp ? M[r][c] : v;
+        rowv[lane + 32 * c] = v;
+      }
+    }
+    if (tid == 0) { piv[k] = p; stepof[p] = k; }
+    __syncthreads();
+    float rj[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int j = lane + 32 * c;
+      rj[c] = (j == k ? 1.f : rowv[j]) * pinv;
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int i = w + NW * r;
+      const float ci = colv[buf][i];
+      const bool isp = i == p;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int j = lane + 32 * c;
+        const float m = j == k ? 0.f : M[r][c];
+        M[r][c] = isp ? rj[c] : fmaf(-ci, rj[c], m);
+      }
+    }
+    // publish column k + 1 (its updated values) for the next step
+    const int kn = k + 1;
+    if (kn < n && lane == (kn & 31)) {
+      const int cn = kn >> 5;
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        float v = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) v = c == cn ? M[r][c] : v;
+        const int i = w + NW * r;
+        colv[buf ^ 1][i] = v;
+        cola[buf ^ 1][i] = (i < n && !((used >> r) & 1u)) ? fabsf(v) : -1.f;
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0) atomicOr(singular, 1);
+    return;
+  }
+  // inv[step(i)][p_j] = M_ij; out[c][r] = inv[r][c]: stage[p_j][step(i)]
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int i = w + NW * r;
+    if (i >= n) continue;
+    const int si = stepof[i];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int j = lane + 32 * c;
+      if (j < n) stage[piv[j] * n + si] = M[r][c];
+    }
+  }
+  __syncthreads();
+  TS* o = out + e * (long long)n * n;
+  for (int t = tid; t < n * n; t += NW * 32) o[t] = (TS)stage[t];
+}
+
 // One plane of the downwind block Gauss-Seidel sweep: the elements whose
 // coordinate along axis a is k, one per thread block. t = x_e minus the
 // upstream face terms J_(e,up) z_up that the face kernel left in the face buffer
@@ -1492,7 +1642,28 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
       e = cudaGetLastError();                                                                   \
     }                                                                                           \
   }
-  if (storage == 0) {
+  // FP32 inversion of blocks up to 192 x 192: the register-resident kernel
+#define ENP_GJR(TS, NW, RPW, CPL)                                                                 \
+  {                                                                                               \
+    auto k = enp::gj_invert_regs<float, TS, NW, RPW, CPL>;                                        \
+    const size_t sm = sizeof(float) * (size_t)nb * nb;                                            \
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);            \
+    if (e == cudaSuccess) {                                                                       \
+      k<<<(unsigned)nblk, NW * 32, sm, h->stream>>>(S.blocks32, (TS*)S.binv, nb, S.d_flag, 0.f);  \
+      e = cudaGetLastError();                                                                     \
+    }                                                                                             \
+  }
+#define ENP_GJR_ANY(TS)                                          \
+  if (nb <= 32) ENP_GJR(TS, 4, 8, 1)                             \
+  else if (nb <= 64) ENP_GJR(TS, 8, 8, 2)                        \
+  else if (nb <= 96) ENP_GJR(TS, 8, 12, 3)                       \
+  else if (nb <= 128) ENP_GJR(TS, 16, 8, 4)                      \
+  else ENP_GJR(TS, 16, 12, 6)
+  const bool regs = !f64 && nb <= 192;
+  if (regs) {
+    if (storage == 1) ENP_GJR_ANY(float)
+    else ENP_GJR_ANY(__nv_bfloat16)
+  } else if (storage == 0) {
     if (in_smem) ENP_GJ(double, double, true, double, S.blocks) else ENP_GJ(double, double, false, double, S.blocks)
   } else if (storage == 1) {
     if (in_smem) ENP_GJ(float, float, true, float, S.blocks32) else ENP_GJ(float, float, false, float, S.blocks32)
@@ -1501,6 +1672,8 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     else ENP_GJ(float, __nv_bfloat16, false, float, S.blocks32)
   }
 #undef ENP_GJ
+#undef ENP_GJR_ANY
+#undef ENP_GJR
   if (e != cudaSuccess) return cuda_err(h, e, "block inversion");
   int flag = 0;
   e = cudaMemcpyAsync(&flag, S.d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);

@@ -1,4 +1,4 @@
-// Entry of the double-float hexahedral operator: R(u), J(u)v and J(u)^T w with
+// Entry of the double-float hexahedral operator: R(u), J(u)v, J(u)^T w and block columns with
 // FP64 vectors in and out and double-float arithmetic on the FP32 pipe (the
 // FP64-accurate operator). The kernels of each degree live in op_df_p<p>.cu.
 #include "enp_op_dispatch.cuh"

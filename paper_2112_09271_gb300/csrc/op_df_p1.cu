@@ -1,3 +1,3 @@
-// Double-float hexahedral operator kernels of degree p = 1 (R, J v, J^T w).
+// Double-float hexahedral operator kernels of degree p = 1 (R, J v, J^T w, block columns).
 #include "enp_op_dispatch.cuh"
 ENP_DF_DEGREE(1)

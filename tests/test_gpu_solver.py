@@ -44,15 +44,19 @@ BLOCK_CASES = ["cube_n3_p2", "cube_n2_p3", "channel_n1", "mms2d_n3", "reactor_n1
 def _prob(cfg):
     if cfg == "channel_n1":
         return W.config(cfg, p=2)
+    if cfg == "channel_n1_p3":
+        return W.config("channel_n1", p=3)
     return W.config(cfg)
 
 
+@pytest.mark.parametrize("arith", ["f64", "df32"])
 @pytest.mark.parametrize("cfg", BLOCK_CASES)
-def test_block_diagonal_matches_oracle(cfg):
+def test_block_diagonal_matches_oracle(cfg, arith):
     enp = _enp()
     P = _prob(cfg)
     dirv = W.random_dirichlet(P, 7)
     op = enp.Operator(P)
+    op.set_arithmetic(enp.ARITH_DF32 if arith == "df32" else enp.ARITH_F64)
     op.set_sources(None, _cuda(dirv))
     orc = oracle.Oracle(P, dirichlet=dirv)
     u = W.random_state(P, 2)
@@ -62,7 +66,9 @@ def test_block_diagonal_matches_oracle(cfg):
     assert _rel(g, ref) < 1e-12
 
 
-@pytest.mark.parametrize("cfg", ["cube_n3_p2", "cube_n2_p3", "channel_n1"])
+# block sizes 16, 54, 81, 128 and 192 (every shape of the FP32 register inversion)
+@pytest.mark.parametrize("cfg", ["cube_n3_p1", "cube_n3_p2", "cube_n2_p3", "channel_n1",
+                                 "channel_n1_p3"])
 @pytest.mark.parametrize("storage,tol", [(0, 1e-14), (1, 1e-5), (2, 2e-2)])
 def test_block_jacobi_apply_matches_oracle(cfg, storage, tol):
     enp = _enp()
