@@ -308,13 +308,16 @@ def run_solves(enp, W, name, labels=None, reference="fp64"):
 
 
 def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
-                      labels=("fp64", "mixed", "mixed_sweep", "mixed_paper_guess")):
+                      labels=("fp64", "mixed", "mixed_device_loop", "mixed_sweep",
+                              "mixed_paper_guess")):
     """The operating-point sweep of the plate reactor (Sec. 5.2): `batch`
     applied cathode potentials from volts[0] to volts[1] (anode at 0), all
     solved in one batched Newton run per stage, with continuation in the
     applied potential (Butler-Volmer exponents reach e^31 at 0.8 V, beyond the
     reach of Newton from a plain guess), the two-level preconditioner and FGMRES
-    restart cycles replayed from a captured CUDA graph. FP64 and mixed (FP32
+    restart cycles replayed from a captured CUDA graph (`_device_loop`: every
+    Newton iteration one graph launch with device-side loops over the cycles,
+    the line search and the steps). FP64 and mixed (FP32
     inner operator, FP32 block inverses); initial guess c = c_in,
     Phi = phi_app / 2 at the first stage, or (`_paper_guess`) the initial guess
     of Sec. 4.3 at the first stage's potentials (Phi from the charge equation
@@ -336,7 +339,8 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
     kws = {"fp64": dict(bj_storage=enp.BJ_F64, mixed=False),
            "mixed": dict(bj_storage=enp.BJ_F32, mixed=True),
            "mixed_sweep": dict(bj_storage=enp.BJ_F32, mixed=True),
-           "mixed_paper_guess": dict(bj_storage=enp.BJ_F32, mixed=True)}
+           "mixed_paper_guess": dict(bj_storage=enp.BJ_F32, mixed=True),
+           "mixed_device_loop": dict(bj_storage=enp.BJ_F32, mixed=True, device_loop=True)}
     for label in labels:
         op.set_sweep(1 if label.endswith("_sweep") else 0)
         u = torch.tensor(u0, device="cuda")
@@ -672,8 +676,9 @@ def main():
         solve = run_solves(enp, W, args.solve_workload)
         full = args.reactor_workload.startswith("reactor192")
         batched = run_batched_solve(enp, W, args.reactor_workload,
-                                    labels=("mixed", "mixed_sweep", "mixed_paper_guess") if full
-                                    else ("fp64", "mixed", "mixed_sweep", "mixed_paper_guess"))
+                                    labels=("mixed", "mixed_device_loop", "mixed_sweep") if full
+                                    else ("fp64", "mixed", "mixed_device_loop", "mixed_sweep",
+                                          "mixed_paper_guess"))
         if args.channel_solve:
             solve_channel = run_solves(enp, W, "channel64_p3", labels=CHANNEL_SOLVE_VARIANTS,
                                        reference="fp64_df32_two_level")

@@ -309,6 +309,15 @@ typedef struct {
                             (<= 1: every iteration), and after an inner solve that did
                             not converge; between rebuilds the preconditioner of an
                             earlier iterate is kept (FGMRES needs no exact one) */
+  int device_loop;       /* 1: the Newton iterations between preconditioner setups run
+                            as one CUDA graph launch whose conditional WHILE nodes loop
+                            over the FGMRES restart cycles, the line-search trial steps
+                            and the Newton steps, with device-side iteration counts and
+                            stopping tests (the host acts once per setup; the graph is
+                            captured on the first call and reused while the
+                            preconditioner, the sizes and the options stay the same).
+                            Same iterates as 0 (the eager loop), up to the rounding of
+                            whole restart cycles: converged points are frozen. */
 } enp_newton_opts;
 
 typedef struct {

@@ -118,7 +118,7 @@ class NewtonOpts(ctypes.Structure):
     _fields_ = [("max_it", ctypes.c_int), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("max_backtracks", ctypes.c_int),
                 ("bj_storage", ctypes.c_int), ("mixed", ctypes.c_int), ("krylov", KrylovOpts),
-                ("pc_lag", ctypes.c_int)]
+                ("pc_lag", ctypes.c_int), ("device_loop", ctypes.c_int)]
 
 
 class NewtonStats(ctypes.Structure):
@@ -431,12 +431,14 @@ class Operator:
     def newton_solve(self, u, max_it=20, rtol=1e-10, atol=0.0, armijo_c=1e-4,
                      max_backtracks=12, bj_storage=BJ_F64, mixed=False, krylov_restart=30,
                      krylov_max_it=500, krylov_rtol=1e-3, raise_on_fail=True, graph=False,
-                     pc_lag=1):
-        """Newton with backtracking line search in place on u; returns the stats."""
+                     pc_lag=1, device_loop=False):
+        """Newton with backtracking line search in place on u; returns the stats.
+        device_loop: the Newton iterations between preconditioner setups as one
+        graph launch with device-side loops."""
         import torch
         o = NewtonOpts(max_it, rtol, atol, armijo_c, max_backtracks, bj_storage, int(mixed),
                        KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0, int(graph)),
-                       int(pc_lag))
+                       int(pc_lag), int(device_loop))
         st = NewtonStats()
         rc = self._lib.enp_newton_solve(self.h, _dptr(u, torch.float64), ctypes.byref(o),
                                         ctypes.byref(st))
@@ -450,14 +452,14 @@ class Operator:
     def initial_guess(self, u, max_it=30, rtol=1e-8, atol=0.0, armijo_c=1e-4,
                       max_backtracks=12, bj_storage=BJ_F64, mixed=False, krylov_restart=50,
                       krylov_max_it=4000, krylov_rtol=1e-2, raise_on_fail=True, graph=False,
-                      pc_lag=1):
+                      pc_lag=1, device_loop=False):
         """The initial guess of Sec. 4.3 in place on u: c = c_in everywhere and
         Phi from the charge-conservation equation at constant c, by Newton from
         the Phi in u (inner FGMRES to 1e-2, as the paper); returns the stats."""
         import torch
         o = NewtonOpts(max_it, rtol, atol, armijo_c, max_backtracks, bj_storage, int(mixed),
                        KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0, int(graph)),
-                       int(pc_lag))
+                       int(pc_lag), int(device_loop))
         st = NewtonStats()
         rc = self._lib.enp_initial_guess(self.h, _dptr(u, torch.float64), ctypes.byref(o),
                                          ctypes.byref(st))
@@ -472,7 +474,8 @@ class Operator:
                             grow=1.5, stage_rtol=1e-6, stage_max_it=10, max_it=30, rtol=1e-10,
                             atol=0.0, armijo_c=1e-4, max_backtracks=12, bj_storage=BJ_F64,
                             mixed=False, krylov_restart=50, krylov_max_it=4000,
-                            krylov_rtol=1e-3, graph=False, pc_lag=1, raise_on_fail=True):
+                            krylov_rtol=1e-3, graph=False, pc_lag=1, raise_on_fail=True,
+                            device_loop=False):
         """Continuation in the applied potential up to phi_app ([batch][4]), in
         place on u; returns the stats (the last stage's Newton stats under 'last')."""
         import numpy as np
@@ -481,7 +484,7 @@ class Operator:
         c = ContinuationOpts(step0, step_max, step_min, grow, stage_rtol, stage_max_it)
         o = NewtonOpts(max_it, rtol, atol, armijo_c, max_backtracks, bj_storage, int(mixed),
                        KrylovOpts(krylov_restart, krylov_max_it, krylov_rtol, 0.0, int(graph)),
-                       int(pc_lag))
+                       int(pc_lag), int(device_loop))
         st = ContinuationStats()
         rc = self._lib.enp_newton_continuation(
             self.h, _dptr(u, torch.float64), ph.ctypes.data_as(ctypes.c_void_p),

@@ -1103,6 +1103,124 @@ __global__ void bj_apply_kernel(const TS* __restrict__ BT, const TV* __restrict_
   }
 }
 
+// ------------------------------------------------- graph-driven Newton iteration
+// Device-side control of a Newton solve whose iterations run as one CUDA graph
+// launch with conditional WHILE nodes (the FGMRES restart cycles, the
+// backtracking line search, and the Newton steps between preconditioner
+// setups): the host takes part once per setup.
+struct NewtonCtl {
+  int it;          // Newton iterations of the solve
+  int since;       // Newton iterations since the last preconditioner setup
+  int kry_total;   // FGMRES iterations of the solve
+  int kry_solve;   // FGMRES iterations of the current inner solve
+  int bt;          // backtracking steps of the current line search
+  int nonfinite;   // a non-finite residual or Krylov value
+  int kfail;       // an inner solve stopped at its iteration limit
+  int pad;
+  double hist[64]; // largest ||R|| after each Newton iteration
+};
+
+struct NewtonDev {
+  double *rn, *tol, *lam, *rnew2, *negmask;  // [B]
+  int *mask, *acc;                           // [B]
+  NewtonCtl* c;
+};
+
+__global__ void ng_arm(cudaGraphConditionalHandle h) { cudaGraphSetConditional(h, 1u); }
+
+// Start of a Newton iteration: the running points (||R|| above tolerance), the
+// right-hand-side scale -1 / 0, full steps for the line search.
+__global__ void ng_begin(NewtonDev A, int B) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int run = A.rn[b] > A.tol[b] ? 1 : 0;
+    A.mask[b] = run;
+    A.negmask[b] = run ? -1.0 : 0.0;
+    A.lam[b] = run ? 1.0 : 0.0;
+    A.acc[b] = run ? 0 : 1;
+  }
+  if (threadIdx.x == 0) { A.c->kry_solve = 0; A.c->bt = 0; }
+}
+
+// After an FGMRES restart cycle: count its iterations (up to each point's
+// convergence when the cycle finished every point), and continue while a point
+// runs, the inner limit is not reached and nothing is non-finite.
+__global__ void ng_krylov_count(KrylovDev K, NewtonDev A, const int* __restrict__ dflag, int B,
+                                int m, int max_it, cudaGraphConditionalHandle h) {
+  __shared__ int s_used;
+  if (threadIdx.x == 0) s_used = 0;
+  __syncthreads();
+  int running = 0, used = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int j = K.jconv[b];
+    if (j == -1) running = 1;
+    if (j >= 0) used = max(used, j + 1);
+  }
+  atomicMax(&s_used, used);
+  running = __syncthreads_or(running);
+  if (threadIdx.x == 0) {
+    const int its = A.c->kry_solve + (running ? m : s_used);
+    A.c->kry_solve = its;
+    const int nonf = dflag[1];
+    if (nonf) A.c->nonfinite = 1;
+    if (running && its >= max_it) A.c->kfail = 1;
+    cudaGraphSetConditional(h, (running && its < max_it && !nonf) ? 1u : 0u);
+  }
+}
+
+// Armijo test of every point still searching: accept, or halve its step.
+__global__ void ng_ls_accept(NewtonDev A, int B, double c_armijo, int max_bt,
+                             cudaGraphConditionalHandle h) {
+  const int bt = A.c->bt;
+  int any = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    if (A.acc[b]) continue;
+    const double rnew = sqrt(A.rnew2[b]);
+    if (rnew <= (1.0 - c_armijo * A.lam[b]) * A.rn[b] || bt >= max_bt) {
+      A.acc[b] = 1;
+    } else {
+      A.lam[b] *= 0.5;
+      any = 1;
+    }
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    A.c->bt = bt + 1;
+    cudaGraphSetConditional(h, any ? 1u : 0u);
+  }
+}
+
+// End of a Newton iteration: the new norms, the history, and whether to go on
+// (a point above tolerance, under the iteration limit, and the preconditioner
+// still within its lag).
+__global__ void ng_end(NewtonDev A, int B, int max_it, int per_setup,
+                       cudaGraphConditionalHandle h) {
+  __shared__ unsigned long long s_max;
+  if (threadIdx.x == 0) s_max = 0ull;
+  __syncthreads();
+  int any = 0, nonf = 0;
+  double mx = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double r = sqrt(A.rnew2[b]);
+    A.rn[b] = r;
+    if (!isfinite(r)) nonf = 1;
+    if (r > A.tol[b]) any = 1;
+    mx = fmax(mx, isnan(r) ? INFINITY : r);
+  }
+  atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));  // non-negative: bits ordered
+  any = __syncthreads_or(any);
+  nonf = __syncthreads_or(nonf);
+  if (threadIdx.x == 0) {
+    NewtonCtl* c = A.c;
+    c->kry_total += c->kry_solve;
+    c->it += 1;
+    c->since += 1;
+    if (c->it < 64) c->hist[c->it] = __longlong_as_double((long long)s_max);
+    if (nonf) c->nonfinite = 1;
+    const bool go = any && c->it < max_it && c->since < per_setup && !c->nonfinite && !c->kfail;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+  }
+}
+
 }  // namespace enp
 
 // ====================================================================== host
@@ -1145,6 +1263,16 @@ struct SolverState {
   size_t gbuf_bytes = 0;
   const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
   int gkey_i[4] = {0, 0, 0, 0};
+  // graph-driven Newton iteration (enp_newton_opts.device_loop): the graph, the
+  // streams its nested bodies were captured on, handle-owned copies of the
+  // Newton vectors, the device control block, and the key it was captured for
+  cudaStream_t nstream[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t nexec = nullptr;
+  void* nbuf = nullptr;           // u, r, du, ut, rt (FP64) [+ u, b, x in FP32]
+  size_t nbuf_bytes = 0;
+  void* nsmall = nullptr;         // NewtonCtl + per-point arrays
+  size_t nsmall_bytes = 0;
+  std::vector<char> nkey;
   // preconditioner generation: bumped whenever its configuration changes or a
   // buffer it reads is reallocated, so that a captured FGMRES cycle is replayed
   // only with the preconditioner it was captured with
@@ -1506,6 +1634,10 @@ cudaError_t coarse_apply(enp_handle h, const TV* r, TV* z) {
 void enp_solver_free(enp_handle h) {
   if (!h || !h->solver) return;
   SolverState& S = h->solver->s;
+  if (S.nexec) cudaGraphExecDestroy(S.nexec);
+  for (auto& st : S.nstream)
+    if (st) cudaStreamDestroy(st);
+  cudaFree(S.nbuf); cudaFree(S.nsmall);
   cudaFree(S.blocks); cudaFree(S.binv); cudaFree(S.gj_work); cudaFree(S.d_flag);
   cudaFree(S.blocks32); cudaFree(S.u32);
   cudaFree(S.part); cudaFree(S.dsmall); cudaFree(S.V); cudaFree(S.dRdtheta);
@@ -2232,9 +2364,315 @@ extern "C" enp_status enp_fgmres_solve_f32(enp_handle h, const float* u_lin, con
 // its tolerance gets a zero right-hand side (FGMRES leaves it at du = 0). The
 // block-Jacobi preconditioner is rebuilt at every Newton iterate. Norms in the
 // statistics are the largest over the operating points.
+// ---------------------------------------------------------------------------
+// Graph-driven Newton iteration. One CUDA graph holds a WHILE node over Newton
+// steps; its body forms -R on the running points, solves J du = -R by FGMRES
+// (a WHILE node over restart cycles, each cycle the sequence of fgmres_graph),
+// runs the backtracking line search (a WHILE node over trial steps) and
+// updates u and R. Device kernels count iterations and set the loop
+// conditions, so one launch carries the solve from one preconditioner setup to
+// the next (opts->pc_lag Newton steps), to convergence, to max_it, or to an
+// inner solve that stopped at its limit; the host sets up the preconditioner
+// between launches. The Newton vectors live in handle-owned buffers (u is
+// copied in and out) so that the captured graph is reused across calls.
+
+// The graph being captured on stream s, and a conditional handle in it.
+static cudaError_t capture_handle(cudaStream_t s, cudaGraphConditionalHandle* hnd) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+  return cudaGraphConditionalHandleCreate(hnd, g, 1, cudaGraphCondAssignDefault);
+}
+
+// Append a WHILE node on handle hnd at the capture point of stream s and start
+// capturing its body on stream sb.
+static cudaError_t begin_while(cudaStream_t s, cudaStream_t sb, cudaGraphConditionalHandle hnd) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hnd;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+      cudaSuccess)
+    return e;
+  return cudaStreamBeginCaptureToGraph(sb, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeRelaxed);
+}
+
+static cudaError_t end_while(cudaStream_t sb) {
+  cudaGraph_t g = nullptr;
+  return cudaStreamEndCapture(sb, &g);
+}
+
+template <class TV>
+static enp_status newton_device(enp_handle h, double* u_user, const enp_newton_opts* o,
+                                enp_newton_stats* st) {
+  SolverState& S = state_of(h);
+  const OpParams& P = h->prm;
+  constexpr bool mixed = std::is_same<TV, float>::value;
+  const long long n = h->n_dof;
+  const int B = h->batch;
+  const long long ntot = n * B;
+  const int m = std::max(1, std::min(o->krylov.restart, 255));
+  const int per_setup = std::max(o->pc_lag, 1);
+  cudaStream_t user = h->stream;
+  cudaError_t e;
+  using clk = std::chrono::steady_clock;
+  auto seconds_since = [](clk::time_point t0) {
+    return std::chrono::duration<double>(clk::now() - t0).count();
+  };
+  auto fail = [&](cudaError_t er, const char* what) { h->stream = user; return cuda_err(h, er, what); };
+  // handle-owned Newton vectors
+  const size_t vb64 = sizeof(double) * ntot, vb32 = sizeof(float) * ntot;
+  const size_t nbuf_need = 5 * vb64 + (mixed ? 3 * vb32 : 0);
+  if (S.nbuf_bytes < nbuf_need) {
+    if (S.nexec) { cudaGraphExecDestroy(S.nexec); S.nexec = nullptr; }
+    cudaFree(S.nbuf); S.nbuf = nullptr; S.nbuf_bytes = 0;
+    if ((e = cudaMalloc(&S.nbuf, nbuf_need)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc newton vectors");
+    S.nbuf_bytes = nbuf_need;
+  }
+  double* u = (double*)S.nbuf;
+  double *r = u + ntot, *du = r + ntot, *ut = du + ntot, *rt = ut + ntot;
+  float* u32 = mixed ? (float*)(rt + ntot) : nullptr;
+  float* b32 = mixed ? u32 + ntot : nullptr;
+  float* x32 = mixed ? b32 + ntot : nullptr;
+  const size_t nsm_need = sizeof(enp::NewtonCtl) + (size_t)B * (5 * sizeof(double) + 2 * sizeof(int));
+  if (S.nsmall_bytes < nsm_need) {
+    if (S.nexec) { cudaGraphExecDestroy(S.nexec); S.nexec = nullptr; }
+    cudaFree(S.nsmall); S.nsmall = nullptr; S.nsmall_bytes = 0;
+    if ((e = cudaMalloc(&S.nsmall, nsm_need)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc newton state");
+    S.nsmall_bytes = nsm_need;
+  }
+  enp::NewtonDev A;
+  A.c = (enp::NewtonCtl*)S.nsmall;
+  A.rn = (double*)(A.c + 1);
+  A.tol = A.rn + B; A.lam = A.tol + B; A.rnew2 = A.lam + B; A.negmask = A.rnew2 + B;
+  A.mask = (int*)(A.negmask + B); A.acc = A.mask + B;
+  for (auto& sx : S.nstream)
+    if (!sx && (e = cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_err(h, e, "create graph streams");
+  // u in, the initial residual and tolerances (eager, on the caller's stream)
+  cudaMemcpyAsync(u, u_user, vb64, cudaMemcpyDeviceToDevice, user);
+  if ((e = apply_residual(h, u, r, B)) != cudaSuccess ||
+      (e = multidot<double>(h, r, 0, 1, r, A.rnew2)) != cudaSuccess)
+    return cuda_err(h, e, "newton residual");
+  std::vector<double> r0(B), tol(B), rnh(B);
+  cudaMemcpyAsync(r0.data(), A.rnew2, sizeof(double) * B, cudaMemcpyDeviceToHost, user);
+  if ((e = cudaStreamSynchronize(user)) != cudaSuccess) return cuda_err(h, e, "newton sync");
+  double r0max = 0.0;
+  for (int b = 0; b < B; ++b) {
+    r0[b] = std::sqrt(r0[b]);
+    if (!std::isfinite(r0[b])) { h->err = "non-finite initial residual"; return ENP_ERR_NONFINITE; }
+    tol[b] = std::max(o->rtol * r0[b], o->atol);
+    r0max = std::max(r0max, r0[b]);
+  }
+  cudaMemcpyAsync(A.rn, r0.data(), sizeof(double) * B, cudaMemcpyHostToDevice, user);
+  cudaMemcpyAsync(A.tol, tol.data(), sizeof(double) * B, cudaMemcpyHostToDevice, user);
+  cudaMemsetAsync(A.c, 0, sizeof(enp::NewtonCtl), user);
+  // Krylov workspace (as fgmres_graph)
+  const size_t vbytes = sizeof(TV) * ntot;
+  const size_t kneed = vbytes * (size_t)(2 * m + 1);
+  if (S.krylov_bytes < kneed) {
+    if (S.gexec) { cudaGraphExecDestroy(S.gexec); S.gexec = nullptr; }
+    cudaFree(S.V); S.V = nullptr; S.krylov_bytes = 0;
+    if ((e = cudaMalloc(&S.V, kneed)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc Krylov basis");
+    S.krylov_bytes = kneed;
+  }
+  const size_t nH = (size_t)B * (m + 1) * m, nG = (size_t)B * (m + 1), nM = (size_t)B * m;
+  const size_t nsmallk = nH + 2 * nG + 2 * nM + nM + (size_t)B * (m + 1) + 7 * (size_t)B + 4;
+  enp_newton_stats acc{};
+  acc.initial_norm = r0max;
+  acc.history[0] = r0max;
+  int setups = 0;
+  double t_setup = 0.0, t_graph = 0.0;
+  enp_status status = ENP_OK;
+  enp::NewtonCtl ch{};
+  while (true) {
+    cudaMemcpyAsync(&ch, A.c, sizeof(ch), cudaMemcpyDeviceToHost, user);
+    cudaMemcpyAsync(rnh.data(), A.rn, sizeof(double) * B, cudaMemcpyDeviceToHost, user);
+    if ((e = cudaStreamSynchronize(user)) != cudaSuccess) return cuda_err(h, e, "newton sync");
+    if (ch.nonfinite) { status = ENP_ERR_NONFINITE; h->err = "non-finite residual"; break; }
+    bool conv = true;
+    for (int b = 0; b < B; ++b) conv = conv && rnh[b] <= tol[b];
+    if (conv) break;
+    if (ch.it >= o->max_it) { status = ENP_ERR_NOT_CONVERGED; h->err = "Newton reached max_it"; break; }
+    // preconditioner at the current u, then up to per_setup Newton steps on the device
+    const auto t0 = clk::now();
+    enp_status s2 = enp_block_jacobi_setup(h, u, o->bj_storage);  // synchronises
+    t_setup += seconds_since(t0);
+    ++setups;
+    if (s2 != ENP_OK) { status = s2; break; }
+    cudaMemsetAsync(&A.c->since, 0, sizeof(int), user);
+    cudaMemsetAsync(&A.c->kfail, 0, sizeof(int), user);
+    if ((e = small(h, nsmallk)) != cudaSuccess) return cuda_err(h, e, "cudaMalloc small");
+    if ((e = ensure(&S.part, S.part_count, (size_t)B * (m + 1) * enp::kRedBlocks)) != cudaSuccess)
+      return cuda_err(h, e, "cudaMalloc partials");
+    // the capture key: every pointer and setting the captured sequence bakes in,
+    // including the operator parameters the kernels receive by value
+    const double kv[] = {
+        (double)(uintptr_t)S.V, (double)(uintptr_t)S.binv, (double)(uintptr_t)S.dsmall,
+        (double)(uintptr_t)S.part, (double)(uintptr_t)S.nbuf, (double)(uintptr_t)S.nsmall,
+        (double)m, (double)S.storage, (double)sizeof(TV), (double)B, (double)S.pc_gen,
+        (double)S.potential_only, o->krylov.rtol, o->krylov.atol, (double)o->krylov.max_it,
+        (double)o->max_it, o->armijo_c, (double)o->max_backtracks, (double)per_setup};
+    std::vector<char> key(sizeof(kv) + sizeof(OpParams));
+    std::memcpy(key.data(), kv, sizeof(kv));
+    std::memcpy(key.data() + sizeof(kv), &P, sizeof(OpParams));
+    if (!S.nexec || S.nkey != key) {
+      if (S.nexec) { cudaGraphExecDestroy(S.nexec); S.nexec = nullptr; }
+      double* q = S.dsmall;
+      enp::KrylovDev K;
+      K.H = q; q += nH;
+      K.g = q; q += nG;
+      K.hcol = q; q += nG;
+      K.cs = q; q += nM;
+      K.sn = q; q += nM;
+      K.coef = q; q += nM;
+      K.dh = q; q += (size_t)B * (m + 1);
+      K.hn2 = q; q += B;
+      K.inv = q; q += B;
+      K.beta = q; q += B;
+      K.bn2 = q; q += B;
+      K.tol = q; q += B;
+      K.resn = q; q += B;
+      int* dflag = reinterpret_cast<int*>(q + B);
+      K.jconv = reinterpret_cast<int*>(q);
+      TV* V = (TV*)S.V;
+      TV* Z = (TV*)((char*)S.V + vbytes * (m + 1));
+      const long long vs = ntot;
+      TV* xk = mixed ? (TV*)x32 : (TV*)du;
+      const TV* bk = mixed ? (const TV*)b32 : (const TV*)rt;
+      const TV* uk = mixed ? (const TV*)u32 : (const TV*)u;
+      const bool precond = S.storage >= 0;
+      const int gx = grid_for(n), gt = grid_for(ntot);
+      const dim3 gv(gx, B);
+      const int tb = std::min(B, 256), gbk = (B + tb - 1) / tb;
+      // one eager J v launch so that every kernel's attributes are set outside capture
+      if (mixed) enp::convert_kernel<double, float><<<gt, 256, 0, user>>>(u, u32, ntot);
+      cudaMemsetAsync(xk, 0, vbytes, user);
+      if ((e = apply_jv<TV>(h, P, uk, xk, (TV*)V, B)) != cudaSuccess) return fail(e, "newton warm-up");
+      if ((e = cudaStreamSynchronize(user)) != cudaSuccess) return fail(e, "newton warm-up");
+      cudaStream_t s0 = S.nstream[0], s1 = S.nstream[1], s2s = S.nstream[2];
+      cudaGraph_t graph = nullptr;
+      cudaGraphConditionalHandle hN, hK, hL;
+      auto capture = [&]() -> cudaError_t {
+        cudaError_t er;
+        h->stream = s0;
+        if ((er = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return er;
+        if ((er = capture_handle(s0, &hN)) != cudaSuccess) return er;
+        if ((er = begin_while(s0, s1, hN)) != cudaSuccess) return er;
+        h->stream = s1;
+        enp::ng_begin<<<1, 256, 0, s1>>>(A, B);
+        enp::scale_batched<<<gt, 256, 0, s1>>>(r, A.negmask, rt, n, B);
+        if (mixed) {
+          enp::convert_kernel<double, float><<<gt, 256, 0, s1>>>(u, u32, ntot);
+          enp::convert_kernel<double, float><<<gt, 256, 0, s1>>>(rt, b32, ntot);
+        }
+        cudaMemsetAsync(xk, 0, vbytes, s1);
+        multidot<TV>(h, bk, 0, 1, bk, K.bn2);
+        enp::krylov_tolerance<<<gbk, tb, 0, s1>>>(K, B, o->krylov.rtol, o->krylov.atol);
+        // FGMRES restart cycles
+        if ((er = capture_handle(s1, &hK)) != cudaSuccess) return er;
+        enp::ng_arm<<<1, 1, 0, s1>>>(hK);
+        if ((er = begin_while(s1, s2s, hK)) != cudaSuccess) return er;
+        h->stream = s2s;
+        apply_jv<TV>(h, P, uk, xk, V, B);
+        enp::b_minus<TV><<<gt, 256, 0, s2s>>>(bk, V, ntot);
+        multidot<TV>(h, V, 0, 1, V, K.dh);
+        cudaMemsetAsync(dflag, 0, 2 * sizeof(int), s2s);
+        enp::krylov_cycle_init<<<gbk, tb, 0, s2s>>>(K, B, m, dflag, dflag + 1);
+        enp::scale_copy<TV, TV><<<gv, 256, 0, s2s>>>(V, K.inv, 0.0, V, n, n);
+        for (int j = 0; j < m; ++j) {
+          TV* vj = V + j * vs;
+          TV* zj = Z + j * vs;
+          TV* w = V + (j + 1) * vs;
+          if (precond) bj_apply_any<TV>(h, vj, zj);
+          else cudaMemcpyAsync(zj, vj, vbytes, cudaMemcpyDeviceToDevice, s2s);
+          apply_jv<TV>(h, P, uk, zj, w, B);
+          arnoldi_orthogonalise<TV>(h, K, V, vs, j, w, m, dflag + 1);
+          enp::scale_copy<TV, TV><<<gv, 256, 0, s2s>>>(w, K.inv, 0.0, w, n, n);
+        }
+        enp::krylov_solve_upper<<<gbk, tb, 0, s2s>>>(K, B, m, m);
+        enp::combine<TV, TV><<<gv, 256, 0, s2s>>>(Z, vs, m, K.coef, m, xk, n, n, 1);
+        enp::ng_krylov_count<<<1, 256, 0, s2s>>>(K, A, dflag, B, m, o->krylov.max_it, hK);
+        if ((er = end_while(s2s)) != cudaSuccess) return er;
+        h->stream = s1;
+        if (mixed) enp::convert_kernel<float, double><<<gt, 256, 0, s1>>>(x32, du, ntot);
+        // backtracking line search
+        if ((er = capture_handle(s1, &hL)) != cudaSuccess) return er;
+        enp::ng_arm<<<1, 1, 0, s1>>>(hL);
+        if ((er = begin_while(s1, s2s, hL)) != cudaSuccess) return er;
+        h->stream = s2s;
+        enp::axpy_batched<<<gt, 256, 0, s2s>>>(u, A.lam, du, ut, n, B);
+        apply_residual(h, ut, rt, B);
+        multidot<double>(h, rt, 0, 1, rt, A.rnew2);
+        enp::ng_ls_accept<<<1, 256, 0, s2s>>>(A, B, o->armijo_c, o->max_backtracks, hL);
+        if ((er = end_while(s2s)) != cudaSuccess) return er;
+        h->stream = s1;
+        cudaMemcpyAsync(u, ut, vb64, cudaMemcpyDeviceToDevice, s1);
+        cudaMemcpyAsync(r, rt, vb64, cudaMemcpyDeviceToDevice, s1);
+        enp::ng_end<<<1, 256, 0, s1>>>(A, B, o->max_it, per_setup, hN);
+        if ((er = end_while(s1)) != cudaSuccess) return er;
+        h->stream = s0;
+        return cudaStreamEndCapture(s0, &graph);
+      };
+      e = capture();
+      h->stream = user;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&S.nexec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        // leave no stream in capture mode
+        for (auto sx : S.nstream) {
+          cudaStreamCaptureStatus cs;
+          if (cudaStreamIsCapturing(sx, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g2 = nullptr;
+            cudaStreamEndCapture(sx, &g2);
+            if (g2) cudaGraphDestroy(g2);
+          }
+        }
+        cudaGetLastError();
+        S.nexec = nullptr;
+        return cuda_err(h, e, "capture Newton graph");
+      }
+      S.nkey = key;
+    }
+    const auto tg = clk::now();
+    if ((e = cudaGraphLaunch(S.nexec, user)) != cudaSuccess) return cuda_err(h, e, "Newton graph launch");
+    if ((e = cudaStreamSynchronize(user)) != cudaSuccess) return cuda_err(h, e, "Newton graph");
+    t_graph += seconds_since(tg);
+  }
+  cudaMemcpyAsync(u_user, u, vb64, cudaMemcpyDeviceToDevice, user);
+  cudaStreamSynchronize(user);
+  if (st) {
+    *st = acc;
+    st->iterations = ch.it;
+    st->krylov_iterations = ch.kry_total;
+    st->setups = setups;
+    st->setup_seconds = t_setup;
+    st->krylov_seconds = t_graph;
+    double mx = 0.0;
+    for (double x : rnh) mx = std::max(mx, std::isnan(x) ? INFINITY : x);
+    st->residual_norm = mx;
+    for (int i = 1; i < 64 && i <= ch.it; ++i) st->history[i] = ch.hist[i];
+    st->converged = status == ENP_OK ? 1 : 0;
+  }
+  return status;
+}
+
 extern "C" enp_status enp_newton_solve(enp_handle h, double* u, const enp_newton_opts* o,
                                        enp_newton_stats* st) {
   if (!h || !u || !o || o->max_it < 0) return ENP_ERR_INVALID_ARG;
+  if (o->device_loop) return o->mixed ? newton_device<float>(h, u, o, st) : newton_device<double>(h, u, o, st);
   SolverState& S = state_of(h);
   const long long n = h->n_dof;
   const long long ntot = n * h->batch;
