@@ -309,7 +309,7 @@ def run_solves(enp, W, name, labels=None, reference="fp64"):
 
 def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
                       labels=("fp64", "mixed", "mixed_device_loop", "mixed_sweep",
-                              "mixed_paper_guess")):
+                              "mixed_paper_guess"), pc_lag=1):
     """The operating-point sweep of the plate reactor (Sec. 5.2): `batch`
     applied cathode potentials from volts[0] to volts[1] (anode at 0), all
     solved in one batched Newton run per stage, with continuation in the
@@ -333,6 +333,7 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
     step0 = 0.125
     u0 = W.reactor_initial_state(prob, phis * step0)
     out = {"workload": name, "batch": batch, "volts": list(volts), "n_dof_per_point": prob.n_dof,
+           "pc_lag": pc_lag,
            "rtol_last_stage": 1e-10, "continuation": "lambda from 0.125, x1.5 after a converged "
            "stage (max 0.25), /2 after a failed one; intermediate stages to 1e-6 in 10 iterations"}
     sols = {}
@@ -352,7 +353,7 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
             gst = op.initial_guess(u, rtol=1e-8, krylov_rtol=1e-2, graph=True,
                                    raise_on_fail=False, **kws[label])
         st = op.newton_continuation(u, target, step0=step0, graph=True, raise_on_fail=False,
-                                    **kws[label])
+                                    pc_lag=pc_lag, **kws[label])
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         sols[label] = u.cpu().numpy()
@@ -452,6 +453,12 @@ def main():
     ap.add_argument("--reactor-workload", default="reactor_n2_p2",
                     help="workload of the batched 0.1-0.8 V sweep (reactor192_p2: the full "
                          "plate reactor, mixed precision only, about 13 minutes)")
+    ap.add_argument("--reactor-only", default=None,
+                    help="comma-separated labels of the batched sweep (fp64, mixed, "
+                         "mixed_device_loop, mixed_sweep, mixed_paper_guess): run only the "
+                         "batched 0.1-0.8 V sweep of --reactor-workload and print its record")
+    ap.add_argument("--reactor-pc-lag", type=int, default=1,
+                    help="preconditioner rebuilds every this many Newton iterations in the sweep")
     ap.add_argument("--channel-solve", type=int, default=0,
                     help="1: also solve channel64_p3 (3 species, 6.3M DOFs) to 1e-10, FP64 "
                          "(double-float arithmetic) and mixed (FP32 inner, BF16 inverses)")
@@ -483,6 +490,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     enp.build()
+    if args.reactor_only:
+        if rank == 0:
+            t0 = time.perf_counter()
+            rec = run_batched_solve(enp, W, args.reactor_workload,
+                                    labels=tuple(args.reactor_only.split(",")),
+                                    pc_lag=args.reactor_pc_lag)
+            rec["wall_seconds"] = time.perf_counter() - t0
+            print(json.dumps({"reactor_only": rec}), flush=True)
+        return
     if args.only in ("fgmres_f64", "fgmres_f32"):
         if rank == 0:
             print(json.dumps(run_fgmres_profile(enp, W, args)), flush=True)
@@ -508,7 +524,8 @@ def main():
         # launch shape per operator and arithmetic, before any timing
         for ar, code in (("f64", enp.ARITH_F64), ("df32", enp.ARITH_DF32)):
             op.set_arithmetic(code)
-            tuned[ar] = op.autotune()
+            op.autotune()
+            tuned[ar] = op.launch_shapes()
         op.set_arithmetic(enp.ARITH_F64)
         op.block_jacobi_setup(u, enp.BJ_F32)   # preconditioner set up once, outside the steps
     fp64_ops = ["residual_f64", "jvp_f64", "vjp_f64", "residual_df32", "jvp_df32", "vjp_df32"]
@@ -711,9 +728,11 @@ def main():
                                    "block-Jacobi apply (FP32 inverses), c_m recovery, inner "
                                    "product",
                            "applications_per_step": len(applications),
-                           "elements_per_block": {ar: dict(zip(["residual", "jvp", "vjp",
-                                                                "jvp_f32", "residual_f32"], t))
-                                                  for ar, t in tuned.items()},
+                           "tile_shapes": {ar: {nm: {"elements_per_block": eb, "faces_per_block": fb}
+                                                for nm, eb, fb in zip(["residual", "jvp", "vjp",
+                                                                       "jvp_f32", "residual_f32"],
+                                                                      t[0], t[1])}
+                                           for ar, t in tuned.items()},
                            "l2": "flushed between steps (512 MB write)"},
                 "jvp_GDOF_s": {"f64": n / (ms_jv["f64"] * 1e-3) / 1e9,
                                "df32": n / (ms_jv["df32"] * 1e-3) / 1e9,

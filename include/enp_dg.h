@@ -392,13 +392,21 @@ enp_status enp_newton_continuation(enp_handle h, double* u, const double* phi_ap
                                    const enp_continuation_opts* copts,
                                    const enp_newton_opts* opts, enp_continuation_stats* stats);
 
-/* Choose the launch shape of the hexahedral operator kernel for this handle's
- * degree and field count: for each of R (FP64), J v (FP64), J^T w (FP64),
- * J v (FP32) and R (FP32), every feasible number of elements per thread block
- * is timed on this mesh (three launches, CUDA events) and the fastest kept
- * for the process. chosen (host, 5 ints, may be NULL) receives the choices in
- * that order. Allocates and frees three work vectors; synchronises. No-op in 2D. */
+/* Choose the tile shapes of the hexahedral operator for this handle's degree
+ * and field count: for each of R, J v, J^T w (FP64-accurate, in the handle's
+ * arithmetic), J v (FP32) and R (FP32), first every feasible number of faces
+ * per thread block of the face kernel, then every feasible number of elements
+ * per thread block of the element kernel, is timed on this mesh (three
+ * launches of the whole operator, CUDA events), and the fastest is kept for the
+ * process (per degree, field count, mode and arithmetic). chosen (host, 5 ints,
+ * may be NULL) receives the elements per block in that order. Allocates and
+ * frees three work vectors; synchronises. No-op in 2D. */
 enp_status enp_autotune(enp_handle h, int* chosen);
+
+/* The tile shapes in use for this handle (host arrays of 5 ints, either NULL):
+ * elements per block and faces per block of R, J v, J^T w (in the handle's
+ * arithmetic), J v (FP32), R (FP32); 0 = the built-in default. */
+enp_status enp_launch_shapes(enp_handle h, int* eb, int* fpb);
 
 /* Number of parameters theta of enp_param_jacobian / enp_param_vjp: 2m + 3,
  * ordered (D_1..D_m, c_in_1..c_in_{m-1}, phi_app of electrodes 0..3). */

@@ -177,6 +177,7 @@ _PROTOS = [
     ("enp_newton_continuation", _I, [_V, _V, _V, _V, _V, _V]),
     ("enp_initial_guess", _I, [_V, _V, _V, _V]),
     ("enp_autotune", _I, [_V, _V]),
+    ("enp_launch_shapes", _I, [_V, _V, _V]),
     ("enp_param_count", _I, [_V, ctypes.POINTER(_I)]),
     ("enp_param_jacobian", _I, [_V, _V, _V]),
     ("enp_param_vjp", _I, [_V, _V, _V, _V]),
@@ -500,11 +501,19 @@ class Operator:
         return out
 
     def autotune(self):
-        """Pick the elements per block of the hexahedral kernel for this shape;
-        returns the choices for R, J v, J^T w (FP64), J v, R (FP32)."""
+        """Pick the tile shapes (faces per block of the face kernel, elements
+        per block of the element kernel) for this shape; returns the elements
+        per block for R, J v, J^T w (FP64-accurate), J v, R (FP32)."""
         c = (ctypes.c_int * 5)()
         self._check(self._lib.enp_autotune(self.h, c))
         return list(c)
+
+    def launch_shapes(self):
+        """(elements per block, faces per block) in use for R, J v, J^T w
+        (FP64-accurate), J v, R (FP32); 0 = default."""
+        eb, fpb = (ctypes.c_int * 5)(), (ctypes.c_int * 5)()
+        self._check(self._lib.enp_launch_shapes(self.h, eb, fpb))
+        return list(eb), list(fpb)
 
     @property
     def n_theta(self):

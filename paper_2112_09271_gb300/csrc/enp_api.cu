@@ -544,33 +544,55 @@ static cudaError_t tune_launch(int mode, const OpParams& P, const Tables* t, enp
   else return enp::launch_op<R>(mode, P, t, u, v, out, 1, s);
 }
 
+// The tile shapes of one operator mode: faces per block of the face kernel
+// (modes R, J v, J^T w), then elements per block of the element kernel, each
+// timed over its feasible range (three launches of the whole operator, CUDA
+// events) with the other at its current value; the fastest is kept.
 template <class R>
 static cudaError_t tune_mode(enp_handle h, int mode, enp::io_t<R>* u, enp::io_t<R>* v,
-                             enp::io_t<R>* out, int* chosen) {
+                             enp::io_t<R>* out, int* chosen, int* chosen_fpb) {
   OpParams P = h->prm;
   P.arith = enp::kArithF64;  // launch_op<double> then runs the FP64 kernels themselves
-  const int mx = enp::eb3d_max<R>(P.p, P.NF, mode);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_eb = 0;
   cudaError_t err = cudaSuccess;
-  for (int eb = 1; eb <= mx && err == cudaSuccess; ++eb) {
-    enp::eb3d_set<R>(P.p, P.NF, mode, eb);
-    err = tune_launch<R>(mode, P, h->d_tab, u, v, out, h->stream);
-    if (err != cudaSuccess) break;
+  auto time_it = [&](float* ms) -> cudaError_t {
+    cudaError_t er = tune_launch<R>(mode, P, h->d_tab, u, v, out, h->stream);
+    if (er != cudaSuccess) return er;
     cudaEventRecord(e0, h->stream);
     for (int r = 0; r < 3; ++r) tune_launch<R>(mode, P, h->d_tab, u, v, out, h->stream);
     cudaEventRecord(e1, h->stream);
-    err = cudaEventSynchronize(e1);
+    er = cudaEventSynchronize(e1);
+    *ms = 0.f;
+    cudaEventElapsedTime(ms, e0, e1);
+    return er;
+  };
+  int best_fpb = 0;
+  if (mode <= enp::kVjp) {
+    const int fx = enp::fpb3d_max<R>(P.p, P.NF, mode);
+    float best = 1e30f;
+    for (int f = 1; f <= fx && err == cudaSuccess; ++f) {
+      enp::fpb3d_set<R>(P.p, P.NF, mode, f);
+      float ms = 0.f;
+      err = time_it(&ms);
+      if (err == cudaSuccess && ms < best) { best = ms; best_fpb = f; }
+    }
+    enp::fpb3d_set<R>(P.p, P.NF, mode, best_fpb);
+  }
+  const int mx = enp::eb3d_max<R>(P.p, P.NF, mode);
+  float best = 1e30f;
+  int best_eb = 0;
+  for (int eb = 1; eb <= mx && err == cudaSuccess; ++eb) {
+    enp::eb3d_set<R>(P.p, P.NF, mode, eb);
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    err = time_it(&ms);
     if (err == cudaSuccess && ms < best) { best = ms; best_eb = eb; }
   }
   enp::eb3d_set<R>(P.p, P.NF, mode, best_eb);
   if (mode == enp::kJvp) enp::eb3d_set<R>(P.p, P.NF, enp::kBlockCol, best_eb);
   if (chosen) *chosen = best_eb;
+  if (chosen_fpb) *chosen_fpb = best_fpb;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return err;
@@ -588,18 +610,20 @@ enp_status enp_autotune(enp_handle h, int* chosen) {
   v = u + n;
   o = v + n;
   cudaMemsetAsync(u, 0, 3 * n * sizeof(double), h->stream);
-  int c[5] = {0, 0, 0, 0, 0};
+  int c[5] = {0, 0, 0, 0, 0}, f[5] = {0, 0, 0, 0, 0};
   if (h->prm.arith == enp::kArithDF) {  // the FP64-accurate operator runs in double-float
-    e = tune_mode<enp::df>(h, enp::kResidual, u, v, o, &c[0]);
-    if (e == cudaSuccess) e = tune_mode<enp::df>(h, enp::kJvp, u, v, o, &c[1]);
-    if (e == cudaSuccess) e = tune_mode<enp::df>(h, enp::kVjp, u, v, o, &c[2]);
+    e = tune_mode<enp::df>(h, enp::kResidual, u, v, o, &c[0], &f[0]);
+    if (e == cudaSuccess) e = tune_mode<enp::df>(h, enp::kJvp, u, v, o, &c[1], &f[1]);
+    if (e == cudaSuccess) e = tune_mode<enp::df>(h, enp::kVjp, u, v, o, &c[2], &f[2]);
   } else {
-    e = tune_mode<double>(h, enp::kResidual, u, v, o, &c[0]);
-    if (e == cudaSuccess) e = tune_mode<double>(h, enp::kJvp, u, v, o, &c[1]);
-    if (e == cudaSuccess) e = tune_mode<double>(h, enp::kVjp, u, v, o, &c[2]);
+    e = tune_mode<double>(h, enp::kResidual, u, v, o, &c[0], &f[0]);
+    if (e == cudaSuccess) e = tune_mode<double>(h, enp::kJvp, u, v, o, &c[1], &f[1]);
+    if (e == cudaSuccess) e = tune_mode<double>(h, enp::kVjp, u, v, o, &c[2], &f[2]);
   }
-  if (e == cudaSuccess) e = tune_mode<float>(h, enp::kJvp, (float*)u, (float*)v, (float*)o, &c[3]);
-  if (e == cudaSuccess) e = tune_mode<float>(h, enp::kResidual, (float*)u, (float*)v, (float*)o, &c[4]);
+  if (e == cudaSuccess)
+    e = tune_mode<float>(h, enp::kJvp, (float*)u, (float*)v, (float*)o, &c[3], &f[3]);
+  if (e == cudaSuccess)
+    e = tune_mode<float>(h, enp::kResidual, (float*)u, (float*)v, (float*)o, &c[4], &f[4]);
   cudaFree(u);
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
   if (chosen)
@@ -618,6 +642,28 @@ enp_status enp_set_arithmetic(enp_handle h, int arith) {
 enp_status enp_get_arithmetic(enp_handle h, int* arith) {
   if (!h || !arith) return ENP_ERR_INVALID_ARG;
   *arith = h->prm.arith == enp::kArithDF ? ENP_ARITH_DF32 : ENP_ARITH_F64;
+  return ENP_OK;
+}
+
+enp_status enp_launch_shapes(enp_handle h, int* eb, int* fpb) {
+  if (!h) return ENP_ERR_INVALID_ARG;
+  const OpParams& P = h->prm;
+  if (P.dim != 3) {
+    for (int i = 0; i < 5; ++i) { if (eb) eb[i] = 0; if (fpb) fpb[i] = 0; }
+    return ENP_OK;
+  }
+  const bool dfa = P.arith == enp::kArithDF;
+  const int modes[5] = {enp::kResidual, enp::kJvp, enp::kVjp, enp::kJvp, enp::kResidual};
+  for (int i = 0; i < 5; ++i) {
+    const int md = modes[i];
+    if (i < 3) {
+      if (eb) eb[i] = dfa ? enp::eb3d_get<enp::df>(P.p, P.NF, md) : enp::eb3d_get<double>(P.p, P.NF, md);
+      if (fpb) fpb[i] = dfa ? enp::fpb3d_get<enp::df>(P.p, P.NF, md) : enp::fpb3d_get<double>(P.p, P.NF, md);
+    } else {
+      if (eb) eb[i] = enp::eb3d_get<float>(P.p, P.NF, md);
+      if (fpb) fpb[i] = enp::fpb3d_get<float>(P.p, P.NF, md);
+    }
+  }
   return ENP_OK;
 }
 

@@ -38,6 +38,10 @@ bool shape_supported(int dim, int p, int nf);
 template <class R> int eb3d_max(int p, int nf, int mode);
 template <class R> void eb3d_set(int p, int nf, int mode, int eb);
 template <class R> int eb3d_get(int p, int nf, int mode);
+// Faces per block of the hexahedral face kernel (modes 0..2).
+template <class R> int fpb3d_max(int p, int nf, int mode);
+template <class R> void fpb3d_set(int p, int nf, int mode, int fpb);
+template <class R> int fpb3d_get(int p, int nf, int mode);
 
 // Upload the degree-p basis tables to the constant memory the kernels of type R
 // read (current device).

@@ -43,6 +43,34 @@ inline int (&eb3d_table())[kMaxP + 1][4][5] {
   static int t[kMaxP + 1][4][5] = {};
   return t;
 }
+// Faces per block of the face kernel (modes R, J v, J^T w), the same way.
+template <class R>
+inline int (&fpb3d_table())[kMaxP + 1][4][3] {
+  static int t[kMaxP + 1][4][3] = {};
+  return t;
+}
+
+template <int P, int NF, int MODE, class R>
+static constexpr size_t face_bytes() {
+  return (size_t)SmemF<P, NF, MODE, tpf3d<P, R>()>::total * sizeof(R);
+}
+// The default faces per block (shared memory near 96 KB) and the largest
+// feasible value (threads <= kMaxThreads3D, shared memory <= 200 KB).
+template <int P, int NF, int MODE, class R>
+static int default_fpb() {
+  constexpr int TF = tpf3d<P, R>();
+  int f = (int)((96 * 1024) / face_bytes<P, NF, MODE, R>());
+  f = f < 1 ? 1 : f;
+  if (f * TF > kMaxThreads3D) f = kMaxThreads3D / TF;
+  return f < 1 ? 1 : f;
+}
+template <int P, int NF, int MODE, class R>
+static int max_fpb() {
+  constexpr int TF = tpf3d<P, R>();
+  int f = kMaxThreads3D / TF;
+  while (f > 1 && (size_t)f * face_bytes<P, NF, MODE, R>() > 200 * 1024) --f;
+  return f < 1 ? 1 : f;
+}
 
 template <int P, int NF, int MODE, class R>
 static int default_eb() {
@@ -80,12 +108,12 @@ static cudaError_t launch_3d(const OpParams& prm, const io_t<R>* u, const io_t<R
   if constexpr (S3::kFB) {
     // the faces first: each face once, both sides' terms into the face buffer
     constexpr int TF = tpf3d<P, R>();
-    constexpr size_t per_face = (size_t)SmemF<P, NF, MODE, TF>::total * sizeof(R);
-    constexpr int fpb_s = (int)((96 * 1024) / per_face);
-    constexpr int fpb = fpb_s < 1 ? 1 : (fpb_s * TF > kMaxThreads3D ? kMaxThreads3D / TF : fpb_s);
+    constexpr size_t per_face = face_bytes<P, NF, MODE, R>();
+    int fpb = fpb3d_table<R>()[P][NF][MODE];
+    if (fpb <= 0) fpb = default_fpb<P, NF, MODE, R>();
     auto fk = face3d_kernel<P, NF, MODE, R>;
     static SmemAttr fattr;
-    cudaError_t ef = raise_smem_limit(fattr, fk, fpb * per_face);
+    cudaError_t ef = raise_smem_limit(fattr, fk, (size_t)max_fpb<P, NF, MODE, R>() * per_face);
     if (ef != cudaSuccess) return ef;
     const long long nf = prm.foff[3];
     dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
@@ -159,11 +187,10 @@ static cudaError_t launch_face_plane_pn(const OpParams& prm, const R* u, const R
                                         cudaStream_t stream, int a, int ia) {
   constexpr int TF = tpf3d<P, R>();
   constexpr size_t per_face = (size_t)SmemF<P, NF, kJvp, TF>::total * sizeof(R);
-  constexpr int fpb_s = (int)((96 * 1024) / per_face);
-  constexpr int fpb = fpb_s < 1 ? 1 : (fpb_s * TF > kMaxThreads3D ? kMaxThreads3D / TF : fpb_s);
+  const int fpb = default_fpb<P, NF, kJvp, R>();
   auto fk = face3d_kernel<P, NF, kJvp, R>;
-  static SmemAttr attr;
-  cudaError_t ea = raise_smem_limit(attr, fk, fpb * per_face);
+  static SmemAttr attr;  // the limit launch_3d sets for the same kernel
+  cudaError_t ea = raise_smem_limit(attr, fk, (size_t)max_fpb<P, NF, kJvp, R>() * per_face);
   if (ea != cudaSuccess) return ea;
   const long long nf = (long long)prm.ne[a == 0 ? 1 : 0] * prm.ne[a == 2 ? 1 : 2];
   dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
@@ -197,6 +224,29 @@ int eb3d_max(int p, int nf, int mode) {
 #undef ENP_EBM_P
 #undef ENP_EBM
   return 1;
+}
+
+// Faces per block of the face kernel (modes 0..2), as above.
+template <class R>
+int fpb3d_max(int p, int nf, int mode) {
+#define ENP_FBM(PP, NFF, MM) if (p == PP && nf == NFF && mode == MM) return max_fpb<PP, NFF, MM, R>();
+#define ENP_FBM_P(PP) ENP_FBM(PP, 2, 0) ENP_FBM(PP, 2, 1) ENP_FBM(PP, 2, 2) \
+  ENP_FBM(PP, 3, 0) ENP_FBM(PP, 3, 1) ENP_FBM(PP, 3, 2)
+  ENP_FBM_P(1) ENP_FBM_P(2) ENP_FBM_P(3) ENP_FBM_P(4)
+#undef ENP_FBM_P
+#undef ENP_FBM
+  return 1;
+}
+
+template <class R>
+void fpb3d_set(int p, int nf, int mode, int fpb) {
+  if (p >= 1 && p <= kMaxP && nf >= 2 && nf <= 3 && mode >= 0 && mode <= 2) fpb3d_table<R>()[p][nf][mode] = fpb;
+}
+
+template <class R>
+int fpb3d_get(int p, int nf, int mode) {
+  if (p >= 1 && p <= kMaxP && nf >= 2 && nf <= 3 && mode >= 0 && mode <= 2) return fpb3d_table<R>()[p][nf][mode];
+  return 0;
 }
 
 template <class R>

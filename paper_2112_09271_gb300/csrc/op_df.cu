@@ -28,3 +28,6 @@ cudaError_t enp::prepare_tables_df(int p, const Tables& t) {
 template int enp::eb3d_max<enp::df>(int, int, int);
 template void enp::eb3d_set<enp::df>(int, int, int, int);
 template int enp::eb3d_get<enp::df>(int, int, int);
+template int enp::fpb3d_max<enp::df>(int, int, int);
+template void enp::fpb3d_set<enp::df>(int, int, int, int);
+template int enp::fpb3d_get<enp::df>(int, int, int);

@@ -6,5 +6,8 @@ template cudaError_t enp::prepare_tables<double>(int, const Tables&);
 template int enp::eb3d_max<double>(int, int, int);
 template void enp::eb3d_set<double>(int, int, int, int);
 template int enp::eb3d_get<double>(int, int, int);
+template int enp::fpb3d_max<double>(int, int, int);
+template void enp::fpb3d_set<double>(int, int, int, int);
+template int enp::fpb3d_get<double>(int, int, int);
 template cudaError_t enp::launch_face_plane<double>(const OpParams&, const double*, const double*, int,
                                                  cudaStream_t, int, int);

@@ -90,8 +90,9 @@ def test_batched_newton_equals_single_solves(mixed, graph):
 
 
 def test_autotune_keeps_results():
-    """The launch shape chosen by the autotuner changes the block decomposition,
-    not the arithmetic: results are unchanged bit for bit."""
+    """The tile shapes chosen by the autotuner (faces per block, elements per
+    block) change the block decomposition, not the arithmetic: results are
+    unchanged bit for bit, in FP64 and double-float."""
     import torch
     enp = _enp()
     P = W.config("channel_n2")
@@ -100,9 +101,19 @@ def test_autotune_keeps_results():
     before = (op.residual(u).cpu().numpy(), op.jvp(u, v).cpu().numpy())
     chosen = op.autotune()
     assert len(chosen) == 5 and all(c >= 1 for c in chosen)
+    eb, fpb = op.launch_shapes()
+    assert eb == chosen and all(f >= 1 for f in fpb)
     after = (op.residual(u).cpu().numpy(), op.jvp(u, v).cpu().numpy())
     np.testing.assert_array_equal(before[0], after[0])
     np.testing.assert_array_equal(before[1], after[1])
+    # every face tile shape gives the same bits (each face is computed by one
+    # group of threads whatever the number of faces per block)
+    op.set_arithmetic(enp.ARITH_DF32)
+    op.autotune()
+    d_after = op.jvp(u, v).cpu().numpy()
+    op2 = enp.Operator(P)
+    op2.set_arithmetic(enp.ARITH_DF32)
+    np.testing.assert_array_equal(op2.jvp(u, v).cpu().numpy(), d_after)
 
 
 @pytest.mark.parametrize("mixed", [False, True])
