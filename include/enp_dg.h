@@ -211,6 +211,19 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage);
  * x, y: [batch][m][E][Np]. */
 enp_status enp_block_jacobi_apply(enp_handle h, const double* x, double* y);
 
+/* Memory strategy of the block inverses for large batches: point = -1 (the
+ * default) stores one set of element-block inverses per operating point;
+ * point >= 0 stores only the inverses of operating point `point` and applies
+ * them to every operating point of the batch (a lagged, shared
+ * preconditioner: FGMRES is flexible and needs no exact one). The blocks are
+ * assembled and inverted one operating point at a time either way, so the
+ * setup's FP32 staging holds one point's blocks. For the plate reactor at
+ * p = 4 (147,456 elements, blocks of 250 x 250) one set is 36.9 GB in FP32 and
+ * 18.4 GB in BF16: eight sets would not fit next to the Krylov basis in
+ * 288 GB, one does. The two-level coarse correction stays per point.
+ * Takes effect at the next setup. Errors: INVALID_ARG. */
+enp_status enp_set_shared_blocks(enp_handle h, int point);
+
 /* Choose the preconditioner that the next enp_block_jacobi_setup builds (and
  * that FGMRES and Newton then use). two_level = 0: block-Jacobi alone (the
  * element-wise Jacobi of Sec. 4.2, the default). two_level = 1 (hexahedral

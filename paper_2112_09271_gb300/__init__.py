@@ -168,6 +168,7 @@ _PROTOS = [
     ("enp_block_jacobi_setup", _I, [_V, _V, _I]),
     ("enp_block_jacobi_apply", _I, [_V, _V, _V]),
     ("enp_set_preconditioner", _I, [_V, _I]),
+    ("enp_set_shared_blocks", _I, [_V, _I]),
     ("enp_set_coarse_options", _I, [_V, _I, _I, ctypes.c_double]),
     ("enp_set_sweep", _I, [_V, _I]),
     ("enp_coarse_operator", _I, [_V, _V]),
@@ -397,6 +398,11 @@ class Operator:
         """0: block-Jacobi; 1: block-Jacobi plus the coarse potential correction
         (takes effect at the next block_jacobi_setup)."""
         self._check(self._lib.enp_set_preconditioner(self.h, int(two_level)))
+
+    def set_shared_blocks(self, point):
+        """-1: block inverses per operating point; b >= 0: the inverses of point
+        b serve the whole batch (next setup)."""
+        self._check(self._lib.enp_set_shared_blocks(self.h, int(point)))
 
     def set_sweep(self, on):
         """1: downwind block Gauss-Seidel instead of block-Jacobi (next setup)."""

@@ -11,6 +11,7 @@
 //    products reduced on the device in a fixed order (warp shuffles, then one
 //    partial per block, then one block), so results do not depend on timing.
 //  * Newton's method with backtracking line search on ||R|| (Sec. 4).
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <type_traits>
@@ -1002,6 +1003,160 @@ gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
   for (int t = tid; t < n * n; t += NW * 32) o[t] = (TS)stage[t];
 }
 
+// The same register-resident Gauss-Jordan for blocks of up to 256 x 256, whose
+// 65,536 entries exceed one SM's registers: each block is spread over a
+// cluster of two CTAs on two SMs. Global row i lives in CTA i % 2 as local row
+// i / 2 (warp w: local rows w + 16 r, r < 8; lane l: columns l + 32 c, c < 8).
+// Each CTA publishes its rows' part of the pivot column in its own shared
+// memory; after a cluster barrier every warp of both CTAs reads both halves
+// (the other through distributed shared memory) and finds the same pivot; the
+// owning CTA publishes the pivot row, a second cluster barrier, every thread
+// reads it from the owner. The inverse is staged in the shared memory of the
+// CTA that owns each output row (out[c][.] in CTA c % 2) and written out
+// coalesced. Singular pivots and the output order are as in gj_invert_regs.
+constexpr int kGjcNW = 16, kGjcRPW = 8, kGjcCPL = 8;
+constexpr int kGjcRows = kGjcNW * kGjcRPW;  // local rows per CTA (128)
+constexpr int kGjcCols = 32 * kGjcCPL;      // columns (256)
+
+template <class TS>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGjcNW * 32, 1)
+gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
+                  int* __restrict__ singular) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank(), peer = rank ^ 1;
+  extern __shared__ __align__(16) unsigned char gcs[];
+  float* stage = reinterpret_cast<float*>(gcs);   // [(n + 1) / 2][n]: out rows c with c % 2 == rank
+  __shared__ float colv[2][kGjcRows], cola[2][kGjcRows];
+  __shared__ float rowv[kGjcCols];
+  __shared__ int piv[kGjcCols], stepof[2 * kGjcRows];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const long long e = blockIdx.x / 2;
+  const float* src = blocks + e * (long long)n * n;
+  float* colv_p[2] = {cluster.map_shared_rank(&colv[0][0], peer), cluster.map_shared_rank(&colv[1][0], peer)};
+  float* cola_p[2] = {cluster.map_shared_rank(&cola[0][0], peer), cluster.map_shared_rank(&cola[1][0], peer)};
+  float* rowv_p = cluster.map_shared_rank(&rowv[0], peer);
+  float* stage_p = cluster.map_shared_rank(stage, peer);
+  float M[kGjcRPW][kGjcCPL];
+  // global row of local row li in this CTA: 2 li + rank
+#pragma unroll
+  for (int r = 0; r < kGjcRPW; ++r) {
+    const int i = 2 * (w + kGjcNW * r) + rank;
+#pragma unroll
+    for (int c = 0; c < kGjcCPL; ++c) {
+      const int j = lane + 32 * c;
+      M[r][c] = (i < n && j < n) ? src[(long long)i * n + j] : (i == j ? 1.f : 0.f);
+    }
+  }
+  unsigned used = 0u;
+  if (lane == 0) {
+#pragma unroll
+    for (int r = 0; r < kGjcRPW; ++r) {
+      const int li = w + kGjcNW * r, i = 2 * li + rank;
+      colv[0][li] = M[r][0];
+      cola[0][li] = i < n ? fabsf(M[r][0]) : -1.f;
+    }
+  }
+  cluster.sync();
+  bool bad = false;
+  for (int k = 0; k < n; ++k) {
+    const int buf = k & 1;
+    // pivot: the largest |M_ik| over unused rows of both CTAs, ties to the lower row
+    float best = -1.f;
+    int bi = 0;
+    for (int li = lane; li < kGjcRows; li += 32) {
+      const float v0 = rank == 0 ? cola[buf][li] : cola_p[buf][li];   // row 2 li
+      const float v1 = rank == 1 ? cola[buf][li] : cola_p[buf][li];   // row 2 li + 1
+      if (v0 > best) { best = v0; bi = 2 * li; }
+      if (v1 > best) { best = v1; bi = 2 * li + 1; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (!(best > 0.f) || !isfinite(best)) { bad = true; break; }  // the same in both CTAs
+    const int p = bi, owner = p & 1, lp = p >> 1;
+    const float pivv = owner == rank ? colv[buf][lp] : colv_p[buf][lp];
+    const float pinv = 1.f / pivv;
+    if (owner == rank && w == lp % kGjcNW) {
+      const int rp = lp / kGjcNW;
+      used |= 1u << rp;
+#pragma unroll
+      for (int c = 0; c < kGjcCPL; ++c) {
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < kGjcRPW; ++r) v = r == rp ? M[r][c] : v;
+        rowv[lane + 32 * c] = v;
+      }
+    }
+    if (tid == 0) { piv[k] = p; stepof[p] = k; }
+    cluster.sync();
+    const float* rsrc = owner == rank ? rowv : rowv_p;
+    float rj[kGjcCPL];
+#pragma unroll
+    for (int c = 0; c < kGjcCPL; ++c) {
+      const int j = lane + 32 * c;
+      rj[c] = (j == k ? 1.f : rsrc[j]) * pinv;
+    }
+#pragma unroll
+    for (int r = 0; r < kGjcRPW; ++r) {
+      const int li = w + kGjcNW * r, i = 2 * li + rank;
+      const float ci = colv[buf][li];
+      const bool isp = i == p;
+#pragma unroll
+      for (int c = 0; c < kGjcCPL; ++c) {
+        const int j = lane + 32 * c;
+        const float m = j == k ? 0.f : M[r][c];
+        M[r][c] = isp ? rj[c] : fmaf(-ci, rj[c], m);
+      }
+    }
+    const int kn = k + 1;
+    if (kn < n && lane == (kn & 31)) {
+      const int cn = kn >> 5;
+#pragma unroll
+      for (int r = 0; r < kGjcRPW; ++r) {
+        float v = 0.f;
+#pragma unroll
+        for (int c = 0; c < kGjcCPL; ++c) v = c == cn ? M[r][c] : v;
+        const int li = w + kGjcNW * r, i = 2 * li + rank;
+        colv[buf ^ 1][li] = v;
+        cola[buf ^ 1][li] = (i < n && !((used >> r) & 1u)) ? fabsf(v) : -1.f;
+      }
+    }
+    cluster.sync();
+  }
+  if (bad) {
+    if (tid == 0 && rank == 0) atomicOr(singular, 1);
+    cluster.sync();  // no CTA leaves while the other may still read its shared memory
+    return;
+  }
+  // inv[step(i)][p_j] = M_ij -> out[p_j][step(i)], staged in CTA p_j % 2
+#pragma unroll
+  for (int r = 0; r < kGjcRPW; ++r) {
+    const int i = 2 * (w + kGjcNW * r) + rank;
+    if (i >= n) continue;
+    const int si = stepof[i];
+#pragma unroll
+    for (int c = 0; c < kGjcCPL; ++c) {
+      const int j = lane + 32 * c;
+      if (j < n) {
+        const int oc = piv[j];
+        float* dst = (oc & 1) == rank ? stage : stage_p;
+        dst[(oc >> 1) * n + si] = M[r][c];
+      }
+    }
+  }
+  cluster.sync();
+  TS* o = out + e * (long long)n * n;
+  const int nrow = (n - rank + 1) / 2;  // output rows c = 2 q + rank < n
+  for (int t = tid; t < nrow * n; t += kGjcNW * 32) {
+    const int q = t / n, r = t % n;
+    o[(long long)(2 * q + rank) * n + r] = (TS)stage[q * n + r];
+  }
+}
+
 // One plane of the downwind block Gauss-Seidel sweep: the elements whose
 // coordinate along axis a is k, one per thread block. t = x_e minus the
 // upstream face terms J_(e,up) z_up that the face kernel left in the face buffer
@@ -1014,7 +1169,7 @@ __global__ void sweep_plane_kernel(const TS* __restrict__ BT, const TV* __restri
                                    long long bstride, int a, int k, int ne0, int ne1, int ne2,
                                    int upstream, const TV* __restrict__ fb, long long fb_stride,
                                    long long foff_a, int ia, int side,
-                                   const double* __restrict__ dL) {
+                                   const double* __restrict__ dL, int shared_blocks) {
   extern __shared__ __align__(16) unsigned char ssm_raw[];
   TA* ts = reinterpret_cast<TA*>(ssm_raw);
   const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
@@ -1050,7 +1205,7 @@ __global__ void sweep_plane_kernel(const TS* __restrict__ BT, const TV* __restri
     ts[c] = t;
   }
   __syncthreads();
-  const TS* B = BT + ((long long)b * E + e) * (long long)n * n;
+  const TS* B = BT + ((long long)(shared_blocks ? 0 : b) * E + e) * (long long)n * n;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     TA acc[8] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
     int c = 0;
@@ -1072,7 +1227,7 @@ __global__ void sweep_plane_kernel(const TS* __restrict__ BT, const TV* __restri
 template <class TS, class TA, class TV>
 __global__ void bj_apply_kernel(const TS* __restrict__ BT, const TV* __restrict__ x,
                                 TV* __restrict__ y, int n, int NF, int Np, long long EN,
-                                long long bstride) {
+                                long long bstride, int shared_blocks) {
   extern __shared__ __align__(16) unsigned char xsm_raw[];
   TA* xs = reinterpret_cast<TA*>(xsm_raw);
   const long long e = blockIdx.x;
@@ -1084,7 +1239,7 @@ __global__ void bj_apply_kernel(const TS* __restrict__ BT, const TV* __restrict_
     xs[c] = (TA)xb[f * EN + e * Np + i];
   }
   __syncthreads();
-  const TS* B = BT + ((long long)b * E + e) * (long long)n * n;
+  const TS* B = BT + ((long long)(shared_blocks ? 0 : b) * E + e) * (long long)n * n;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     // eight independent partial sums keep eight loads per thread in flight
     TA acc[8] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
@@ -1237,11 +1392,13 @@ struct SolverState {
   // block-Jacobi
   int nb = 0;
   int storage = -1;               // 0 f64, 1 f32, 2 bf16
-  double* blocks = nullptr;       // [batch][E][nb][nb] assembled blocks (FP64 setup)
-  float* blocks32 = nullptr;      // [batch][E][nb][nb] assembled blocks (FP32 setup)
+  double* blocks = nullptr;       // [E][nb][nb] assembled blocks of one point (FP64 setup)
+  size_t blocks_count = 0;
+  float* blocks32 = nullptr;      // [E][nb][nb] assembled blocks of one point (FP32 setup)
   float* u32 = nullptr;           // the linearisation point in FP32
   size_t blocks32_count = 0, u32_count = 0;
-  void* binv = nullptr;           // [batch][E][nb][nb] inverse, transposed, in `storage`
+  void* binv = nullptr;           // [sets][E][nb][nb] inverse, transposed, in `storage`
+  int binv_sets = 0;              // batch, or 1 when one set is shared
   void* gj_work = nullptr;        // global work for blocks too large for shared memory
   size_t gj_work_bytes = 0;
   int* d_flag = nullptr;
@@ -1280,6 +1437,9 @@ struct SolverState {
   // two-level preconditioner: element-mean potential correction
   bool sweep = false;             // downwind block Gauss-Seidel (enp_set_sweep)
   bool potential_only = false;    // the potential rows alone (enp_initial_guess)
+  int pc_shared = -1;             // >= 0: one set of block inverses, of this operating
+                                  // point, for the whole batch (enp_set_shared_blocks)
+  int pc_shared_built = 0;        // the stored inverses are one shared set
   bool sweep_ready = false;
   int sweep_axis = 0, sweep_dir = 1;
   double* upc64 = nullptr;        // the linearisation point of the last setup
@@ -1706,54 +1866,48 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
   const std::vector<const void*> pc_before = pc_ptrs(S);
   const OpParams& P = h->prm;
   const int nb = P.NF * P.Np;
-  const long long nblk = (long long)h->batch * P.E;
   const size_t nn = (size_t)nb * nb;
   const bool f64 = storage == 0;  // FP64 storage: FP64 assembly and inversion; else FP32
+  // one set of inverses per operating point, or (pc_shared >= 0) one set, of
+  // that point, for the whole batch; either way the blocks are assembled and
+  // inverted one operating point at a time, so the assembly staging holds one
+  // point's blocks
+  const int shared = S.pc_shared >= 0 && S.pc_shared < h->batch ? 1 : 0;
+  const int nsets = shared ? 1 : h->batch;
+  const long long nblk = (long long)P.E;  // blocks per set
   cudaError_t e;
   const size_t esz = storage == 0 ? 8 : (storage == 1 ? 4 : 2);
-  if (!S.binv || S.nb != nb || S.storage != storage) {
+  if (!S.binv || S.nb != nb || S.storage != storage || S.binv_sets != nsets) {
     cudaFree(S.binv);
     S.binv = nullptr;
-    e = cudaMalloc(&S.binv, esz * nn * nblk);
+    S.binv_sets = 0;
+    e = cudaMalloc(&S.binv, esz * nn * nblk * nsets);
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc block inverses");
+    S.binv_sets = nsets;
   }
   if (!S.d_flag) {
     e = cudaMalloc(&S.d_flag, sizeof(int));
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc flag");
   }
   if (f64) {
-    if (!S.blocks || S.nb != nb) {
+    if (!S.blocks || S.nb != nb || S.blocks_count < nn * nblk) {
       cudaFree(S.blocks);
       S.blocks = nullptr;
+      S.blocks_count = 0;
       e = cudaMalloc(&S.blocks, sizeof(double) * nn * nblk);
       if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc blocks");
+      S.blocks_count = nn * nblk;
     }
-    S.nb = nb;
-    enp_status st = enp_block_diagonal(h, u, S.blocks);
-    if (st != ENP_OK) return st;
-    if (S.potential_only)
-      enp::block_species_identity<double><<<grid_for((long long)(nb - P.Np) * nb * nblk), 256, 0,
-                                            h->stream>>>(S.blocks, nblk, nb, P.Np);
   } else {
     const long long ntot = h->n_dof * h->batch;
     if ((e = ensure(&S.blocks32, S.blocks32_count, nn * nblk)) != cudaSuccess ||
         (e = ensure(&S.u32, S.u32_count, (size_t)ntot)) != cudaSuccess)
       return cuda_err(h, e, "cudaMalloc FP32 blocks");
-    S.nb = nb;
     enp::convert_kernel<double, float><<<grid_for(ntot), 256, 0, h->stream>>>(u, S.u32, ntot);
-    const long long bsz = (long long)P.E * nb * nb;
-    for (int b = 0; b < h->batch; ++b) {
-      OpParams Pb = P;
-      if (P.phiapp_batch) Pb.phiapp_batch = P.phiapp_batch + 4 * b;
-      e = enp::launch_op<float>(enp::kBlockCol, Pb, h->d_tab, S.u32 + b * P.batch_stride, nullptr,
-                                S.blocks32 + b * bsz, nb, h->stream);
-      if (e != cudaSuccess) return cuda_err(h, e, "FP32 block columns");
-    }
-    if (S.potential_only)
-      enp::block_species_identity<float><<<grid_for((long long)(nb - P.Np) * nb * nblk), 256, 0,
-                                           h->stream>>>(S.blocks32, nblk, nb, P.Np);
   }
+  S.nb = nb;
   S.storage = storage;
+  S.pc_shared_built = shared;
   cudaMemsetAsync(S.d_flag, 0, sizeof(int), h->stream);
   const size_t telt = f64 ? 8 : 4;
   const size_t smem_full = telt * ((size_t)nb * (nb + 1) + 2 * nb) + sizeof(int) * nb;
@@ -1764,12 +1918,33 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc inversion work");
   }
   const size_t smem = in_smem ? smem_full : telt * 2 * nb + sizeof(int) * nb;
+  for (int set = 0; set < nsets; ++set) {
+    const int b = shared ? S.pc_shared : set;
+    OpParams Pb = P;
+    if (P.phiapp_batch) Pb.phiapp_batch = P.phiapp_batch + 4 * b;
+    // assemble operating point b's blocks: column j of every block per grid.y
+    if (f64) {
+      e = enp::launch_op<double>(enp::kBlockCol, Pb, h->d_tab, u + b * P.batch_stride, nullptr,
+                                 S.blocks, nb, h->stream);
+      if (e != cudaSuccess) return cuda_err(h, e, "block columns");
+      if (S.potential_only)
+        enp::block_species_identity<double><<<grid_for((long long)(nb - P.Np) * nb * nblk), 256, 0,
+                                              h->stream>>>(S.blocks, nblk, nb, P.Np);
+    } else {
+      e = enp::launch_op<float>(enp::kBlockCol, Pb, h->d_tab, S.u32 + b * P.batch_stride, nullptr,
+                                S.blocks32, nb, h->stream);
+      if (e != cudaSuccess) return cuda_err(h, e, "FP32 block columns");
+      if (S.potential_only)
+        enp::block_species_identity<float><<<grid_for((long long)(nb - P.Np) * nb * nblk), 256, 0,
+                                             h->stream>>>(S.blocks32, nblk, nb, P.Np);
+    }
+    void* out = (char*)S.binv + esz * nn * nblk * set;
 #define ENP_GJ(T, TS, SM, TB, SRC)                                                              \
   {                                                                                             \
     auto k = enp::gj_invert<T, TS, SM, TB>;                                                     \
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
     if (e == cudaSuccess) {                                                                     \
-      k<<<(unsigned)nblk, threads, smem, h->stream>>>(SRC, (T*)S.gj_work, (TS*)S.binv, nb,      \
+      k<<<(unsigned)nblk, threads, smem, h->stream>>>(SRC, (T*)S.gj_work, (TS*)out, nb,         \
                                                       S.d_flag, T(0));                          \
       e = cudaGetLastError();                                                                   \
     }                                                                                           \
@@ -1781,7 +1956,18 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     const size_t sm = sizeof(float) * (size_t)nb * nb;                                            \
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);            \
     if (e == cudaSuccess) {                                                                       \
-      k<<<(unsigned)nblk, NW * 32, sm, h->stream>>>(S.blocks32, (TS*)S.binv, nb, S.d_flag, 0.f);  \
+      k<<<(unsigned)nblk, NW * 32, sm, h->stream>>>(S.blocks32, (TS*)out, nb, S.d_flag, 0.f);     \
+      e = cudaGetLastError();                                                                     \
+    }                                                                                             \
+  }
+// FP32 inversion of blocks up to 256 x 256: a two-CTA cluster per block
+#define ENP_GJC(TS)                                                                               \
+  {                                                                                               \
+    auto k = enp::gj_invert_cluster<TS>;                                                          \
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);            \
+    if (e == cudaSuccess) {                                                                       \
+      k<<<(unsigned)(2 * nblk), enp::kGjcNW * 32, sm, h->stream>>>(S.blocks32, (TS*)out, nb,      \
+                                                                  S.d_flag);                      \
       e = cudaGetLastError();                                                                     \
     }                                                                                             \
   }
@@ -1791,21 +1977,28 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
   else if (nb <= 96) ENP_GJR(TS, 8, 12, 3)                       \
   else if (nb <= 128) ENP_GJR(TS, 16, 8, 4)                      \
   else ENP_GJR(TS, 16, 12, 6)
-  const bool regs = !f64 && nb <= 192;
-  if (regs) {
-    if (storage == 1) ENP_GJR_ANY(float)
-    else ENP_GJR_ANY(__nv_bfloat16)
-  } else if (storage == 0) {
-    if (in_smem) ENP_GJ(double, double, true, double, S.blocks) else ENP_GJ(double, double, false, double, S.blocks)
-  } else if (storage == 1) {
-    if (in_smem) ENP_GJ(float, float, true, float, S.blocks32) else ENP_GJ(float, float, false, float, S.blocks32)
-  } else {
-    if (in_smem) ENP_GJ(float, __nv_bfloat16, true, float, S.blocks32)
-    else ENP_GJ(float, __nv_bfloat16, false, float, S.blocks32)
-  }
+    const bool regs = !f64 && nb <= 192;
+    const bool clus = !f64 && !regs && nb <= enp::kGjcCols;
+    if (regs) {
+      if (storage == 1) ENP_GJR_ANY(float)
+      else ENP_GJR_ANY(__nv_bfloat16)
+    } else if (clus) {
+      const size_t sm = sizeof(float) * (size_t)((nb + 1) / 2) * nb;
+      if (storage == 1) ENP_GJC(float) else ENP_GJC(__nv_bfloat16)
+    } else if (storage == 0) {
+      if (in_smem) ENP_GJ(double, double, true, double, S.blocks) else ENP_GJ(double, double, false, double, S.blocks)
+    } else if (storage == 1) {
+      if (in_smem) ENP_GJ(float, float, true, float, S.blocks32) else ENP_GJ(float, float, false, float, S.blocks32)
+    } else {
+      if (in_smem) ENP_GJ(float, __nv_bfloat16, true, float, S.blocks32)
+      else ENP_GJ(float, __nv_bfloat16, false, float, S.blocks32)
+    }
 #undef ENP_GJ
+#undef ENP_GJC
 #undef ENP_GJR_ANY
 #undef ENP_GJR
+    if (e != cudaSuccess) break;
+  }
   if (e != cudaSuccess) return cuda_err(h, e, "block inversion");
   int flag = 0;
   e = cudaMemcpyAsync(&flag, S.d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
@@ -1864,15 +2057,15 @@ static cudaError_t bj_apply_plain(enp_handle h, const TV* x, TV* y) {
   if (S.storage == 0) {
     size_t sm = sizeof(double) * nb;
     enp::bj_apply_kernel<double, double, TV><<<g, threads, sm, h->stream>>>(
-        (const double*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride);
+        (const double*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride, S.pc_shared_built);
   } else if (S.storage == 1) {
     size_t sm = sizeof(float) * nb;
     enp::bj_apply_kernel<float, float, TV><<<g, threads, sm, h->stream>>>(
-        (const float*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride);
+        (const float*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride, S.pc_shared_built);
   } else {
     size_t sm = sizeof(float) * nb;
     enp::bj_apply_kernel<__nv_bfloat16, float, TV><<<g, threads, sm, h->stream>>>(
-        (const __nv_bfloat16*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride);
+        (const __nv_bfloat16*)S.binv, x, y, nb, P.NF, P.Np, EN, P.batch_stride, S.pc_shared_built);
   }
   return cudaGetLastError();
 }
@@ -1912,7 +2105,7 @@ static cudaError_t sweep_apply(enp_handle h, const TV* x, TV* z) {
 #define ENP_SWEEP(TS, TA)                                                                          \
   enp::sweep_plane_kernel<TS, TA, TV><<<g, threads, sizeof(TA) * nb, h->stream>>>(                 \
       reinterpret_cast<const TS*>(S.binv), x, z, nb, P.NF, P.n, EN, P.batch_stride, a, k,          \
-      P.ne[0], P.ne[1], P.ne[2], up, fb, P.fbuf_stride, P.foff[a], ia, side, dL)
+      P.ne[0], P.ne[1], P.ne[2], up, fb, P.fbuf_stride, P.foff[a], ia, side, dL, S.pc_shared_built)
     if (S.storage == 0) ENP_SWEEP(double, double);
     else if (S.storage == 1) ENP_SWEEP(float, float);
     else ENP_SWEEP(__nv_bfloat16, float);
@@ -1920,6 +2113,20 @@ static cudaError_t sweep_apply(enp_handle h, const TV* x, TV* z) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+extern "C" enp_status enp_set_shared_blocks(enp_handle h, int point) {
+  if (!h) return ENP_ERR_INVALID_ARG;
+  if (point < -1 || point >= h->batch) {
+    h->err = "point must be -1 or an operating point of the batch";
+    return ENP_ERR_INVALID_ARG;
+  }
+  SolverState& S = state_of(h);
+  if (S.pc_shared != point) {
+    S.pc_shared = point;
+    ++S.pc_gen;
+  }
+  return ENP_OK;
 }
 
 extern "C" enp_status enp_set_preconditioner(enp_handle h, int two_level) {

@@ -66,9 +66,10 @@ def test_block_diagonal_matches_oracle(cfg, arith):
     assert _rel(g, ref) < 1e-12
 
 
-# block sizes 16, 54, 81, 128 and 192 (every shape of the FP32 register inversion)
+# block sizes 16, 54, 81, 128 and 192 (every shape of the FP32 register inversion) and
+# 250 (p = 4, two fields: the two-CTA cluster inversion)
 @pytest.mark.parametrize("cfg", ["cube_n3_p1", "cube_n3_p2", "cube_n2_p3", "channel_n1",
-                                 "channel_n1_p3"])
+                                 "channel_n1_p3", "cube_n2_p4"])
 @pytest.mark.parametrize("storage,tol", [(0, 1e-14), (1, 1e-5), (2, 2e-2)])
 def test_block_jacobi_apply_matches_oracle(cfg, storage, tol):
     enp = _enp()
@@ -241,3 +242,43 @@ def test_inner_product_matches_numpy():
     x, y = W.random_vector(P, 1), W.random_vector(P, 2)
     d = op.inner_product(_cuda(x), _cuda(y))[0]
     assert abs(d - float(np.dot(x, y))) <= 1e-13 * float(np.dot(np.abs(x), np.abs(y)))
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_shared_block_inverses(storage):
+    """One set of block inverses for the whole batch (enp_set_shared_blocks):
+    with identical operating points the apply equals the per-point apply bit
+    for bit; with different states FGMRES preconditioned by the shared set
+    reaches the per-point solutions."""
+    import torch
+    enp = _enp()
+    P = W.config("reactor_n1_p2")
+    B = 2
+    phis = np.array([[4.0, 0, 0, 0], [4.0, 0, 0, 0]])
+    u1 = W.random_state(P, 2)
+    x = np.concatenate([W.random_vector(P, 5), W.random_vector(P, 6)])
+    ys = []
+    for shared in (-1, 1):
+        op = enp.Operator(P, batch=B)
+        op.set_phi_app(phis)
+        op.set_shared_blocks(shared)
+        op.block_jacobi_setup(_cuda(np.concatenate([u1, u1])), storage)
+        ys.append(op.block_jacobi_apply(_cuda(x)).cpu().numpy())
+    np.testing.assert_array_equal(ys[0], ys[1])
+    # different operating points: the shared set still preconditions FGMRES
+    phis = np.array([[4.0, 0, 0, 0], [20.0, 0, 0, 0]])
+    u = _cuda(np.concatenate([W.random_state(P, 2), W.random_state(P, 3)]))
+    b = _cuda(x)
+    sols = []
+    for shared in (-1, 0):
+        op = enp.Operator(P, batch=B)
+        op.set_phi_app(phis)
+        op.set_shared_blocks(shared)
+        op.block_jacobi_setup(u, storage)
+        xs = torch.zeros_like(b)
+        st = op.fgmres_solve(u, b, xs, restart=40, max_it=3000, rtol=1e-10)
+        assert st["converged"] == 1, st
+        sols.append(xs.cpu().numpy())
+    assert _rel(sols[1], sols[0]) < 1e-7
+    with pytest.raises(enp.EnpError):
+        op.set_shared_blocks(B)
