@@ -309,7 +309,8 @@ def run_solves(enp, W, name, labels=None, reference="fp64"):
 
 def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
                       labels=("fp64", "mixed", "mixed_device_loop", "mixed_sweep",
-                              "mixed_paper_guess"), pc_lag=1):
+                              "mixed_paper_guess"), pc_lag=1, shared_blocks=-1, storage="f32",
+                      restart=50):
     """The operating-point sweep of the plate reactor (Sec. 5.2): `batch`
     applied cathode potentials from volts[0] to volts[1] (anode at 0), all
     solved in one batched Newton run per stage, with continuation in the
@@ -330,18 +331,22 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
     op = enp.Operator(prob, batch=batch)
     op.autotune()
     op.set_preconditioner(1)
+    op.set_shared_blocks(shared_blocks)
+    bj_mixed = enp.BJ_BF16 if storage == "bf16" else enp.BJ_F32
     step0 = 0.125
     u0 = W.reactor_initial_state(prob, phis * step0)
     out = {"workload": name, "batch": batch, "volts": list(volts), "n_dof_per_point": prob.n_dof,
-           "pc_lag": pc_lag,
+           "pc_lag": pc_lag, "shared_blocks": shared_blocks, "mixed_storage": storage,
+           "restart": restart,
            "rtol_last_stage": 1e-10, "continuation": "lambda from 0.125, x1.5 after a converged "
            "stage (max 0.25), /2 after a failed one; intermediate stages to 1e-6 in 10 iterations"}
     sols = {}
     kws = {"fp64": dict(bj_storage=enp.BJ_F64, mixed=False),
-           "mixed": dict(bj_storage=enp.BJ_F32, mixed=True),
-           "mixed_sweep": dict(bj_storage=enp.BJ_F32, mixed=True),
-           "mixed_paper_guess": dict(bj_storage=enp.BJ_F32, mixed=True),
-           "mixed_device_loop": dict(bj_storage=enp.BJ_F32, mixed=True, device_loop=True)}
+           "mixed": dict(bj_storage=bj_mixed, mixed=True),
+           "mixed_sweep": dict(bj_storage=bj_mixed, mixed=True),
+           "mixed_paper_guess": dict(bj_storage=bj_mixed, mixed=True),
+           "mixed_device_loop": dict(bj_storage=bj_mixed, mixed=True, device_loop=True),
+           "mixed_device_loop_sweep": dict(bj_storage=bj_mixed, mixed=True, device_loop=True)}
     for label in labels:
         op.set_sweep(1 if label.endswith("_sweep") else 0)
         u = torch.tensor(u0, device="cuda")
@@ -353,7 +358,7 @@ def run_batched_solve(enp, W, name, batch=8, volts=(0.1, 0.8),
             gst = op.initial_guess(u, rtol=1e-8, krylov_rtol=1e-2, graph=True,
                                    raise_on_fail=False, **kws[label])
         st = op.newton_continuation(u, target, step0=step0, graph=True, raise_on_fail=False,
-                                    pc_lag=pc_lag, **kws[label])
+                                    pc_lag=pc_lag, krylov_restart=restart, **kws[label])
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         sols[label] = u.cpu().numpy()
@@ -459,6 +464,12 @@ def main():
                          "batched 0.1-0.8 V sweep of --reactor-workload and print its record")
     ap.add_argument("--reactor-pc-lag", type=int, default=1,
                     help="preconditioner rebuilds every this many Newton iterations in the sweep")
+    ap.add_argument("--reactor-shared-blocks", type=int, default=-1,
+                    help=">= 0: one set of block inverses (of this operating point) for the "
+                         "whole batch in the sweep (the memory strategy at p = 4)")
+    ap.add_argument("--reactor-storage", default="f32", choices=["f32", "bf16"],
+                    help="block-inverse storage of the mixed sweeps")
+    ap.add_argument("--reactor-restart", type=int, default=50, help="FGMRES restart of the sweep")
     ap.add_argument("--channel-solve", type=int, default=0,
                     help="1: also solve channel64_p3 (3 species, 6.3M DOFs) to 1e-10, FP64 "
                          "(double-float arithmetic) and mixed (FP32 inner, BF16 inverses)")
@@ -495,7 +506,10 @@ def main():
             t0 = time.perf_counter()
             rec = run_batched_solve(enp, W, args.reactor_workload,
                                     labels=tuple(args.reactor_only.split(",")),
-                                    pc_lag=args.reactor_pc_lag)
+                                    pc_lag=args.reactor_pc_lag,
+                                    shared_blocks=args.reactor_shared_blocks,
+                                    storage=args.reactor_storage,
+                                    restart=args.reactor_restart)
             rec["wall_seconds"] = time.perf_counter() - t0
             print(json.dumps({"reactor_only": rec}), flush=True)
         return

@@ -21,6 +21,8 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -1913,7 +1915,10 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
   const size_t smem_full = telt * ((size_t)nb * (nb + 1) + 2 * nb) + sizeof(int) * nb;
   const bool in_smem = smem_full <= 200 * 1024;
   const int threads = 512;
-  if (!in_smem) {
+  // the global-memory work copy serves only the generic kernel on blocks too
+  // large for shared memory (FP64 beyond 160, FP32 beyond 256 unknowns)
+  const bool generic = f64 || nb > enp::kGjcCols;
+  if (generic && !in_smem) {
     e = ensure((char**)&S.gj_work, S.gj_work_bytes, telt * (size_t)nb * (nb + 1) * nblk);
     if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc inversion work");
   }
@@ -3065,6 +3070,9 @@ extern "C" enp_status enp_newton_continuation(enp_handle h, double* u, const dou
   enp_continuation_stats cs{};
   double lam = 0.0, dl = c->step0;
   enp_status status = ENP_OK;
+  // ENP_CONTINUATION_LOG set: one progress line per stage on stderr (long runs)
+  const bool log = std::getenv("ENP_CONTINUATION_LOG") != nullptr;
+  const auto t_start = std::chrono::steady_clock::now();
   while (true) {
     const double nl = std::min(1.0, lam + dl);
     const bool last = nl >= 1.0;
@@ -3081,6 +3089,15 @@ extern "C" enp_status enp_newton_continuation(enp_handle h, double* u, const dou
     cs.newton_iterations += ns.iterations;
     cs.krylov_iterations += ns.krylov_iterations;
     cs.last = ns;
+    if (log) {
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      std::fprintf(stderr,
+                   "continuation stage %d: lambda %.4f status %d newton %d krylov %d ||R||/||R0|| %.3e "
+                   "elapsed %.1f s\n",
+                   cs.stages, last ? 1.0 : nl, (int)s2, ns.iterations, ns.krylov_iterations,
+                   ns.initial_norm > 0 ? ns.residual_norm / ns.initial_norm : 0.0, el);
+      std::fflush(stderr);
+    }
     if (s2 == ENP_OK) {
       e = cudaMemcpyAsync(u, ut, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, h->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
