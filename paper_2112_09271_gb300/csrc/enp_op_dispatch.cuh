@@ -7,6 +7,7 @@
 #include "enp_internal.h"
 #include "enp_operator.cuh"
 #include "enp_operator3d.cuh"
+#include "enp_blockcols.cuh"
 
 namespace enp {
 
@@ -91,10 +92,46 @@ static int max_eb() {
   return eb < 1 ? 1 : eb;
 }
 
-// Hexahedra: the thread-per-pencil kernel with EB elements per block.
+// Columns of the element-diagonal blocks per (element, chunk of kBlockChunk
+// columns), the state's point values and face traces formed once per chunk.
+constexpr int kBlockChunk = 16;
+template <int P, int NF, class R>
+static cudaError_t launch_blockcols(const OpParams& prm, const io_t<R>* u, io_t<R>* out,
+                                    cudaStream_t stream) {
+  constexpr int NT = tpe3d<P, R>();
+  constexpr size_t smem = (size_t)SmemB<P, NF, NT, kBlockChunk>::total * sizeof(R);
+  static_assert(smem <= 200 * 1024, "block-column kernel shared memory");
+  auto k = blockcol3d_kernel<P, NF, kBlockChunk, R>;
+  static SmemAttr attr;
+  cudaError_t e = raise_smem_limit(attr, k, smem);
+  if (e != cudaSuccess) return e;
+  constexpr int nb = NF * (P + 1) * (P + 1) * (P + 1);
+  const dim3 grid((unsigned)prm.E, (nb + kBlockChunk - 1) / kBlockChunk);
+  k<<<grid, NT, smem, stream>>>(prm, u, out);
+  return cudaGetLastError();
+}
+
+template <int P, int NF, int MODE, class R>
+static cudaError_t launch_3d_op(const OpParams& prm, const io_t<R>* u, const io_t<R>* v,
+                                io_t<R>* out, int batch, cudaStream_t stream);
+
+// Hexahedra: the thread-per-pencil kernel with EB elements per block (the FP32
+// block columns: blockcol3d_kernel).
 template <int P, int NF, int MODE, class R>
 static cudaError_t launch_3d(const OpParams& prm, const io_t<R>* u, const io_t<R>* v, io_t<R>* out,
                              int batch, cudaStream_t stream) {
+  if constexpr (MODE == kBlockCol) {
+    (void)v;
+    (void)batch;  // the nb columns
+    return launch_blockcols<P, NF, R>(prm, u, out, stream);
+  } else {
+    return launch_3d_op<P, NF, MODE, R>(prm, u, v, out, batch, stream);
+  }
+}
+
+template <int P, int NF, int MODE, class R>
+static cudaError_t launch_3d_op(const OpParams& prm, const io_t<R>* u, const io_t<R>* v,
+                                io_t<R>* out, int batch, cudaStream_t stream) {
   constexpr int NT = tpe3d<P, R>();
   using S3 = Smem3<P, NF, MODE, NT>;
   constexpr size_t per_el = (size_t)S3::total * sizeof(R);

@@ -21,7 +21,7 @@
 
 namespace enp {
 
-constexpr int kTabSz = 96;  // per degree: B (Q*N), Dq (Q*Q), dL (2N), wq (Q), xq (Q)
+constexpr int kTabSz = 128;  // per degree: B (Q*N), Dq (Q*Q), dL (2N), wq (Q), xq (Q), BD (Q*N)
 static __constant__ double c_tabd[kMaxP + 1][kTabSz];
 static __constant__ float c_tabf[kMaxP + 1][kTabSz];
 static __constant__ float2 c_tabdf[kMaxP + 1][kTabSz];   // (hi, lo) double-float pairs
@@ -39,6 +39,14 @@ static inline cudaError_t upload_const_tables(int p, const Tables& t) {
   for (int i = 0; i < 2 * n; ++i) d[o++] = t.dL[i];
   for (int i = 0; i < q; ++i) d[o++] = t.wq[i];
   for (int i = 0; i < q; ++i) d[o++] = t.xq[i];
+  // BD = Dq B: the derivative of each basis function at the Gauss points, as the
+  // operator forms gradients (collocation derivative of the interpolant)
+  for (int a = 0; a < q; ++a)
+    for (int i = 0; i < n; ++i) {
+      double sacc = 0.0;
+      for (int b = 0; b < q; ++b) sacc += t.Dq[a * q + b] * t.B[b * n + i];
+      d[o++] = sacc;
+    }
   for (int i = 0; i < kTabSz; ++i) {
     f[i] = (float)d[i];
     const df x(d[i]);
@@ -59,6 +67,8 @@ __device__ __forceinline__ R ctab(int i) {
 template <int P> struct TabOff {
   static constexpr int N = P + 1, Q = P + 2;
   static constexpr int B = 0, Dq = Q * N, dL = Q * N + Q * Q, W = dL + 2 * N, X = W + Q;
+  static constexpr int BD = X + Q;
+  static_assert(BD + Q * N <= kTabSz, "table block too small");
 };
 
 // One thread per pencil: out = M in along direction DIR of a 3D array with

@@ -46,6 +46,10 @@ def _prob(cfg):
         return W.config(cfg, p=2)
     if cfg == "channel_n1_p3":
         return W.config("channel_n1", p=3)
+    if cfg == "cube_n2_p3_dirichlet":
+        import dataclasses
+        P = W.config("cube_n2_p3")
+        return dataclasses.replace(P, tags=[np.full_like(t, W.DIRICHLET) for t in P.tags])
     return W.config(cfg)
 
 
@@ -69,7 +73,8 @@ def test_block_diagonal_matches_oracle(cfg, arith):
 # block sizes 16, 54, 81, 128 and 192 (every shape of the FP32 register inversion) and
 # 250 (p = 4, two fields: the two-CTA cluster inversion)
 @pytest.mark.parametrize("cfg", ["cube_n3_p1", "cube_n3_p2", "cube_n2_p3", "channel_n1",
-                                 "channel_n1_p3", "cube_n2_p4"])
+                                 "channel_n1_p3", "cube_n2_p4", "reactor_n1_p2",
+                                 "cube_n2_p3_dirichlet"])
 @pytest.mark.parametrize("storage,tol", [(0, 1e-14), (1, 1e-5), (2, 2e-2)])
 def test_block_jacobi_apply_matches_oracle(cfg, storage, tol):
     enp = _enp()
