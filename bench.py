@@ -62,10 +62,9 @@ DF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
 # of the sources that kernel is built from (stale -> reported null): the
 # operator kernels from the operator headers, the block apply from the solver.
 TRAFFIC = {
-    ("451a1176cccc", "jvp_f64", "channel64_p3"): 692.34e6,   # face + element kernel
-    ("451a1176cccc", "jvp_f32", "channel64_p3"): 244.96e6,   # face + element kernel
-    ("451a1176cccc", "vjp_f64", "channel64_p3"): 689.70e6,   # face + element kernel
-    ("dfe77693e020", "bj_apply_f32", "channel64_p3"): 4933.86e6,
+    ("f72a4843adac", "jvp_df32", "channel64_p3"): 702.67e6,  # face + element kernel
+    ("f72a4843adac", "jvp_f32", "channel64_p3"): 245.62e6,   # face + element kernel
+    ("33fe528c30dc", "bj_apply_f32", "channel64_p3"): 4933.98e6,
 }
 
 KERNEL_SOURCES = {
@@ -104,6 +103,7 @@ def _kernel_hash(kind=None):
 
 def _family(op_name):
     return "solver" if op_name.startswith("bj_") else "operator"
+
 
 
 def contraction_flops(dim, p, nf, mode):
@@ -475,7 +475,8 @@ def main():
                          "(double-float arithmetic) and mixed (FP32 inner, BF16 inverses)")
     ap.add_argument("--only", default=None,
                     help="time one operator alone (for profiling): residual_f64, jvp_f64, "
-                         "vjp_f64, residual_df32, jvp_df32, vjp_df32, jvp_f32, bj_apply_f32; "
+                         "vjp_f64, residual_df32, jvp_df32, vjp_df32, jvp_f32, bj_apply_f32, "
+                         "bj_setup_f32 (block-Jacobi setup: FP32 block columns and inversion); "
                          "no autotune, solves or e2e; or "
                          "fgmres_f64 / fgmres_f32: FGMRES(50) cycles with the two-level "
                          "preconditioner on the solve workload")
@@ -549,7 +550,8 @@ def main():
         ops, applications = [args.only], [args.only]
     op_l = 2 if prob.dim == 3 else 1   # hexahedra: a face launch, then an element launch
     launches = {nm: op_l for nm in fp64_ops + ["jvp_f32"]}
-    launches.update({"bj_apply_f32": 1, "recover_cm": 1, "inner_product": 2})
+    launches.update({"bj_apply_f32": 1, "recover_cm": 1, "inner_product": 2,
+                     "bj_setup_f32": 3})  # FP32 copy of u, block columns, inversion
     launches_per_step = sum(launches[nm] for nm in ops)
     ip_out = np.zeros(1)
 
@@ -567,6 +569,8 @@ def main():
             op.jvp_f32(u32, v32, out=jv32)
         elif name == "bj_apply_f32":
             op.block_jacobi_apply(v, out=z)
+        elif name == "bj_setup_f32":
+            op.block_jacobi_setup(u, enp.BJ_F32)  # block columns + inversion (synchronises)
         elif name == "recover_cm":
             op.recover_cm(u, out=cm)
         else:
