@@ -470,6 +470,9 @@ def main():
     ap.add_argument("--reactor-storage", default="f32", choices=["f32", "bf16"],
                     help="block-inverse storage of the mixed sweeps")
     ap.add_argument("--reactor-restart", type=int, default=50, help="FGMRES restart of the sweep")
+    ap.add_argument("--reactor-parts", type=int, default=1,
+                    help="solve the 8 operating points as this many consecutive batches (each "
+                         "with its own per-point block inverses: the memory strategy at p = 4)")
     ap.add_argument("--channel-solve", type=int, default=0,
                     help="1: also solve channel64_p3 (3 species, 6.3M DOFs) to 1e-10, FP64 "
                          "(double-float arithmetic) and mixed (FP32 inner, BF16 inverses)")
@@ -505,12 +508,18 @@ def main():
     if args.reactor_only:
         if rank == 0:
             t0 = time.perf_counter()
-            rec = run_batched_solve(enp, W, args.reactor_workload,
-                                    labels=tuple(args.reactor_only.split(",")),
-                                    pc_lag=args.reactor_pc_lag,
-                                    shared_blocks=args.reactor_shared_blocks,
-                                    storage=args.reactor_storage,
-                                    restart=args.reactor_restart)
+            parts = max(1, args.reactor_parts)
+            volts = np.linspace(0.1, 0.8, 8)
+            recs = []
+            for part in np.array_split(volts, parts):
+                recs.append(run_batched_solve(enp, W, args.reactor_workload, batch=len(part),
+                                              volts=(float(part[0]), float(part[-1])),
+                                              labels=tuple(args.reactor_only.split(",")),
+                                              pc_lag=args.reactor_pc_lag,
+                                              shared_blocks=args.reactor_shared_blocks,
+                                              storage=args.reactor_storage,
+                                              restart=args.reactor_restart))
+            rec = recs[0] if parts == 1 else {"parts": recs}
             rec["wall_seconds"] = time.perf_counter() - t0
             print(json.dumps({"reactor_only": rec}), flush=True)
         return
