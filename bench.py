@@ -62,8 +62,8 @@ DF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
 # of the sources that kernel is built from (stale -> reported null): the
 # operator kernels from the operator headers, the block apply from the solver.
 TRAFFIC = {
-    ("f72a4843adac", "jvp_df32", "channel64_p3"): 702.67e6,  # face + element kernel
-    ("f72a4843adac", "jvp_f32", "channel64_p3"): 245.62e6,   # face + element kernel
+    ("21842bd24676", "jvp_df32", "channel64_p3"): 699.90e6,  # face + element kernel
+    ("21842bd24676", "jvp_f32", "channel64_p3"): 242.14e6,   # face + element kernel
     ("33fe528c30dc", "bj_apply_f32", "channel64_p3"): 4933.98e6,
 }
 
@@ -416,6 +416,56 @@ def run_fgmres_profile(enp, W, args):
             "iterations": its, "ms_per_iteration": 1e3 * t / its, "kernel_hash": _kernel_hash()}
 
 
+def run_precond_profile(enp, W, args):
+    """Block-Jacobi against the downwind block Gauss-Seidel sweep (`--only
+    precond_f32`) on the solve workload, FP32 inverses and the two-level
+    correction: the time of one preconditioner application to an FP32 vector
+    (CUDA events, L2 flushed before each) and one FP32 FGMRES(50) linear solve
+    to 1e-4 at the reactor's initial state for 0.45 V (a random state on other
+    workloads)."""
+    import torch
+    prob = W.config(args.solve_workload)
+    op = enp.Operator(prob)
+    op.autotune()
+    op.set_preconditioner(1)
+    if prob.name.startswith("reactor"):
+        u = torch.tensor(W.reactor_initial_state(prob, [0.45 * 38.92]), device="cuda")
+    else:
+        u = torch.tensor(W.random_state(prob, 2), device="cuda")
+    x = torch.tensor(W.random_vector(prob, 6), device="cuda").float()
+    y = torch.empty_like(x)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"only": args.only, "workload": prob.name, "n_dof": prob.n_dof,
+           "fgmres": "FP32, restart 50, rtol 1e-4", "kernel_hash": _kernel_hash()}
+    for sweep in (0, 1):
+        op.set_sweep(sweep)
+        op.block_jacobi_setup(u, enp.BJ_F32)
+        ms = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            op.block_jacobi_apply_f32(x, out=y)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        z = torch.zeros_like(x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.fgmres_solve(u.float(), x, z, restart=50, max_it=5000, rtol=1e-4,
+                             raise_on_fail=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["sweep" if sweep else "block_jacobi"] = {
+            "apply_ms": float(np.median(ms)), "fgmres_iterations": st["iterations"],
+            "fgmres_seconds": dt, "ms_per_iteration": 1e3 * dt / max(1, st["iterations"]),
+            "converged": st["converged"] == 1,
+            # the true residual of the FP32 iterate (an FP32 J v), relative to b
+            "relative_residual": st["relative_residual"]}
+    return out
+
+
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
@@ -482,7 +532,9 @@ def main():
                          "bj_setup_f32 (block-Jacobi setup: FP32 block columns and inversion); "
                          "no autotune, solves or e2e; or "
                          "fgmres_f64 / fgmres_f32: FGMRES(50) cycles with the two-level "
-                         "preconditioner on the solve workload")
+                         "preconditioner on the solve workload; precond_f32: block-Jacobi "
+                         "against the downwind sweep on the solve workload (one application, "
+                         "one linear solve to 1e-4)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -526,6 +578,10 @@ def main():
     if args.only in ("fgmres_f64", "fgmres_f32"):
         if rank == 0:
             print(json.dumps(run_fgmres_profile(enp, W, args)), flush=True)
+        return
+    if args.only == "precond_f32":
+        if rank == 0:
+            print(json.dumps(run_precond_profile(enp, W, args)), flush=True)
         return
     prob = W.config(args.workload)
     stream = torch.cuda.Stream()

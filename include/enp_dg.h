@@ -207,9 +207,15 @@ enp_status enp_block_diagonal(enp_handle h, const double* u, double* blocks);
 enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage);
 
 /* y = M^{-1} x with M the preconditioner of the last setup: the inverse block
- * diagonal, plus the coarse correction when the two-level preconditioner is on.
- * x, y: [batch][m][E][Np]. */
+ * diagonal (or, with enp_set_sweep on, the downwind block Gauss-Seidel sweep),
+ * plus the coarse correction when the two-level preconditioner is on.
+ * x, y: device [batch][m][E][Np], not overlapping. Runs on the handle's stream.
+ * Errors: INVALID_ARG before a setup. */
 enp_status enp_block_jacobi_apply(enp_handle h, const double* x, double* y);
+
+/* The same with FP32 vectors, as the FP32 Krylov solve of the mixed-precision
+ * Newton method applies it (the sweep's upstream face terms in FP32). */
+enp_status enp_block_jacobi_apply_f32(enp_handle h, const float* x, float* y);
 
 /* Memory strategy of the block inverses for large batches: point = -1 (the
  * default) stores one set of element-block inverses per operating point;
@@ -254,17 +260,22 @@ enp_status enp_set_preconditioner(enp_handle h, int two_level);
 enp_status enp_set_coarse_options(enp_handle h, int cycles, int smooth, double omega);
 
 /* Replace the block-Jacobi part of the preconditioner by one downwind block
- * Gauss-Seidel sweep (on = 1; 0 restores block-Jacobi), hexahedral meshes:
+ * Gauss-Seidel sweep (on = 1; 0 keeps block-Jacobi; 2, the default, chooses:
+ * the sweep on hexahedral meshes with a non-zero velocity and at least 128
+ * elements along the flow axis, block-Jacobi otherwise), hexahedral meshes:
  * z = (D + L)^-1 r, D the element-diagonal blocks of the last setup and L the
  * coupling of every element to its upstream neighbour along the flow axis (the
  * plate-flow axis in the sign of its mean speed, or the largest component of a
- * constant velocity, in its direction). The element planes across that axis are solved in flow order:
- * each plane subtracts the face terms of J(u) z of the planes already solved
- * (the face kernel restricted to the faces in between, at the u of the last
- * setup) and applies its block inverses; 2 launches per plane. With upwind
- * advection dominating, this carries information along the whole channel in
- * one application, where block-Jacobi moves it one element per Krylov
- * iteration (Pe = 1e4 in the plate reactor of Sec. 5.2). Combines with the
+ * constant velocity, in its direction). The element planes across that axis
+ * are solved in flow order, one launch per plane: each element evaluates the
+ * face term of J(u) z between it and its upstream neighbour (the face kernel's
+ * arithmetic, at the u of the last setup, z of the plane solved before) and
+ * applies its block inverse. With upwind advection dominating, this carries
+ * information along the whole channel in one application, where block-Jacobi
+ * moves it one element per Krylov iteration (Pe = 1e4 in the plate reactor of
+ * Sec. 5.2); it costs about 9 us per plane, so it pays on long channels (on the
+ * plate reactor: 1.5x faster linear solves at 192 elements along the flow,
+ * slower at 96 and below, hence the automatic threshold). Combines with the
  * two-level correction (added after the sweep). Takes effect at the next
  * enp_block_jacobi_setup, which then also keeps a copy of u.
  * Errors: INVALID_ARG, UNSUPPORTED (on = 1 on a 2D mesh). */

@@ -167,6 +167,7 @@ _PROTOS = [
     ("enp_block_diagonal", _I, [_V, _V, _V]),
     ("enp_block_jacobi_setup", _I, [_V, _V, _I]),
     ("enp_block_jacobi_apply", _I, [_V, _V, _V]),
+    ("enp_block_jacobi_apply_f32", _I, [_V, _V, _V]),
     ("enp_set_preconditioner", _I, [_V, _I]),
     ("enp_set_shared_blocks", _I, [_V, _I]),
     ("enp_set_coarse_options", _I, [_V, _I, _I, ctypes.c_double]),
@@ -394,6 +395,14 @@ class Operator:
                                                      _dptr(out, torch.float64)))
         return out
 
+    def block_jacobi_apply_f32(self, x, out=None):
+        """The preconditioner on FP32 vectors (the mixed-precision inner solve's)."""
+        import torch
+        out = self._new(torch.float32) if out is None else out
+        self._check(self._lib.enp_block_jacobi_apply_f32(self.h, _dptr(x, torch.float32),
+                                                         _dptr(out, torch.float32)))
+        return out
+
     def set_preconditioner(self, two_level):
         """0: block-Jacobi; 1: block-Jacobi plus the coarse potential correction
         (takes effect at the next block_jacobi_setup)."""
@@ -405,7 +414,8 @@ class Operator:
         self._check(self._lib.enp_set_shared_blocks(self.h, int(point)))
 
     def set_sweep(self, on):
-        """1: downwind block Gauss-Seidel instead of block-Jacobi (next setup)."""
+        """1: downwind block Gauss-Seidel instead of block-Jacobi; 0: block-Jacobi;
+        2 (the default): the sweep on long channels (next setup)."""
         self._check(self._lib.enp_set_sweep(self.h, int(on)))
 
     def set_coarse_options(self, cycles=1, smooth=2, omega=1.0):

@@ -36,7 +36,7 @@ struct SmemB {
   static constexpr int kFC = 6 * 2 * NF * FQ;         // face coefficients [face][S, T][f]
   static constexpr int kG1 = 6 * 2 * NF * Q * N;
   static constexpr int kG2 = 6 * 2 * NF * FNP;
-  static constexpr int kCOL = NF * NN * CH;           // the chunk's columns [row][column]
+  static constexpr int kCOL = NF * NN * (CH + 1);     // the chunk's columns [row][column], rows padded
   // the neighbour and face-trace scratch of the set-up phase reuse PO/T2/T1
   static constexpr int kSetup = NF * NNP + 2 * NF * 2 * FNP + 2 * NF * 2 * Q * N + 2 * NF * 2 * FQ;
   static constexpr int kColWork = kPO + kT2 + (kT1 > kFC + kG1 + kG2 ? kT1 : kFC + kG1 + kG2);
@@ -61,7 +61,7 @@ blockcol3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, io_t<R>* __
   R* PU = XA + S::kX;                        // [NF][4][NQ]
   R* TRU = PU + S::kPU;                      // [6][2][NF][2][FQ]
   R* RO = TRU + S::kTRU;                     // [NF][NNP]
-  R* COL = RO + S::kRO;                      // [nb][CH]
+  R* COL = RO + S::kRO;                      // [nb][CH + 1]: consecutive rows in different banks
   R* WK = COL + S::kCOL;
   const int tid = threadIdx.x;
   const int e = blockIdx.x;
@@ -99,9 +99,7 @@ blockcol3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, io_t<R>* __
     __syncthreads();
     pencil<P, Q, Q, N, 2, 0, false, false, NF, Q * Q * N, 4 * NQ>(T2, PU, tid, NT);
     __syncthreads();
-    pencil<P, Q, Q, Q, 0, 1, false, false, NF, 4 * NQ, 4 * NQ>(PU, PU + NQ, tid, NT);
-    pencil<P, Q, Q, Q, 1, 1, false, false, NF, 4 * NQ, 4 * NQ>(PU, PU + 2 * NQ, tid, NT);
-    pencil<P, Q, Q, Q, 2, 1, false, false, NF, 4 * NQ, 4 * NQ>(PU, PU + 3 * NQ, tid, NT);
+    pencil_grad3<P, NF, 4 * NQ>(PU, tid, NT);
     __syncthreads();
   }
   // the six faces: this element's and the neighbour's traces of the state
@@ -324,14 +322,14 @@ blockcol3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, io_t<R>* __
         if (k == (hi ? N - 1 : 0)) add += sv;
         acc += add;
       }
-      COL[t * CH + cc] = acc;
+      COL[t * (CH + 1) + cc] = acc;
     }
     __syncthreads();
   }
   // the chunk's columns, row by row
   for (int t = tid; t < nb * ncol; t += NT) {
     const int r = t / ncol, cc = t % ncol;
-    out[((long long)e * nb + r) * nb + c0 + cc] = to_io(COL[r * CH + cc]);
+    out[((long long)e * nb + r) * nb + c0 + cc] = to_io(COL[r * (CH + 1) + cc]);
   }
 }
 

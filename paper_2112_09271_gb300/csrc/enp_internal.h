@@ -48,11 +48,16 @@ template <class R> int fpb3d_get(int p, int nf, int mode);
 template <class R>
 cudaError_t prepare_tables(int p, const Tables& t);
 
-// J v face terms of the faces of plane ia of direction a only, into the face
-// buffer (hexahedra).
-template <class R>
-cudaError_t launch_face_plane(const OpParams& prm, const R* u, const R* v, int batch,
-                              cudaStream_t s, int a, int ia);
+// One element plane k (along axis a, flow direction dir = +-1) of the downwind
+// block Gauss-Seidel sweep for every operating point: z_e = Binv_e (x_e -
+// J_(e,up) z_up), the upstream face term evaluated in the same launch
+// (upstream = 0 for the first plane). binv: the transposed block inverses in
+// `storage` (0 FP64, 1 FP32, 2 BF16), one set per point or one shared set;
+// upc: the linearisation point (hexahedra).
+template <class TV>
+cudaError_t launch_sweep_plane(const OpParams& prm, const void* binv, int storage, const TV* x,
+                               TV* z, const TV* upc, int batch, cudaStream_t s, int a, int k,
+                               int dir, int upstream, int shared_blocks);
 
 }  // namespace enp
 

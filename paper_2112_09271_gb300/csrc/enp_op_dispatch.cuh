@@ -8,6 +8,7 @@
 #include "enp_operator.cuh"
 #include "enp_operator3d.cuh"
 #include "enp_blockcols.cuh"
+#include "enp_sweep.cuh"
 
 namespace enp {
 
@@ -154,7 +155,7 @@ static cudaError_t launch_3d_op(const OpParams& prm, const io_t<R>* u, const io_
     if (ef != cudaSuccess) return ef;
     const long long nf = prm.foff[3];
     dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
-    fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v, -1, 0);
+    fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v);
   }
   dim3 grid((prm.E + eb - 1) / eb, batch);
   kern<<<grid, eb * NT, smem, stream>>>(prm, u, v, out);
@@ -217,35 +218,40 @@ static cudaError_t launch_nf(int mode, const OpParams& prm, const Tables* t, con
   return cudaErrorInvalidConfiguration;
 }
 
-// The face kernel of J v on the faces of plane ia of direction a only (the
-// upstream coupling of one plane of a block Gauss-Seidel sweep).
-template <int P, int NF, class R>
-static cudaError_t launch_face_plane_pn(const OpParams& prm, const R* u, const R* v, int batch,
-                                        cudaStream_t stream, int a, int ia) {
-  constexpr int TF = tpf3d<P, R>();
-  constexpr size_t per_face = (size_t)SmemF<P, NF, kJvp, TF>::total * sizeof(R);
-  const int fpb = default_fpb<P, NF, kJvp, R>();
-  auto fk = face3d_kernel<P, NF, kJvp, R>;
-  static SmemAttr attr;  // the limit launch_3d sets for the same kernel
-  cudaError_t ea = raise_smem_limit(attr, fk, (size_t)max_fpb<P, NF, kJvp, R>() * per_face);
-  if (ea != cudaSuccess) return ea;
-  const long long nf = (long long)prm.ne[a == 0 ? 1 : 0] * prm.ne[a == 2 ? 1 : 2];
-  dim3 fgrid((unsigned)((nf + fpb - 1) / fpb), batch);
-  fk<<<fgrid, fpb * TF, fpb * per_face, stream>>>(prm, u, v, a, ia);
+// One plane of the downwind block Gauss-Seidel sweep (sweep_fused_kernel).
+template <int P, int NF, class TV>
+static cudaError_t launch_sweep_pn(const OpParams& prm, const void* binv, int storage, const TV* x,
+                                   TV* z, const TV* upc, int batch, cudaStream_t stream, int a,
+                                   int k, int dir, int upstream, int shared_blocks) {
+  using SS = SweepSmem<P, NF, TV>;
+  auto kern = sweep_fused_kernel<P, NF, TV>;
+  static SmemAttr attr;
+  cudaError_t e = raise_smem_limit(attr, kern, SS::bytes);
+  if (e != cudaSuccess) return e;
+  const int nplane = prm.ne[a == 0 ? 1 : 0] * prm.ne[a == 2 ? 1 : 2];
+  const dim3 grid((unsigned)nplane, (unsigned)batch);
+  kern<<<grid, SS::NT, SS::bytes, stream>>>(prm, binv, storage, x, z, upc, a, k, dir, upstream,
+                                            shared_blocks);
   return cudaGetLastError();
 }
 
-template <class R>
-cudaError_t launch_face_plane(const OpParams& prm, const R* u, const R* v, int batch,
-                              cudaStream_t s, int a, int ia) {
-  if (prm.dim != 3) return cudaErrorInvalidConfiguration;
-#define ENP_FP(PP)                                                                      \
-  case PP:                                                                              \
-    if (prm.NF == 2) return launch_face_plane_pn<PP, 2, R>(prm, u, v, batch, s, a, ia); \
-    if (prm.NF == 3) return launch_face_plane_pn<PP, 3, R>(prm, u, v, batch, s, a, ia); \
+template <class TV>
+cudaError_t launch_sweep_plane(const OpParams& prm, const void* binv, int storage, const TV* x,
+                               TV* z, const TV* upc, int batch, cudaStream_t s, int a, int k,
+                               int dir, int upstream, int shared_blocks) {
+  if (prm.dim != 3 || storage < 0 || storage > 2 || (dir != 1 && dir != -1))
     return cudaErrorInvalidConfiguration;
-  switch (prm.p) { ENP_FP(1) ENP_FP(2) ENP_FP(3) ENP_FP(4) }
-#undef ENP_FP
+#define ENP_SW(PP)                                                                              \
+  case PP:                                                                                      \
+    if (prm.NF == 2)                                                                            \
+      return launch_sweep_pn<PP, 2, TV>(prm, binv, storage, x, z, upc, batch, s, a, k, dir,     \
+                                        upstream, shared_blocks);                               \
+    if (prm.NF == 3)                                                                            \
+      return launch_sweep_pn<PP, 3, TV>(prm, binv, storage, x, z, upc, batch, s, a, k, dir,     \
+                                        upstream, shared_blocks);                               \
+    return cudaErrorInvalidConfiguration;
+  switch (prm.p) { ENP_SW(1) ENP_SW(2) ENP_SW(3) ENP_SW(4) }
+#undef ENP_SW
   return cudaErrorInvalidConfiguration;
 }
 

@@ -71,6 +71,60 @@ template <int P> struct TabOff {
   static_assert(BD + Q * N <= kTabSz, "table block too small");
 };
 
+// The outputs of one pencil: dst[r * os] = sum_k M[r][k] src[k * is] (+ dst[r * os]
+// when ACC), r < ROWS, k < COLS, with M the B table (TAB 0, Q x N, or its
+// transpose) or the Dq table (TAB 1, Q x Q); table entries at compile-time
+// indices.
+template <int P, int TAB, bool TRANS, bool ACC, int COLS, int ROWS, class R>
+__device__ __forceinline__ void pencil_rows(const R* __restrict__ src, int is, R* __restrict__ dst,
+                                            int os) {
+  using T = TabOff<P>;
+  R x[COLS];
+#pragma unroll
+  for (int k = 0; k < COLS; ++k) x[k] = src[k * is];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    if constexpr (std::is_same<R, df>::value) {
+      // double-float dot product: the leading parts summed with TwoSum, the
+      // product errors, cross terms and sum errors gathered in one binary32
+      // term, one renormalisation per output
+      float s = 0.f, t = 0.f;
+      if (ACC) { s = dst[r * os].hi; t = dst[r * os].lo; }
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        int idx;
+        if (TAB == 0) idx = T::B + (TRANS ? k * T::N + r : r * T::N + k);
+        else idx = T::Dq + (TRANS ? k * T::Q + r : r * T::Q + k);
+        const float2 m = c_tabdf[P][idx];
+        const float p = __fmul_rn(m.x, x[k].hi);
+        float e = __fmaf_rn(m.x, x[k].hi, -p);
+        e = __fmaf_rn(m.x, x[k].lo, e);
+        e = __fmaf_rn(m.y, x[k].hi, e);
+        if (!ACC && k == 0) {
+          s = p;
+          t = e;
+        } else {
+          float s2, err;
+          two_sum(s, p, s2, err);
+          s = s2;
+          t = __fadd_rn(t, __fadd_rn(err, e));
+        }
+      }
+      dst[r * os] = fast_two_sum(s, t);
+    } else {
+      R acc = ACC ? dst[r * os] : R(0);
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        int idx;
+        if (TAB == 0) idx = T::B + (TRANS ? k * T::N + r : r * T::N + k);
+        else idx = T::Dq + (TRANS ? k * T::Q + r : r * T::Q + k);
+        acc = mad(ctab<P, R>(idx), x[k], acc);
+      }
+      dst[r * os] = acc;
+    }
+  }
+}
+
 // One thread per pencil: out = M in along direction DIR of a 3D array with
 // input extents (E0, E1, E2); M is the B table (TAB 0, ROWS x COLS = Q x N, or
 // its transpose) or the Dq table (TAB 1, Q x Q). CNT arrays (stride IN_ST in
@@ -103,55 +157,31 @@ __device__ __forceinline__ void pencil(const R* __restrict__ in, R* __restrict__
     if (DIR == 0) { ibase = IX * (ia + E1 * ib); obase = OXX * (ia + O1 * ib); }
     else if (DIR == 1) { ibase = ia + IX * E1 * ib; obase = ia + OXX * O1 * ib; }
     else { ibase = ia + IX * ib; obase = ia + OXX * ib; }
-    const R* src = in + c * IN_ST + ibase;
-    R* dst = out + c * OUT_ST + obase;
-    R x[COLS];
-#pragma unroll
-    for (int k = 0; k < COLS; ++k) x[k] = src[k * IS];
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-      if constexpr (std::is_same<R, df>::value) {
-        // double-float dot product: the leading parts summed with TwoSum, the
-        // product errors, cross terms and sum errors gathered in one binary32
-        // term, one renormalisation per output
-        float s = 0.f, t = 0.f;
-        if (ACC) { s = dst[r * OS].hi; t = dst[r * OS].lo; }
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) {
-          int idx;
-          if (TAB == 0) idx = T::B + (TRANS ? k * T::N + r : r * T::N + k);
-          else idx = T::Dq + (TRANS ? k * T::Q + r : r * T::Q + k);
-          const float2 m = c_tabdf[P][idx];
-          const float p = __fmul_rn(m.x, x[k].hi);
-          float e = __fmaf_rn(m.x, x[k].hi, -p);
-          e = __fmaf_rn(m.x, x[k].lo, e);
-          e = __fmaf_rn(m.y, x[k].hi, e);
-          if (!ACC && k == 0) {
-            s = p;
-            t = e;
-          } else {
-            float s2, err;
-            two_sum(s, p, s2, err);
-            s = s2;
-            t = __fadd_rn(t, __fadd_rn(err, e));
-          }
-        }
-        dst[r * OS] = fast_two_sum(s, t);
-      } else {
-        R acc = ACC ? dst[r * OS] : R(0);
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) {
-          int idx;
-          if (TAB == 0) idx = T::B + (TRANS ? k * T::N + r : r * T::N + k);
-          else idx = T::Dq + (TRANS ? k * T::Q + r : r * T::Q + k);
-          acc = mad(ctab<P, R>(idx), x[k], acc);
-        }
-        dst[r * OS] = acc;
-      }
-    }
+    pencil_rows<P, TAB, TRANS, ACC, COLS, ROWS, R>(in + c * IN_ST + ibase, IS,
+                                                    out + c * OUT_ST + obase, OS);
     c += dc;
     pp += dp;
     if (pp >= NP) { pp -= NP; ++c; }
+  }
+}
+
+// The three reference derivatives at the Q^3 points in one pass: for each of
+// CNT arrays (stride ST) of point values V, the arrays V + d Q^3 (d = 1, 2, 3)
+// receive Dq V along x, y and z. Work items run over (direction, array,
+// pencil), so the three directions share the passes of the block's threads.
+template <int P, int CNT, int ST, class R>
+__device__ __forceinline__ void pencil_grad3(R* V, int tid, int NT) {
+  constexpr int Q = P + 2, NQ = Q * Q * Q, NP = Q * Q, PER = NP * CNT;
+#pragma unroll 1
+  for (int w = tid; w < 3 * PER; w += NT) {
+    const int d = w / PER, r = w - d * PER;
+    const int c = r / NP, pp = r - c * NP;
+    const int ia = pp % Q, ib = pp / Q;
+    // pencil along d: the other two coordinates are (ia, ib) in increasing order
+    const int is = d == 0 ? 1 : (d == 1 ? Q : Q * Q);
+    const int base = d == 0 ? Q * (ia + Q * ib) : (d == 1 ? ia + Q * Q * ib : ia + Q * ib);
+    const R* src = V + c * ST + base;
+    pencil_rows<P, 1, false, false, Q, Q, R>(src, is, V + c * ST + (1 + d) * NQ + base, is);
   }
 }
 
@@ -347,9 +377,7 @@ op3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __
   __syncthreads();
   pencil<P, Q, Q, N, 2, 0, false, false, NA, Q * Q * N, 4 * NQ>(T2, PT, tid, NT);
   __syncthreads();
-  pencil<P, Q, Q, Q, 0, 1, false, false, NA, 4 * NQ, 4 * NQ>(PT, PT + NQ, tid, NT);
-  pencil<P, Q, Q, Q, 1, 1, false, false, NA, 4 * NQ, 4 * NQ>(PT, PT + 2 * NQ, tid, NT);
-  pencil<P, Q, Q, Q, 2, 1, false, false, NA, 4 * NQ, 4 * NQ>(PT, PT + 3 * NQ, tid, NT);
+  pencil_grad3<P, NA, 4 * NQ>(PT, tid, NT);
   __syncthreads();
 
   {
@@ -710,11 +738,14 @@ op3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __
 
 // ---------------------------------------------------------------------------
 // Face kernel of R, J v and J^T w: each face of the mesh once, for both of its
-// sides. Threads per face: Q x Q for FP64, 64 for FP32 (p >= 2).
+// sides. Threads per face: Q x Q for FP64; for FP32 and double-float the
+// fewest threads that cover the Q x Q face points in about one pass of the
+// pointwise fluxes (16, 16, 32 and 48 at p = 1..4), so that the costliest
+// stage keeps its lanes busy; faces per block make up the block.
 template <int P, class R>
 __host__ __device__ constexpr int tpf3d() {
   if constexpr (std::is_same<R, double>::value) return (P + 2) * (P + 2);
-  else return P <= 1 ? 32 : 64;
+  else return P <= 2 ? 16 : (P == 3 ? 32 : 48);
 }
 
 template <int P, int NF, int MODE, int NT>
@@ -725,103 +756,58 @@ struct SmemF {
   static constexpr int NNP = NX * N * N, FNP = NX * N;
   static constexpr int NV = MODE == kResidual ? 1 : 2;
   static constexpr int NA = NV * NF;
+  // Two regions, reused stage by stage: A holds both elements' data X, then
+  // (once FL is formed) the interpolation F1 and the traces TR, then (once the
+  // fluxes are formed) the transposed contractions G1 and G2; B holds FL, then
+  // (once F1 is formed) the face coefficients FC.
   static constexpr int kX = 2 * NA * NNP;              // both elements' data
   static constexpr int kF1 = 2 * NA * 2 * Q * N;       // after the first face contraction
   static constexpr int kTR = 2 * NA * 2 * FQ;          // traces at the face points
-  static constexpr int kA = kX > kF1 + kTR ? kX : kF1 + kTR;  // X is dead once FL is formed
-  static constexpr int kFL = 2 * NA * 2 * FNP;         // layer values + normal derivatives
-  static constexpr int kFC = 2 * 2 * NF * FQ;          // [side][S, T][NF] at face points
   static constexpr int kG1 = 2 * 2 * NF * Q * N;
   static constexpr int kG2 = 2 * 2 * NF * FNP;
-  static constexpr int raw = kA + kFL + kFC + kG1 + kG2;
+  static constexpr int kA0 = kX > kF1 + kTR ? kX : kF1 + kTR;
+  static constexpr int kA = kA0 > kG1 + kG2 ? kA0 : kG1 + kG2;
+  static constexpr int kFL = 2 * NA * 2 * FNP;         // layer values + normal derivatives
+  static constexpr int kFC = 2 * 2 * NF * FQ;          // [side][S, T][NF] at face points
+  static constexpr int kB = kFL > kFC ? kFL : kFC;
+  static constexpr int raw = kA + kB;
   static constexpr int total = raw + ((NT - raw % 32) % 32 + 32) % 32;
 };
 
-// pa < 0: every face of the mesh; pa >= 0: only the faces of plane pia of
-// direction pa (the upstream coupling of one plane in a block Gauss-Seidel
-// sweep), written to the same places of the face buffer.
-template <int P, int NF, int MODE, class R>
-__global__ void __launch_bounds__(kMaxThreads3D, MinBlocks3D<R>::value)
-face3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __restrict__ v,
-              int pa, int pia) {
-  constexpr int NT = tpf3d<P, R>();
-  using S = SmemF<P, NF, MODE, NT>;
+// The stages of one face after both elements' data are in XS (the first
+// region of `base`): layer values and normal derivatives, the 2D interpolation
+// to the face points, the pointwise fluxes, and the transposed 2D contraction
+// back to the face nodes. On return (after a barrier) the lifted coefficients
+// of both sides are at face3d_g2(base): [side][S, T][NF][FNP]. All threads of
+// the block take part in every barrier.
+template <int P, int NF, int MODE, class R, int NTS>
+__device__ __forceinline__ R* face3d_g2(R* base) {
+  using S = SmemF<P, NF, MODE, NTS>;
+  return base + S::kG1;
+}
+template <int P, int NF, int MODE, class R, int NTS>
+__device__ __forceinline__ void face3d_stages(const OpParams& prm, R* base, int tid, int NT, int a,
+                                              int ia, int j0, int j1, int bidx) {
+  using S = SmemF<P, NF, MODE, NTS>;
   using TO = TabOff<P>;
-  constexpr int N = S::N, Q = S::Q, NN = S::NN, FN = S::FN, FQ = S::FQ;
+  constexpr int N = S::N, Q = S::Q, FN = S::FN, FQ = S::FQ;
   constexpr int NX = S::NX, NNP = S::NNP, FNP = S::FNP, NA = S::NA;
   const PhysT<R>& ph = phys<R>(prm);
-  extern __shared__ __align__(16) unsigned char smemf_raw[];
-  const int fs = threadIdx.x / NT, tid = threadIdx.x % NT;
-  R* base = reinterpret_cast<R*>(smemf_raw) + fs * S::total;
   R* XS = base;                  // [2][NA][NNP]
   R* F1 = base;                  // [2][NA][2][Q][N] (over XS, once FL is formed)
   R* TR = F1 + S::kF1;           // [2][NA][2][FQ]
-  R* FL = base + S::kA;          // [2][NA][2][FNP]
-  R* FC = FL + S::kFL;           // [2][2][NF][FQ]
-  R* G1 = FC + S::kFC;           // [2][2][NF][N][Q]
+  R* G1 = base;                  // [2][2][NF][N][Q] (over F1 and TR, once FC is formed)
   R* G2 = G1 + S::kG1;           // [2][2][NF][FNP]
-  const int FPB = blockDim.x / NT;
-  const bool plane = pa >= 0;
-  const long long nf = plane ? (long long)prm.ne[pa == 0 ? 1 : 0] * prm.ne[pa == 2 ? 1 : 2]
-                             : prm.foff[3];
-  const long long graw = (long long)blockIdx.x * FPB + fs;
-  const bool valid = graw < nf;
-  const long long g = valid ? graw : nf - 1;     // idle slots shadow a face, write nothing
-  const int bidx = blockIdx.y;
-  const long long boff = (long long)bidx * prm.batch_stride;
-  const long long EN = (long long)prm.E * NN;
-
-  int a, ia, j0, j1;
-  if (plane) {
-    a = pa;
-    ia = pia;
-    const int nb0 = prm.ne[a == 0 ? 1 : 0];
-    j0 = (int)(g % nb0);
-    j1 = (int)(g / nb0);
-  } else {
-    a = (g >= prm.foff[1]) + (g >= prm.foff[2]);
-    const long long fi = g - prm.foff[a];
-    const int na0 = prm.ne[a] + 1;
-    ia = (int)(fi % na0);
-    const long long rr = fi / na0;
-    const int nb0 = prm.ne[a == 0 ? 1 : 0];
-    j0 = (int)(rr % nb0);
-    j1 = (int)(rr / nb0);
-  }
+  R* FL = base + S::kA;          // [2][NA][2][FNP]
+  R* FC = FL;                    // [2][2][NF][FQ] (over FL, once F1 is formed)
   const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
-  const long long gid = prm.foff[a] + ia + (long long)(prm.ne[a] + 1) * (j0 + (long long)prm.ne[b0] * j1);
   const bool hasL = ia > 0, hasU = ia < prm.ne[a];
-  const int stride[3] = {1, prm.ne[0], prm.ne[0] * prm.ne[1]};
-  const int sa = pick3(stride, a);
-  const int eU = ia * sa + j0 * pick3(stride, b0) + j1 * pick3(stride, b1);  // valid when hasU
-  const int eL = eU - sa;                                                   // valid when hasL
   const R lo0 = vertex<R>(prm, b0, j0), lo1 = vertex<R>(prm, b1, j1);
   const R h0 = vertex<R>(prm, b0, j0 + 1) - lo0, h1 = vertex<R>(prm, b1, j1 + 1) - lo1;
   const R xa = vertex<R>(prm, a, ia);
   const R hL = hasL ? xa - vertex<R>(prm, a, ia - 1) : R(1);
   const R hU = hasU ? vertex<R>(prm, a, ia + 1) - xa : R(1);
   const R diagL = sqrtv(hL * hL + h0 * h0 + h1 * h1), diagU = sqrtv(hU * hU + h0 * h0 + h1 * h1);
-
-  // both elements' data (a missing side is zero and never read); node-outer, so
-  // the padded offset is formed once per node
-  {
-    const long long gL = boff + (long long)(hasL ? eL : 0) * NN;
-    const long long gU = boff + (long long)(hasU ? eU : 0) * NN;
-    for (int i = tid; i < NN; i += NT) {
-      const int pi = padded_node<N>(i);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const long long o = f * EN + i;
-        XS[f * NNP + pi] = hasL ? R(u[gL + o]) : R(0);
-        XS[(NA + f) * NNP + pi] = hasU ? R(u[gU + o]) : R(0);
-        if (NA > NF) {
-          XS[(NF + f) * NNP + pi] = hasL ? R(v[gL + o]) : R(0);
-          XS[(NA + NF + f) * NNP + pi] = hasU ? R(v[gU + o]) : R(0);
-        }
-      }
-    }
-  }
-  __syncthreads();
   // face-layer values and reference normal derivatives: the lower element at
   // its upper face (layer N-1, derivative at xi = +1), the upper element at its
   // lower face (layer 0, derivative at xi = -1)
@@ -1002,6 +988,65 @@ face3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* 
   __syncthreads();
   pencil<P, Q, N, 1, 0, 0, true, false, 4 * NF, Q * N, FNP, R, Q, NX>(G1, G2, tid, NT);
   __syncthreads();
+}
+
+template <int P, int NF, int MODE, class R>
+__global__ void __launch_bounds__(kMaxThreads3D, MinBlocks3D<R>::value)
+face3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __restrict__ v) {
+  constexpr int NT = tpf3d<P, R>();
+  using S = SmemF<P, NF, MODE, NT>;
+  constexpr int N = S::N, NN = S::NN, FN = S::FN;
+  constexpr int NX = S::NX, NNP = S::NNP, FNP = S::FNP, NA = S::NA;
+  extern __shared__ __align__(16) unsigned char smemf_raw[];
+  const int fs = threadIdx.x / NT, tid = threadIdx.x % NT;
+  R* base = reinterpret_cast<R*>(smemf_raw) + fs * S::total;
+  R* XS = base;                  // [2][NA][NNP]
+  const int FPB = blockDim.x / NT;
+  const long long nf = prm.foff[3];
+  const long long graw = (long long)blockIdx.x * FPB + fs;
+  const bool valid = graw < nf;
+  const long long g = valid ? graw : nf - 1;     // idle slots shadow a face, write nothing
+  const int bidx = blockIdx.y;
+  const long long boff = (long long)bidx * prm.batch_stride;
+  const long long EN = (long long)prm.E * NN;
+
+  const int a = (g >= prm.foff[1]) + (g >= prm.foff[2]);
+  const long long fi = g - prm.foff[a];
+  const int na0 = prm.ne[a] + 1;
+  const int ia = (int)(fi % na0);
+  const long long rr = fi / na0;
+  const int nb0 = prm.ne[a == 0 ? 1 : 0];
+  const int j0 = (int)(rr % nb0), j1 = (int)(rr / nb0);
+  const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+  const long long gid = prm.foff[a] + ia + (long long)(prm.ne[a] + 1) * (j0 + (long long)prm.ne[b0] * j1);
+  const bool hasL = ia > 0, hasU = ia < prm.ne[a];
+  const int stride[3] = {1, prm.ne[0], prm.ne[0] * prm.ne[1]};
+  const int sa = pick3(stride, a);
+  const int eU = ia * sa + j0 * pick3(stride, b0) + j1 * pick3(stride, b1);  // valid when hasU
+  const int eL = eU - sa;                                                   // valid when hasL
+
+  // both elements' data (a missing side is zero and never read); node-outer, so
+  // the padded offset is formed once per node
+  {
+    const long long gL = boff + (long long)(hasL ? eL : 0) * NN;
+    const long long gU = boff + (long long)(hasU ? eU : 0) * NN;
+    for (int i = tid; i < NN; i += NT) {
+      const int pi = padded_node<N>(i);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const long long o = f * EN + i;
+        XS[f * NNP + pi] = hasL ? R(u[gL + o]) : R(0);
+        XS[(NA + f) * NNP + pi] = hasU ? R(u[gU + o]) : R(0);
+        if (NA > NF) {
+          XS[(NF + f) * NNP + pi] = hasL ? R(v[gL + o]) : R(0);
+          XS[(NA + NF + f) * NNP + pi] = hasU ? R(v[gU + o]) : R(0);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  face3d_stages<P, NF, MODE, R, NT>(prm, base, tid, NT, a, ia, j0, j1, bidx);
+  const R* G2 = face3d_g2<P, NF, MODE, R, NT>(base);
   if (valid) {
     R* fb = reinterpret_cast<R*>(prm.fbuf) + (long long)bidx * prm.fbuf_stride +
             gid * 2 * 2 * NF * FN;

@@ -877,8 +877,10 @@ gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
   constexpr int NR = NW * RPW;   // padded rows
   constexpr int NC = 32 * CPL;   // padded columns
   extern __shared__ __align__(16) unsigned char gsm[];
-  float* stage = reinterpret_cast<float*>(gsm);        // [n][n] transposed inverse
-  __shared__ float colv[2][NR], cola[2][NR];
+  float* stage = reinterpret_cast<float*>(gsm);        // [n][n + 1] transposed inverse
+  __shared__ float colv[2][NR];                        // the pivot column, double-buffered
+  __shared__ float candv[2][32];                       // per warp: largest |M_ik| over its unused rows
+  __shared__ int candi[2][32];                         //           and that row
   __shared__ float rowv[NC];
   __shared__ int piv[NC], stepof[NR];
   __shared__ float s_wmax[NW];
@@ -902,15 +904,30 @@ gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, o));
   if (lane == 0) s_wmax[w] = amax;
   unsigned used = 0u;  // bit r: row w + NW r already a pivot row (same in every lane)
-  // column 0, published by lane 0 of every warp
-  if (lane == 0) {
+  // publish column kc (from lane kc % 32 of every warp): its values for the
+  // update, and the warp's pivot candidate among its unused rows
+  auto publish = [&](int kc, int buf) {
+    if (lane == (kc & 31)) {
+      const int cc = kc >> 5;
+      float best = -1.f;
+      int bi = 0;
 #pragma unroll
-    for (int r = 0; r < RPW; ++r) {
-      const int i = w + NW * r;
-      colv[0][i] = M[r][0];
-      cola[0][i] = i < n ? fabsf(M[r][0]) : -1.f;
+      for (int c = 0; c < CPL; ++c)
+        if (c == cc) {
+#pragma unroll
+          for (int r = 0; r < RPW; ++r) {
+            const int i = w + NW * r;
+            const float v = M[r][c];
+            colv[buf][i] = v;
+            const float av = (i < n && !((used >> r) & 1u)) ? fabsf(v) : -1.f;
+            if (av > best) { best = av; bi = i; }   // rows ascend with r: ties keep the lower
+          }
+        }
+      candv[buf][w] = best;
+      candi[buf][w] = bi;
     }
-  }
+  };
+  publish(0, 0);
   __syncthreads();
   float thr = 0.f;
   if (piv_rtol > 0.f) {
@@ -921,13 +938,9 @@ gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
   bool bad = false;
   for (int k = 0; k < n; ++k) {
     const int buf = k & 1;
-    // the pivot row: argmax of |M_ik| over unused rows, ties to the lower row
-    float best = -1.f;
-    int bi = 0;
-    for (int t = lane; t < n; t += 32) {
-      const float v = cola[buf][t];
-      if (v > best) { best = v; bi = t; }
-    }
+    // the pivot row: the best of the warps' candidates, ties to the lower row
+    float best = lane < NW ? candv[buf][lane] : -1.f;
+    int bi = lane < NW ? candi[buf][lane] : 0x7fffffff;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -936,17 +949,17 @@ gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
     }
     if (!(best > thr) || !isfinite(best)) { bad = true; break; }  // the same in every thread
     const int p = bi;
-    const float pinv = 1.f / colv[buf][p];
-    if (w == p % NW) {
-      const int rp = p / NW;
+    const float pinv = __frcp_rn(colv[buf][p]);
+    const int wp = p % NW, rp = p / NW;
+    // the pivot row, from the warp that owns it
+    if (w == wp) {
       used |= 1u << rp;
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        float v = 0.f;
+      for (int r = 0; r < RPW; ++r)
+        if (r == rp) {
 #pragma unroll
-        for (int r = 0; r < RPW; ++r) v = r == rp ? M[r][c] : v;
-        rowv[lane + 32 * c] = v;
-      }
+          for (int c = 0; c < CPL; ++c) rowv[lane + 32 * c] = M[r][c];
+        }
     }
     if (tid == 0) { piv[k] = p; stepof[p] = k; }
     __syncthreads();
@@ -956,39 +969,43 @@ gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
       const int j = lane + 32 * c;
       rj[c] = (j == k ? 1.f : rowv[j]) * pinv;
     }
+    // column k becomes -M_ik / M_pk: cleared here, the update below fills it
+    if (lane == (k & 31)) {
+      const int ck = k >> 5;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c)
+        if (c == ck) {
+#pragma unroll
+          for (int r = 0; r < RPW; ++r) M[r][c] = 0.f;
+        }
+    }
+    // M_ij -= M_ik M_pj / M_pk off the pivot row
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
       const int i = w + NW * r;
-      const float ci = colv[buf][i];
-      const bool isp = i == p;
+      const float ci = i == p ? 0.f : colv[buf][i];
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const int j = lane + 32 * c;
-        const float m = j == k ? 0.f : M[r][c];
-        M[r][c] = isp ? rj[c] : fmaf(-ci, rj[c], m);
-      }
+      for (int c = 0; c < CPL; ++c) M[r][c] = fmaf(-ci, rj[c], M[r][c]);
     }
-    // publish column k + 1 (its updated values) for the next step
-    const int kn = k + 1;
-    if (kn < n && lane == (kn & 31)) {
-      const int cn = kn >> 5;
+    // the pivot row becomes M_pj / M_pk, and 1 / M_pk at k
+    if (w == wp) {
 #pragma unroll
-      for (int r = 0; r < RPW; ++r) {
-        float v = 0.f;
+      for (int r = 0; r < RPW; ++r)
+        if (r == rp) {
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) v = c == cn ? M[r][c] : v;
-        const int i = w + NW * r;
-        colv[buf ^ 1][i] = v;
-        cola[buf ^ 1][i] = (i < n && !((used >> r) & 1u)) ? fabsf(v) : -1.f;
-      }
+          for (int c = 0; c < CPL; ++c) M[r][c] = rj[c];
+        }
     }
+    if (k + 1 < n) publish(k + 1, buf ^ 1);
     __syncthreads();
   }
   if (bad) {
     if (tid == 0) atomicOr(singular, 1);
     return;
   }
-  // inv[step(i)][p_j] = M_ij; out[c][r] = inv[r][c]: stage[p_j][step(i)]
+  // inv[step(i)][p_j] = M_ij; out[c][r] = inv[r][c]: stage[p_j][step(i)], rows
+  // padded to n + 1 so that a warp's scattered rows p_j fall in different banks
+  const int ld = n + 1;
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     const int i = w + NW * r;
@@ -997,12 +1014,13 @@ gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
       const int j = lane + 32 * c;
-      if (j < n) stage[piv[j] * n + si] = M[r][c];
+      if (j < n) stage[piv[j] * ld + si] = M[r][c];
     }
   }
   __syncthreads();
   TS* o = out + e * (long long)n * n;
-  for (int t = tid; t < n * n; t += NW * 32) o[t] = (TS)stage[t];
+  for (int row = w; row < n; row += NW)
+    for (int col = lane; col < n; col += 32) o[(long long)row * n + col] = (TS)stage[row * ld + col];
 }
 
 // The same register-resident Gauss-Jordan for blocks of up to 256 x 256, whose
@@ -1029,14 +1047,18 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
   const int rank = (int)cluster.block_rank(), peer = rank ^ 1;
   extern __shared__ __align__(16) unsigned char gcs[];
   float* stage = reinterpret_cast<float*>(gcs);   // [(n + 1) / 2][n]: out rows c with c % 2 == rank
-  __shared__ float colv[2][kGjcRows], cola[2][kGjcRows];
+  __shared__ float colv[2][kGjcRows];
+  __shared__ float candv[2][kGjcNW];   // per warp: largest |M_ik| over its unused rows
+  __shared__ int candi[2][kGjcNW];     //           and that (global) row
   __shared__ float rowv[kGjcCols];
   __shared__ int piv[kGjcCols], stepof[2 * kGjcRows];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long long e = blockIdx.x / 2;
   const float* src = blocks + e * (long long)n * n;
-  float* colv_p[2] = {cluster.map_shared_rank(&colv[0][0], peer), cluster.map_shared_rank(&colv[1][0], peer)};
-  float* cola_p[2] = {cluster.map_shared_rank(&cola[0][0], peer), cluster.map_shared_rank(&cola[1][0], peer)};
+  // the peer's copies ([2][...] arrays, row-major as here)
+  const float* colv_p = cluster.map_shared_rank(&colv[0][0], peer);
+  const float* candv_p = cluster.map_shared_rank(&candv[0][0], peer);
+  const int* candi_p = cluster.map_shared_rank(&candi[0][0], peer);
   float* rowv_p = cluster.map_shared_rank(&rowv[0], peer);
   float* stage_p = cluster.map_shared_rank(stage, peer);
   float M[kGjcRPW][kGjcCPL];
@@ -1051,27 +1073,39 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
     }
   }
   unsigned used = 0u;
-  if (lane == 0) {
+  // publish column kc (from lane kc % 32 of every warp): its values, and the
+  // warp's pivot candidate among its unused rows
+  auto publish = [&](int kc, int buf) {
+    if (lane == (kc & 31)) {
+      const int cc = kc >> 5;
+      float best = -1.f;
+      int bi = 0;
 #pragma unroll
-    for (int r = 0; r < kGjcRPW; ++r) {
-      const int li = w + kGjcNW * r, i = 2 * li + rank;
-      colv[0][li] = M[r][0];
-      cola[0][li] = i < n ? fabsf(M[r][0]) : -1.f;
+      for (int c = 0; c < kGjcCPL; ++c)
+        if (c == cc) {
+#pragma unroll
+          for (int r = 0; r < kGjcRPW; ++r) {
+            const int li = w + kGjcNW * r, i = 2 * li + rank;
+            const float v = M[r][c];
+            colv[buf][li] = v;
+            const float av = (i < n && !((used >> r) & 1u)) ? fabsf(v) : -1.f;
+            if (av > best) { best = av; bi = i; }   // rows ascend with r: ties keep the lower
+          }
+        }
+      candv[buf][w] = best;
+      candi[buf][w] = bi;
     }
-  }
+  };
+  publish(0, 0);
   cluster.sync();
   bool bad = false;
   for (int k = 0; k < n; ++k) {
     const int buf = k & 1;
-    // pivot: the largest |M_ik| over unused rows of both CTAs, ties to the lower row
-    float best = -1.f;
-    int bi = 0;
-    for (int li = lane; li < kGjcRows; li += 32) {
-      const float v0 = rank == 0 ? cola[buf][li] : cola_p[buf][li];   // row 2 li
-      const float v1 = rank == 1 ? cola[buf][li] : cola_p[buf][li];   // row 2 li + 1
-      if (v0 > best) { best = v0; bi = 2 * li; }
-      if (v1 > best) { best = v1; bi = 2 * li + 1; }
-    }
+    // pivot: the best of both CTAs' warp candidates, ties to the lower row
+    const int q = lane & (kGjcNW - 1);
+    const bool mine = (lane < kGjcNW) == (rank == 0);   // lanes < 16: CTA 0's warps
+    float best = mine ? candv[buf][q] : candv_p[buf * kGjcNW + q];
+    int bi = mine ? candi[buf][q] : candi_p[buf * kGjcNW + q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -1080,18 +1114,18 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
     }
     if (!(best > 0.f) || !isfinite(best)) { bad = true; break; }  // the same in both CTAs
     const int p = bi, owner = p & 1, lp = p >> 1;
-    const float pivv = owner == rank ? colv[buf][lp] : colv_p[buf][lp];
-    const float pinv = 1.f / pivv;
-    if (owner == rank && w == lp % kGjcNW) {
-      const int rp = lp / kGjcNW;
+    const float pivv = owner == rank ? colv[buf][lp] : colv_p[buf * kGjcRows + lp];
+    const float pinv = __frcp_rn(pivv);
+    const bool own = owner == rank && w == lp % kGjcNW;
+    const int rp = lp / kGjcNW;
+    if (own) {
       used |= 1u << rp;
 #pragma unroll
-      for (int c = 0; c < kGjcCPL; ++c) {
-        float v = 0.f;
+      for (int r = 0; r < kGjcRPW; ++r)
+        if (r == rp) {
 #pragma unroll
-        for (int r = 0; r < kGjcRPW; ++r) v = r == rp ? M[r][c] : v;
-        rowv[lane + 32 * c] = v;
-      }
+          for (int c = 0; c < kGjcCPL; ++c) rowv[lane + 32 * c] = M[r][c];
+        }
     }
     if (tid == 0) { piv[k] = p; stepof[p] = k; }
     cluster.sync();
@@ -1102,31 +1136,34 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
       const int j = lane + 32 * c;
       rj[c] = (j == k ? 1.f : rsrc[j]) * pinv;
     }
+    // column k becomes -M_ik / M_pk: cleared here, the update below fills it
+    if (lane == (k & 31)) {
+      const int ck = k >> 5;
+#pragma unroll
+      for (int c = 0; c < kGjcCPL; ++c)
+        if (c == ck) {
+#pragma unroll
+          for (int r = 0; r < kGjcRPW; ++r) M[r][c] = 0.f;
+        }
+    }
+    // M_ij -= M_ik M_pj / M_pk off the pivot row
 #pragma unroll
     for (int r = 0; r < kGjcRPW; ++r) {
       const int li = w + kGjcNW * r, i = 2 * li + rank;
-      const float ci = colv[buf][li];
-      const bool isp = i == p;
+      const float ci = i == p ? 0.f : colv[buf][li];
 #pragma unroll
-      for (int c = 0; c < kGjcCPL; ++c) {
-        const int j = lane + 32 * c;
-        const float m = j == k ? 0.f : M[r][c];
-        M[r][c] = isp ? rj[c] : fmaf(-ci, rj[c], m);
-      }
+      for (int c = 0; c < kGjcCPL; ++c) M[r][c] = fmaf(-ci, rj[c], M[r][c]);
     }
-    const int kn = k + 1;
-    if (kn < n && lane == (kn & 31)) {
-      const int cn = kn >> 5;
+    // the pivot row becomes M_pj / M_pk, and 1 / M_pk at k
+    if (own) {
 #pragma unroll
-      for (int r = 0; r < kGjcRPW; ++r) {
-        float v = 0.f;
+      for (int r = 0; r < kGjcRPW; ++r)
+        if (r == rp) {
 #pragma unroll
-        for (int c = 0; c < kGjcCPL; ++c) v = c == cn ? M[r][c] : v;
-        const int li = w + kGjcNW * r, i = 2 * li + rank;
-        colv[buf ^ 1][li] = v;
-        cola[buf ^ 1][li] = (i < n && !((used >> r) & 1u)) ? fabsf(v) : -1.f;
-      }
+          for (int c = 0; c < kGjcCPL; ++c) M[r][c] = rj[c];
+        }
     }
+    if (k + 1 < n) publish(k + 1, buf ^ 1);
     cluster.sync();
   }
   if (bad) {
@@ -1156,72 +1193,6 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
   for (int t = tid; t < nrow * n; t += kGjcNW * 32) {
     const int q = t / n, r = t % n;
     o[(long long)(2 * q + rank) * n + r] = (TS)stage[q * n + r];
-  }
-}
-
-// One plane of the downwind block Gauss-Seidel sweep: the elements whose
-// coordinate along axis a is k, one per thread block. t = x_e minus the
-// upstream face terms J_(e,up) z_up that the face kernel left in the face buffer
-// (this element's side `side` of face plane `ia`: side 1 = its lower face, lifted
-// with dL(-1) onto node layer 0; side 0 = its upper face, dL(+1), layer N-1),
-// then z_e = Binv_e t. With upstream = 0 (the first plane) t = x_e.
-template <class TS, class TA, class TV>
-__global__ void sweep_plane_kernel(const TS* __restrict__ BT, const TV* __restrict__ x,
-                                   TV* __restrict__ z, int n, int NF, int N, long long EN,
-                                   long long bstride, int a, int k, int ne0, int ne1, int ne2,
-                                   int upstream, const TV* __restrict__ fb, long long fb_stride,
-                                   long long foff_a, int ia, int side,
-                                   const double* __restrict__ dL, int shared_blocks) {
-  extern __shared__ __align__(16) unsigned char ssm_raw[];
-  TA* ts = reinterpret_cast<TA*>(ssm_raw);
-  const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
-  const int nb0 = a == 0 ? ne1 : ne0;
-  const int j0 = (int)(blockIdx.x % nb0), j1 = (int)(blockIdx.x / nb0);
-  const int stride[3] = {1, ne0, ne0 * ne1};
-  const int sa = a == 0 ? stride[0] : (a == 1 ? stride[1] : stride[2]);
-  const int sb0 = b0 == 0 ? stride[0] : stride[1];
-  const int sb1 = b1 == 1 ? stride[1] : stride[2];
-  const long long e = (long long)k * sa + (long long)j0 * sb0 + (long long)j1 * sb1;
-  const int b = blockIdx.y;
-  const int Np = N * N * N, FN = N * N;
-  const long long E = EN / Np;
-  const TV* xb = x + b * bstride;
-  const long long gid = foff_a + ia + (long long)((a == 0 ? ne0 : (a == 1 ? ne1 : ne2)) + 1) *
-                                          (j0 + (long long)(b0 == 0 ? ne0 : ne1) * j1);
-  const TV* fs = fb + b * fb_stride + (gid * 2 + side) * 2 * NF * FN;
-  const int lay = side == 1 ? 0 : N - 1;
-  const double* dl = dL + (side == 1 ? 0 : N);
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    const int f = c / Np, i = c % Np;
-    TA t = (TA)xb[f * EN + e * Np + i];
-    if (upstream) {
-      const int c3[3] = {i % N, (i / N) % N, i / (N * N)};
-      const int ka = a == 0 ? c3[0] : (a == 1 ? c3[1] : c3[2]);
-      const int j = a == 0 ? c3[1] + N * c3[2] : (a == 1 ? c3[0] + N * c3[2] : c3[0] + N * c3[1]);
-      const TA sv = (TA)fs[(0 * NF + f) * FN + j];
-      const TA tv = (TA)fs[(1 * NF + f) * FN + j];
-      TA add = (TA)dl[ka] * tv;
-      if (ka == lay) add += sv;
-      t -= add;
-    }
-    ts[c] = t;
-  }
-  __syncthreads();
-  const TS* B = BT + ((long long)(shared_blocks ? 0 : b) * E + e) * (long long)n * n;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    TA acc[8] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
-    int c = 0;
-    for (; c + 8 <= n; c += 8) {
-      TS bv[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) bv[q] = B[(long long)(c + q) * n + r];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] += (TA)bv[q] * ts[c + q];
-    }
-    for (; c < n; ++c) acc[0] += (TA)B[(long long)c * n + r] * ts[c];
-    const TA sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-    const int f = r / Np, i = r % Np;
-    z[b * bstride + f * EN + e * Np + i] = (TV)sum;
   }
 }
 
@@ -1437,7 +1408,7 @@ struct SolverState {
   // only with the preconditioner it was captured with
   unsigned long long pc_gen = 1, gkey_gen = 0;
   // two-level preconditioner: element-mean potential correction
-  bool sweep = false;             // downwind block Gauss-Seidel (enp_set_sweep)
+  int sweep_mode = 2;             // downwind block Gauss-Seidel: 0 off, 1 on, 2 automatic
   bool potential_only = false;    // the potential rows alone (enp_initial_guess)
   int pc_shared = -1;             // >= 0: one set of block inverses, of this operating
                                   // point, for the whole batch (enp_set_shared_blocks)
@@ -1816,6 +1787,35 @@ void enp_solver_free(enp_handle h) {
   h->solver = nullptr;
 }
 
+// Elements along the flow axis from which the automatic mode uses the sweep:
+// on the plate reactor (Pe = 1e4) block-Jacobi is faster at 96 elements along
+// the flow and the sweep 1.5x faster at 192 (one FP32 linear solve).
+constexpr int kSweepAutoElements = 128;
+
+// Whether the next setup builds the sweep, and along which axis and direction:
+// the plate-flow axis in the sign of its mean speed, or the largest component
+// of a constant velocity.
+static bool sweep_wanted(enp_handle h) {
+  SolverState& S = state_of(h);
+  const auto& pd = h->prm.pd;
+  double speed;
+  if (pd.vel_kind == 1) {
+    S.sweep_axis = pd.velA;
+    S.sweep_dir = pd.vp[4] < 0.0 ? -1 : 1;
+    speed = std::fabs(pd.vp[4]);
+  } else {
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+      if (std::fabs(pd.vp[d]) > std::fabs(pd.vp[ax])) ax = d;
+    S.sweep_axis = ax;
+    S.sweep_dir = pd.vp[ax] < 0.0 ? -1 : 1;
+    speed = std::fabs(pd.vp[ax]);
+  }
+  if (h->prm.dim != 3 || S.sweep_mode == 0) return false;
+  if (S.sweep_mode == 1) return true;
+  return speed > 0.0 && h->prm.ne[S.sweep_axis] >= kSweepAutoElements;
+}
+
 extern "C" {
 
 enp_status enp_recover_cm(enp_handle h, const double* u, double* cm) {
@@ -1958,7 +1958,7 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
 #define ENP_GJR(TS, NW, RPW, CPL)                                                                 \
   {                                                                                               \
     auto k = enp::gj_invert_regs<float, TS, NW, RPW, CPL>;                                        \
-    const size_t sm = sizeof(float) * (size_t)nb * nb;                                            \
+    const size_t sm = sizeof(float) * (size_t)nb * (nb + 1);                                      \
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);            \
     if (e == cudaSuccess) {                                                                       \
       k<<<(unsigned)nblk, NW * 32, sm, h->stream>>>(S.blocks32, (TS*)out, nb, S.d_flag, 0.f);     \
@@ -2017,7 +2017,7 @@ enp_status enp_block_jacobi_setup(enp_handle h, const double* u, int storage) {
     if ((e = coarse_setup(h, u)) != cudaSuccess) return cuda_err(h, e, "coarse setup");
   }
   S.sweep_ready = false;
-  if (S.sweep) {
+  if (sweep_wanted(h)) {
     // the sweep's upstream couplings are J v face terms at this u: keep a copy
     const long long ntot = h->n_dof * h->batch;
     if ((e = ensure(&S.upc64, S.upc64_count, (size_t)ntot)) != cudaSuccess ||
@@ -2046,7 +2046,7 @@ static cudaError_t sweep_apply(enp_handle h, const TV* x, TV* z);
 template <class TV>
 static cudaError_t bj_apply_any(enp_handle h, const TV* x, TV* y) {
   SolverState& S = state_of(h);
-  cudaError_t e = (S.sweep && S.sweep_ready) ? sweep_apply<TV>(h, x, y) : bj_apply_plain<TV>(h, x, y);
+  cudaError_t e = S.sweep_ready ? sweep_apply<TV>(h, x, y) : bj_apply_plain<TV>(h, x, y);
   if (e == cudaSuccess && S.coarse && S.coarse_ready) e = coarse_apply<TV>(h, x, y);
   return e;
 }
@@ -2077,45 +2077,25 @@ static cudaError_t bj_apply_plain(enp_handle h, const TV* x, TV* y) {
 
 // Downwind block Gauss-Seidel: z = (D + L)^-1 x with D the element blocks and L
 // the couplings of each element to its upstream neighbour along the flow axis;
-// the element planes are solved in flow order, each after its upstream face
-// terms (J v of the planes already solved, restricted to the faces in between).
+// the element planes are solved in flow order, one launch per plane, each
+// element evaluating its upstream face term from the plane solved before.
 template <class TV>
 static cudaError_t sweep_apply(enp_handle h, const TV* x, TV* z) {
   SolverState& S = state_of(h);
   const OpParams& P = h->prm;
   const int B = h->batch;
-  const int nb = S.nb;
-  const long long EN = (long long)P.E * P.Np;
   const long long ntot = h->n_dof * B;
   cudaError_t e = cudaMemsetAsync(z, 0, sizeof(TV) * ntot, h->stream);
   if (e != cudaSuccess) return e;
   const int a = S.sweep_axis, dir = S.sweep_dir;
-  const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
-  const int nplane = P.ne[b0] * P.ne[b1];
   const int nk = P.ne[a];
   const TV* upc = std::is_same<TV, double>::value ? reinterpret_cast<const TV*>(S.upc64)
                                                   : reinterpret_cast<const TV*>(S.upc32);
-  const double* dL = reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->d_tab) +
-                                                     offsetof(enp::Tables, dL));
-  const TV* fb = reinterpret_cast<const TV*>(P.fbuf);
-  const int threads = std::min(256, ((nb + 31) / 32) * 32);
   for (int step = 0; step < nk; ++step) {
     const int k = dir > 0 ? step : nk - 1 - step;
-    const int up = step > 0 ? 1 : 0;
-    const int ia = dir > 0 ? k : k + 1;      // the face plane between k and its upstream plane
-    const int side = dir > 0 ? 1 : 0;        // this plane's side of it
-    if (up && (e = enp::launch_face_plane<TV>(P, upc, z, B, h->stream, a, ia)) != cudaSuccess)
+    if ((e = enp::launch_sweep_plane<TV>(P, S.binv, S.storage, x, z, upc, B, h->stream, a, k, dir,
+                                         step > 0 ? 1 : 0, S.pc_shared_built)) != cudaSuccess)
       return e;
-    const dim3 g(nplane, B);
-#define ENP_SWEEP(TS, TA)                                                                          \
-  enp::sweep_plane_kernel<TS, TA, TV><<<g, threads, sizeof(TA) * nb, h->stream>>>(                 \
-      reinterpret_cast<const TS*>(S.binv), x, z, nb, P.NF, P.n, EN, P.batch_stride, a, k,          \
-      P.ne[0], P.ne[1], P.ne[2], up, fb, P.fbuf_stride, P.foff[a], ia, side, dL, S.pc_shared_built)
-    if (S.storage == 0) ENP_SWEEP(double, double);
-    else if (S.storage == 1) ENP_SWEEP(float, float);
-    else ENP_SWEEP(__nv_bfloat16, float);
-#undef ENP_SWEEP
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -2153,8 +2133,8 @@ extern "C" enp_status enp_set_preconditioner(enp_handle h, int two_level) {
 
 extern "C" enp_status enp_set_sweep(enp_handle h, int on) {
   if (!h) return ENP_ERR_INVALID_ARG;
-  if (on < 0 || on > 1) {
-    h->err = "on must be 0 or 1";
+  if (on < 0 || on > 2) {
+    h->err = "on must be 0, 1 or 2";
     return ENP_ERR_INVALID_ARG;
   }
   if (on == 1 && h->prm.dim != 3) {
@@ -2162,22 +2142,9 @@ extern "C" enp_status enp_set_sweep(enp_handle h, int on) {
     return ENP_ERR_UNSUPPORTED;
   }
   SolverState& S = state_of(h);
-  S.sweep = on == 1;
+  S.sweep_mode = on;
   S.sweep_ready = false;
   ++S.pc_gen;
-  // the flow axis and direction: the plate-flow axis in the sign of its mean
-  // speed, or the largest component of a constant velocity
-  const auto& pd = h->prm.pd;
-  if (pd.vel_kind == 1) {
-    S.sweep_axis = pd.velA;
-    S.sweep_dir = pd.vp[4] < 0.0 ? -1 : 1;
-  } else {
-    int ax = 0;
-    for (int d = 1; d < 3; ++d)
-      if (std::fabs(pd.vp[d]) > std::fabs(pd.vp[ax])) ax = d;
-    S.sweep_axis = ax;
-    S.sweep_dir = pd.vp[ax] < 0.0 ? -1 : 1;
-  }
   return ENP_OK;
 }
 
@@ -2217,6 +2184,16 @@ extern "C" enp_status enp_block_jacobi_apply(enp_handle h, const double* x, doub
   }
   cudaError_t e = bj_apply_any<double>(h, x, y);
   return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "block apply");
+}
+
+extern "C" enp_status enp_block_jacobi_apply_f32(enp_handle h, const float* x, float* y) {
+  if (!h || !x || !y) return ENP_ERR_INVALID_ARG;
+  if (!h->solver || state_of(h).storage < 0) {
+    h->err = "enp_block_jacobi_setup has not been called";
+    return ENP_ERR_INVALID_ARG;
+  }
+  cudaError_t e = bj_apply_any<float>(h, x, y);
+  return e == cudaSuccess ? ENP_OK : cuda_err(h, e, "block apply (FP32)");
 }
 
 // ---------------------------------------------------------------- FGMRES
@@ -3039,13 +3016,13 @@ extern "C" enp_status enp_initial_guess(enp_handle h, double* u, const enp_newto
   // of the system are c - c^in (zero here) with unit Jacobian rows, so every
   // Newton step leaves c = c^in; the sweep (which couples species across
   // elements) is off meanwhile
-  const bool sweep = S.sweep;
-  S.sweep = false;
+  const int sweep_mode = S.sweep_mode;
+  S.sweep_mode = 0;
   S.potential_only = true;
   ++S.pc_gen;
   enp_status s = enp_newton_solve(h, u, o, st);
   S.potential_only = false;
-  S.sweep = sweep;
+  S.sweep_mode = sweep_mode;
   S.sweep_ready = false;
   ++S.pc_gen;
   return s;

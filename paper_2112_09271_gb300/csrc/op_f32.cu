@@ -10,5 +10,6 @@ template int enp::eb3d_get<float>(int, int, int);
 template int enp::fpb3d_max<float>(int, int, int);
 template void enp::fpb3d_set<float>(int, int, int, int);
 template int enp::fpb3d_get<float>(int, int, int);
-template cudaError_t enp::launch_face_plane<float>(const OpParams&, const float*, const float*, int,
-                                                 cudaStream_t, int, int);
+template cudaError_t enp::launch_sweep_plane<float>(const OpParams&, const void*, int, const float*,
+                                                  float*, const float*, int, cudaStream_t, int, int,
+                                                  int, int, int);

@@ -9,5 +9,6 @@ template int enp::eb3d_get<double>(int, int, int);
 template int enp::fpb3d_max<double>(int, int, int);
 template void enp::fpb3d_set<double>(int, int, int, int);
 template int enp::fpb3d_get<double>(int, int, int);
-template cudaError_t enp::launch_face_plane<double>(const OpParams&, const double*, const double*, int,
-                                                 cudaStream_t, int, int);
+template cudaError_t enp::launch_sweep_plane<double>(const OpParams&, const void*, int, const double*,
+                                                  double*, const double*, int, cudaStream_t, int, int,
+                                                  int, int, int);

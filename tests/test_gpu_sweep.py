@@ -105,6 +105,49 @@ def test_sweep_follows_the_flow_direction(flow):
     assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("storage,tol", [(1, 1e-5), (2, 5e-2)])
+@pytest.mark.parametrize("shared", [-1, 0])
+def test_sweep_batched_storage_and_shared_blocks(storage, tol, shared):
+    """Two operating points with different states in one batch, FP32 or BF16
+    inverses, per point or one shared set (the inverses of point 0), FP64 and
+    FP32 vectors: point b's sweep solves (D_s + L_b) z = r_b, with D_s the
+    diagonal blocks of the point s whose inverses are stored and L_b point b's
+    own upstream couplings."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    enp = _enp()
+    P = W.config("reactor_n1_p2")
+    B = 2
+    phis = np.array([[4.0, 0, 0, 0], [20.0, 0, 0, 0]])
+    us = [W.random_state(P, 2), W.random_state(P, 3)]
+    rs = [W.random_vector(P, 5), W.random_vector(P, 6)]
+    op = enp.Operator(P, batch=B)
+    op.set_phi_app(phis)
+    op.set_shared_blocks(shared)
+    op.set_sweep(1)
+    op.block_jacobi_setup(_cuda(np.concatenate(us)), storage)
+    rd = _cuda(np.concatenate(rs))
+    z = op.block_jacobi_apply(rd).cpu().numpy().reshape(B, -1)
+    # FP32 vectors (the mixed inner solve's): the same system
+    z32 = op.block_jacobi_apply_f32(rd.float()).double().cpu().numpy().reshape(B, -1)
+    orcs = [oracle.Oracle(dataclasses.replace(P, bv_phi_app=list(phis[b]))) for b in range(B)]
+    n = P.n_dof
+    for b in range(B):
+        s = b if shared < 0 else shared
+        Ms = _lower_block_system(orcs[s], P, us[s]).tocoo()
+        Mb = _lower_block_system(orcs[b], P, us[b]).tocoo()
+        same = lambda M: (M.row // P.Np) % P.E == (M.col // P.Np) % P.E
+        ds, db = same(Ms), same(Mb)
+        M = sp.csr_matrix((np.concatenate([Ms.data[ds], Mb.data[~db]]),
+                           (np.concatenate([Ms.row[ds], Mb.row[~db]]),
+                            np.concatenate([Ms.col[ds], Mb.col[~db]]))), shape=(n, n))
+        ref = spla.spsolve(M.tocsc(), rs[b])
+        kappa = float(np.max(np.linalg.cond(orcs[s].block_diagonal(us[s]))))
+        bound = tol * kappa if storage == 1 else tol
+        assert np.linalg.norm(z[b] - ref) <= bound * np.linalg.norm(ref), (b, kappa)
+        assert np.linalg.norm(z32[b] - ref) <= bound * np.linalg.norm(ref), (b, kappa)
+
+
 def _fgmres(op, enp, u, b, sweep, f32=False, rtol=1e-10, graph=False):
     import torch
     op.set_sweep(1 if sweep else 0)
@@ -185,10 +228,41 @@ def test_sweep_newton_matches_oracle_newton(mixed):
 def test_sweep_argument_errors():
     enp = _enp()
     op = enp.Operator(W.config("cube_n2_p2"))
-    with pytest.raises(enp.EnpError) as ei:
-        op.set_sweep(2)
-    assert ei.value.status == enp.ENP_ERR_INVALID_ARG
+    for bad in (-1, 3):
+        with pytest.raises(enp.EnpError) as ei:
+            op.set_sweep(bad)
+        assert ei.value.status == enp.ENP_ERR_INVALID_ARG
     op2 = enp.Operator(W.config("mms2d_n3"))
     with pytest.raises(enp.EnpError) as ei:
         op2.set_sweep(1)
     assert ei.value.status == enp.ENP_ERR_UNSUPPORTED
+    op2.set_sweep(2)  # automatic: block-Jacobi on a 2D mesh
+
+
+def _channel_line(n_along):
+    """A plate-flow channel of n_along x 2 x 1 elements at p = 1."""
+    n_el = [n_along, 2, 1]
+    coords = W._linspace_coords(n_el, [n_along / 16.0, 1.0, 1.0])
+    P = W.config("cube_n2_p2", p=1)
+    return dataclasses.replace(P, n_el=n_el, coords=coords,
+                               tags=W._reactor_tags(3, n_el, coords, 1.0 / 3.0, 2.0 / 3.0),
+                               name="line")
+
+
+@pytest.mark.parametrize("n_along,same_as", [(96, 0), (128, 1)])
+def test_sweep_automatic_mode(n_along, same_as):
+    """The default (2) picks block-Jacobi below 128 elements along the flow and
+    the sweep from 128 on: its application equals that mode's bit for bit."""
+    enp = _enp()
+    P = _channel_line(n_along)
+    u = _cuda(W.random_state(P, 2))
+    r = _cuda(W.random_vector(P, 5))
+    zs = {}
+    for mode in (2, same_as, 1 - same_as):
+        op = enp.Operator(P)
+        if mode != 2:
+            op.set_sweep(mode)
+        op.block_jacobi_setup(u, enp.BJ_F64)
+        zs[mode] = op.block_jacobi_apply(r).cpu().numpy()
+    np.testing.assert_array_equal(zs[2], zs[same_as])
+    assert np.linalg.norm(zs[2] - zs[1 - same_as]) > 0
