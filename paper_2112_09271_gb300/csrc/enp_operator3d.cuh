@@ -201,6 +201,26 @@ __device__ __forceinline__ int face_node_pad(int a, int k, int j1, int j2) {
   return j1 + X * (j2 + N * k);
 }
 
+// Staging of global values into shared memory with asynchronous copies
+// (cp.async), so that all of a stage's loads are in flight at once without
+// holding registers. A slot of R receives the raw value of the vector type IO
+// (the same bytes for FP32 and FP64; a double into a double-float slot, whose
+// 8 bytes it fills, converted in place by stage_finish once the copies landed).
+template <class R, class IO>
+__device__ __forceinline__ void stage_copy(R* dst, const IO* src) {
+  static_assert(sizeof(IO) == sizeof(R) && (sizeof(R) == 4 || sizeof(R) == 8), "slot size");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(sizeof(R))
+               : "memory");
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// After stage_wait, by the thread that issued the copy: the slot's value as R.
+template <class R>
+__device__ __forceinline__ void stage_finish(R* slot) {
+  if constexpr (std::is_same<R, df>::value)
+    *slot = df_from_double_dev(*reinterpret_cast<const double*>(slot));
+}
+
 // The coefficients as forward tangents seeded on parameter j of
 // theta = (D_1..D_m, c_in_1..c_in_{m-1}, phi_app_0..phi_app_3).
 template <class R>
@@ -342,8 +362,19 @@ op3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __
     const int f = t / NN, i = t % NN;
     const long long gi = boff + f * EN + (long long)ee * NN + i;
     const int pi = f * NNP + padded_node<N>(i);
-    XA[pi] = R(u[gi]);
-    if (NV == 2) XA[NF * NNP + pi] = kBlk ? R(t == col ? 1 : 0) : R(v[gi]);
+    stage_copy(XA + pi, u + gi);
+    if (NV == 2) {
+      if (kBlk) XA[NF * NNP + pi] = R(t == col ? 1 : 0);
+      else stage_copy(XA + NF * NNP + pi, v + gi);
+    }
+  }
+  stage_wait();
+  if constexpr (std::is_same<R, df>::value) {
+    for (int t = tid; t < NF * NN; t += NT) {
+      const int pi = (t / NN) * NNP + padded_node<N>(t % NN);
+      stage_finish(XA + pi);
+      if (NV == 2 && !kBlk) stage_finish(XA + NF * NNP + pi);
+    }
   }
   // neighbour data of a face, fetched into registers one face ahead so that the
   // global loads overlap the computation of the previous stage
@@ -365,6 +396,26 @@ op3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __
     }
   };
   if constexpr (!S::kFB) prefetch(0);
+  if constexpr (S::kFB) {
+    // the six sides' lifted face terms are read after the volume terms: start
+    // moving them into L2 now (one 128-byte line per work item)
+    constexpr int PER = 2 * NF * FN;
+    constexpr int LINES = (PER * (int)sizeof(R) + 127) / 128 + 1;  // + 1: unaligned start
+    for (int q = tid; q < 6 * LINES; q += NT) {
+      const int s = q / LINES, l = q % LINES;
+      const int a = s >> 1, hi = s & 1;
+      const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+      // run-time axes: selections, not indexed arrays (which would go to local memory)
+      const long long gid = pick3(prm.foff, a) + (pick3(idx, a) + hi) +
+                            (long long)(pick3(prm.ne, a) + 1) *
+                                (pick3(idx, b0) + (long long)pick3(prm.ne, b0) * pick3(idx, b1));
+      const char* src = reinterpret_cast<const char*>(reinterpret_cast<const R*>(prm.fbuf) +
+                                                      (long long)bidx * prm.fbuf_stride +
+                                                      (gid * 2 + (hi ? 0 : 1)) * PER);
+      const int off = l * 128 < PER * (int)sizeof(R) ? l * 128 : PER * (int)sizeof(R) - 1;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(src + off));
+    }
+  }
   __syncthreads();
 
   // ---------------------------------------------------------------- volume
@@ -497,8 +548,9 @@ op3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* __
       const long long gid = prm.foff[a] + (idx[a] + hi) +
                             (long long)(prm.ne[a] + 1) * (idx[b0] + (long long)prm.ne[b0] * idx[b1]);
       const R* src = fb + (gid * 2 + (hi ? 0 : 1)) * PER;
-      for (int r = tid; r < PER; r += NT) FS[s * PER + r] = src[r];
+      for (int r = tid; r < PER; r += NT) stage_copy(FS + s * PER + r, src + r);
     }
+    stage_wait();
     __syncthreads();
     // each row gathers its six face terms in side order (no two threads write
     // one row)
@@ -1035,11 +1087,30 @@ face3d_kernel(const OpParams prm, const io_t<R>* __restrict__ u, const io_t<R>* 
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const long long o = f * EN + i;
-        XS[f * NNP + pi] = hasL ? R(u[gL + o]) : R(0);
-        XS[(NA + f) * NNP + pi] = hasU ? R(u[gU + o]) : R(0);
+        if (hasL) stage_copy(XS + f * NNP + pi, u + gL + o);
+        else XS[f * NNP + pi] = R(0);
+        if (hasU) stage_copy(XS + (NA + f) * NNP + pi, u + gU + o);
+        else XS[(NA + f) * NNP + pi] = R(0);
         if (NA > NF) {
-          XS[(NF + f) * NNP + pi] = hasL ? R(v[gL + o]) : R(0);
-          XS[(NA + NF + f) * NNP + pi] = hasU ? R(v[gU + o]) : R(0);
+          if (hasL) stage_copy(XS + (NF + f) * NNP + pi, v + gL + o);
+          else XS[(NF + f) * NNP + pi] = R(0);
+          if (hasU) stage_copy(XS + (NA + NF + f) * NNP + pi, v + gU + o);
+          else XS[(NA + NF + f) * NNP + pi] = R(0);
+        }
+      }
+    }
+    stage_wait();
+    if constexpr (std::is_same<R, df>::value) {
+      for (int i = tid; i < NN; i += NT) {
+        const int pi = padded_node<N>(i);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          if (hasL) stage_finish(XS + f * NNP + pi);
+          if (hasU) stage_finish(XS + (NA + f) * NNP + pi);
+          if (NA > NF) {
+            if (hasL) stage_finish(XS + (NF + f) * NNP + pi);
+            if (hasU) stage_finish(XS + (NA + NF + f) * NNP + pi);
+          }
         }
       }
     }
