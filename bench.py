@@ -62,8 +62,8 @@ DF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
 # of the sources that kernel is built from (stale -> reported null): the
 # operator kernels from the operator headers, the block apply from the solver.
 TRAFFIC = {
-    ("21842bd24676", "jvp_df32", "channel64_p3"): 699.90e6,  # face + element kernel
-    ("21842bd24676", "jvp_f32", "channel64_p3"): 242.14e6,   # face + element kernel
+    ("5d4d7cdd78a5", "jvp_df32", "channel64_p3"): 699.86e6,  # face + element kernel
+    ("5d4d7cdd78a5", "jvp_f32", "channel64_p3"): 243.07e6,   # face + element kernel
     ("33fe528c30dc", "bj_apply_f32", "channel64_p3"): 4933.98e6,
 }
 
