@@ -410,9 +410,9 @@ typedef struct {
  * (lambda = step0), on return the solution at the last converged lambda.
  * phi_app: host [batch][4], the target potentials; on return the handle's
  * applied potentials are the target ones. stats: host pointer (may be NULL).
- * With the environment variable ENP_CONTINUATION_LOG set, one progress line
- * per stage (lambda, status, Newton and FGMRES iterations, elapsed time) goes
- * to stderr. Synchronises. Errors: NOT_CONVERGED (the increment fell below
+ * With the environment variable ENP_CONTINUATION_LOG set, two progress lines
+ * per stage (lambda, status, Newton and FGMRES iterations, elapsed time; the
+ * stage's ||R|| / ||R_0|| after each Newton iteration) go to stderr. Synchronises. Errors: NOT_CONVERGED (the increment fell below
  * step_min), INVALID_ARG, NONFINITE, OOM, CUDA. */
 enp_status enp_newton_continuation(enp_handle h, double* u, const double* phi_app,
                                    const enp_continuation_opts* copts,

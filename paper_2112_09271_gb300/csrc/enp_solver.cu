@@ -3047,7 +3047,7 @@ extern "C" enp_status enp_newton_continuation(enp_handle h, double* u, const dou
   enp_continuation_stats cs{};
   double lam = 0.0, dl = c->step0;
   enp_status status = ENP_OK;
-  // ENP_CONTINUATION_LOG set: one progress line per stage on stderr (long runs)
+  // ENP_CONTINUATION_LOG set: progress lines per stage on stderr (long runs)
   const bool log = std::getenv("ENP_CONTINUATION_LOG") != nullptr;
   const auto t_start = std::chrono::steady_clock::now();
   while (true) {
@@ -3073,6 +3073,11 @@ extern "C" enp_status enp_newton_continuation(enp_handle h, double* u, const dou
                    "elapsed %.1f s\n",
                    cs.stages, last ? 1.0 : nl, (int)s2, ns.iterations, ns.krylov_iterations,
                    ns.initial_norm > 0 ? ns.residual_norm / ns.initial_norm : 0.0, el);
+      // the Newton history of the stage: ||R|| / ||R_0|| after each iteration
+      std::fprintf(stderr, "  history");
+      for (int i = 0; i <= ns.iterations && i < 64; ++i)
+        std::fprintf(stderr, " %.2e", ns.initial_norm > 0 ? ns.history[i] / ns.initial_norm : 0.0);
+      std::fprintf(stderr, "\n");
       std::fflush(stderr);
     }
     if (s2 == ENP_OK) {

@@ -46,18 +46,26 @@ template <class TS, class TA, class TV, int NT>
 __device__ __forceinline__ void sweep_gemv(const TS* __restrict__ B, const TA* ts, TV* zb, int n,
                                            int NN, long long EN, long long e) {
   for (int r = threadIdx.x; r < n; r += NT) {
-    // eight independent partial sums keep eight loads per thread in flight
-    TA acc[8] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    // sixteen independent partial sums keep sixteen loads per thread in flight:
+    // a plane has few blocks per SM, and each streams its whole block inverse
+    constexpr int K = 16;
+    TA acc[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] = TA(0);
     int c = 0;
-    for (; c + 8 <= n; c += 8) {
-      TS bv[8];
+    for (; c + K <= n; c += K) {
+      TS bv[K];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) bv[q] = B[(long long)(c + q) * n + r];
+      for (int q = 0; q < K; ++q) bv[q] = B[(long long)(c + q) * n + r];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] += (TA)bv[q] * ts[c + q];
+      for (int q = 0; q < K; ++q) acc[q] += (TA)bv[q] * ts[c + q];
     }
     for (; c < n; ++c) acc[0] += (TA)B[(long long)c * n + r] * ts[c];
-    const TA sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+#pragma unroll
+    for (int h = K / 2; h > 0; h /= 2)
+#pragma unroll
+      for (int q = 0; q < h; ++q) acc[q] += acc[q + h];
+    const TA sum = acc[0];
     const int f = r / NN, i = r % NN;
     zb[f * EN + e * NN + i] = (TV)sum;
   }
@@ -94,13 +102,16 @@ sweep_fused_kernel(const OpParams prm, const void* __restrict__ binv, int storag
   const long long blk = ((long long)(shared_blocks ? 0 : b) * prm.E + e) * (long long)nb * nb;
   {
     // the block inverse does not depend on the face terms: start moving it into
-    // L2 now, so that the product below does not wait on HBM
+    // L2 now, so that the product below does not wait on HBM (blocks up to 64 KB:
+    // a plane of larger ones exceeds L2, and their products stream from HBM)
     const size_t tsz = storage == 0 ? 8 : (storage == 1 ? 4 : 2);
     const char* p0 = reinterpret_cast<const char*>(binv) + blk * tsz;
     const size_t bytes = (size_t)nb * nb * tsz;
-    for (size_t off = (size_t)tid * 128; off < bytes; off += (size_t)NT * 128)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + off));
-    if (tid == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + bytes - 1));
+    if (bytes <= 65536) {
+      for (size_t off = (size_t)tid * 128; off < bytes; off += (size_t)NT * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + off));
+      if (tid == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + bytes - 1));
+    }
   }
   // the face between e and its upstream neighbour: plane ia of direction a;
   // e is its upper element (side 1) when the flow runs along +e_a
