@@ -1028,12 +1028,13 @@ gj_invert_regs(const TB* __restrict__ blocks, TS* __restrict__ out, int n,
 // cluster of two CTAs on two SMs. Global row i lives in CTA i % 2 as local row
 // i / 2 (warp w: local rows w + 16 r, r < 8; lane l: columns l + 32 c, c < 8).
 // Each CTA publishes its rows' part of the pivot column in its own shared
-// memory; after a cluster barrier every warp of both CTAs reads both halves
-// (the other through distributed shared memory) and finds the same pivot; the
-// owning CTA publishes the pivot row, a second cluster barrier, every thread
-// reads it from the owner. The inverse is staged in the shared memory of the
-// CTA that owns each output row (out[c][.] in CTA c % 2) and written out
-// coalesced. Singular pivots and the output order are as in gj_invert_regs.
+// memory, with each warp's best unused row and that row's values; after a
+// cluster barrier every warp of both CTAs reads both halves (the other through
+// distributed shared memory), finds the same pivot and reads the pivot row
+// from the owning CTA: one cluster barrier per step. The inverse is staged in
+// the shared memory of the CTA that owns each output row (out[c][.] in CTA
+// c % 2) and written out coalesced. Singular pivots and the output order are
+// as in gj_invert_regs.
 constexpr int kGjcNW = 16, kGjcRPW = 8, kGjcCPL = 8;
 constexpr int kGjcRows = kGjcNW * kGjcRPW;  // local rows per CTA (128)
 constexpr int kGjcCols = 32 * kGjcCPL;      // columns (256)
@@ -1050,7 +1051,7 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
   __shared__ float colv[2][kGjcRows];
   __shared__ float candv[2][kGjcNW];   // per warp: largest |M_ik| over its unused rows
   __shared__ int candi[2][kGjcNW];     //           and that (global) row
-  __shared__ float rowv[kGjcCols];
+  __shared__ float rowc[2][kGjcNW][kGjcCols];   //      and that row's values
   __shared__ int piv[kGjcCols], stepof[2 * kGjcRows];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long long e = blockIdx.x / 2;
@@ -1059,7 +1060,7 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
   const float* colv_p = cluster.map_shared_rank(&colv[0][0], peer);
   const float* candv_p = cluster.map_shared_rank(&candv[0][0], peer);
   const int* candi_p = cluster.map_shared_rank(&candi[0][0], peer);
-  float* rowv_p = cluster.map_shared_rank(&rowv[0], peer);
+  const float* rowc_p = cluster.map_shared_rank(&rowc[0][0][0], peer);
   float* stage_p = cluster.map_shared_rank(stage, peer);
   float M[kGjcRPW][kGjcCPL];
   // global row of local row li in this CTA: 2 li + rank
@@ -1073,13 +1074,15 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
     }
   }
   unsigned used = 0u;
-  // publish column kc (from lane kc % 32 of every warp): its values, and the
-  // warp's pivot candidate among its unused rows
+  // publish column kc (from lane kc % 32 of every warp): its values, the
+  // warp's pivot candidate among its unused rows and that row's values, so
+  // that the step that picks it needs one cluster barrier, not two
   auto publish = [&](int kc, int buf) {
-    if (lane == (kc & 31)) {
+    const int src_lane = kc & 31;
+    int br = -1;  // the candidate's local row slot r
+    if (lane == src_lane) {
       const int cc = kc >> 5;
       float best = -1.f;
-      int bi = 0;
 #pragma unroll
       for (int c = 0; c < kGjcCPL; ++c)
         if (c == cc) {
@@ -1089,11 +1092,20 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
             const float v = M[r][c];
             colv[buf][li] = v;
             const float av = (i < n && !((used >> r) & 1u)) ? fabsf(v) : -1.f;
-            if (av > best) { best = av; bi = i; }   // rows ascend with r: ties keep the lower
+            if (av > best) { best = av; br = r; }   // rows ascend with r: ties keep the lower
           }
         }
       candv[buf][w] = best;
-      candi[buf][w] = bi;
+      candi[buf][w] = 2 * (w + kGjcNW * (br < 0 ? 0 : br)) + rank;
+    }
+    br = __shfl_sync(0xffffffffu, br, src_lane);
+    if (br >= 0) {
+#pragma unroll
+      for (int r = 0; r < kGjcRPW; ++r)
+        if (r == br) {
+#pragma unroll
+          for (int c = 0; c < kGjcCPL; ++c) rowc[buf][w][lane + 32 * c] = M[r][c];
+        }
     }
   };
   publish(0, 0);
@@ -1116,20 +1128,14 @@ gj_invert_cluster(const float* __restrict__ blocks, TS* __restrict__ out, int n,
     const int p = bi, owner = p & 1, lp = p >> 1;
     const float pivv = owner == rank ? colv[buf][lp] : colv_p[buf * kGjcRows + lp];
     const float pinv = __frcp_rn(pivv);
-    const bool own = owner == rank && w == lp % kGjcNW;
+    const int wp = lp % kGjcNW;
+    const bool own = owner == rank && w == wp;
     const int rp = lp / kGjcNW;
-    if (own) {
-      used |= 1u << rp;
-#pragma unroll
-      for (int r = 0; r < kGjcRPW; ++r)
-        if (r == rp) {
-#pragma unroll
-          for (int c = 0; c < kGjcCPL; ++c) rowv[lane + 32 * c] = M[r][c];
-        }
-    }
+    if (own) used |= 1u << rp;
     if (tid == 0) { piv[k] = p; stepof[p] = k; }
-    cluster.sync();
-    const float* rsrc = owner == rank ? rowv : rowv_p;
+    // the pivot row: its warp's published candidate row, in the owning CTA
+    const float* rsrc = (owner == rank ? &rowc[0][0][0] : rowc_p) +
+                        ((size_t)buf * kGjcNW + wp) * kGjcCols;
     float rj[kGjcCPL];
 #pragma unroll
     for (int c = 0; c < kGjcCPL; ++c) {
